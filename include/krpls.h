@@ -1,0 +1,233 @@
+/*
+ * krpls.h — C ABI of libkrpls, exact leverage-score sampling from Khatri-Rao
+ * products and the sketched least-squares solves it feeds (CP-ALS), for
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: Bharadwaj, Malik, Murray, Grigori, Buluç, Demmel, "Fast Exact
+ * Leverage Score Sampling from Khatri-Rao Products with Applications to
+ * Tensor Decomposition", NeurIPS 2023 (arXiv 2301.12584).
+ *
+ * Conventions for every call below
+ *   - Matrices are row-major and contiguous.  Factor U_k is I_k x R, FP32.
+ *   - Pointers are DEVICE pointers unless the parameter name ends in _host
+ *     or the comment says "host or device" (those accept pinned/pageable
+ *     host memory or device memory; the copy is made with cudaMemcpyDefault).
+ *   - All work is enqueued asynchronously on the CUDA stream passed to
+ *     krp_create (0 = legacy default stream).  Output buffers are valid
+ *     after that stream is synchronised (e.g. by krp_sync_status).
+ *   - The caller owns every buffer it passes in.  The sampler owns copies of
+ *     the factors, the segment trees, and all scratch.  No call allocates
+ *     device memory except krp_create, krp_sptensor_create and the first
+ *     call that needs a larger scratch buffer (documented per call).
+ *   - Errors: arguments the host can check return immediately with a
+ *     negative krp_status and leave no work enqueued.  Conditions found on
+ *     the device (zero or non-finite probability mass, a singular normal
+ *     matrix) set a device status word that krp_sync_status returns and
+ *     clears.  krp_last_error gives a message for the most recent failure.
+ *   - No call prints, aborts or throws across the ABI.
+ */
+#ifndef KRPLS_H
+#define KRPLS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct krp_sampler krp_sampler;     /* opaque */
+typedef struct krp_sptensor krp_sptensor;   /* opaque */
+
+typedef enum {
+    KRP_OK = 0,
+    KRP_EINVAL = -1,      /* bad argument (host-checked)                         */
+    KRP_ENOMEM = -2,      /* device allocation failed                            */
+    KRP_ECUDA = -3,       /* a CUDA runtime call failed                          */
+    KRP_EZERO = -4,       /* total probability mass is zero (A == 0, or U_k unset)*/
+    KRP_ESINGULAR = -5,   /* normal matrix not positive definite                 */
+    KRP_ENUMERIC = -6,    /* NaN or Inf probability mass seen on the device      */
+    KRP_ETIMEOUT = -7,    /* reserved: a bounded device wait gave up             */
+    KRP_ESTATE = -8       /* call made in the wrong state (e.g. factor not set)  */
+} krp_status;
+
+typedef enum {
+    KRP_PREC_FP32 = 0,    /* segment-tree Grams by FP32 FMA                      */
+    KRP_PREC_BF16X3 = 1   /* Grams on tcgen05 tensor cores, BF16 hi/lo split,    */
+                          /* three products, FP32 accumulate                     */
+} krp_precision;
+
+#define KRP_PINV_FALLBACK 1  /* krp_solve_*: if Cholesky fails, use the FP64
+                                eigen-pseudo-inverse instead of failing       */
+
+/* ------------------------------------------------------------------------
+ * Construction (Thm 1.1 part 1; Alg. 1 ConstructKRPSampler; Alg. 3
+ * BuildSampler; Lemma 3.2).
+ *
+ * krp_create: a sampler for N factors U_k (I_host[k] x R).  F is the leaf
+ * size of each factor's segment tree T_{I_k,F} (F = 0 selects F = R, the
+ * paper's choice for the row samplers Z_k).  The tree's leaf count is
+ * ceil(I_k/F) padded to a power of two with empty leaves.  Limits:
+ * 1 <= N <= 16, 1 <= R <= 128, 1 <= I_k < 2^31, 1 <= F <= 4*R.
+ * `stream` is a cudaStream_t (may be NULL).  Allocates all factor, tree and
+ * sampler storage.  On failure *out is set to NULL.
+ * ---------------------------------------------------------------------- */
+krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, int F,
+                      int precision, void* stream);
+
+/* Release everything the sampler owns (NULL is a no-op).  Synchronises the
+ * sampler's stream first. */
+void krp_destroy(krp_sampler* s);
+
+/* Full-factor update (Thm 1.1 part 1; Alg. 1 lines 2-3).  Copies U (I_j x R,
+ * host or device) into the sampler and rebuilds Z_j: leaf partial Grams
+ * G^v = U[S(v)]ᵀ U[S(v)] and their sums up the tree (Eq. partial_gram),
+ * whose root is G_j = U_jᵀ U_j.  Returns KRP_EINVAL for j out of range. */
+krp_status krp_set_factor(krp_sampler* s, int j, const float* U);
+
+/* Same as krp_set_factor with an explicit precision for this rebuild. */
+krp_status krp_set_factor_prec(krp_sampler* s, int j, const float* U, int precision);
+
+/* ------------------------------------------------------------------------
+ * Sampling (Thm 1.1 part 2; Alg. 2 KRPSample; Alg. 4 RowSample; Thm 3.1).
+ *
+ * Draws J i.i.d. row indices of A = ⊙_{k != exclude_j} U_k from the exact
+ * leverage-score distribution (Eq. leverage_definition), factors taken in
+ * ascending k.  Per draw the sampler forms G = ⊛ G_k and G⁺ (FP64,
+ * eigen-pseudo-inverse with cutoff R*2^-52*lam_max), and for each included k
+ * G_{>k} = G⁺ ⊛ ⊛_{m>k} G_m (Eq. G_geq_k_defn), its eigendecomposition
+ * (FP64, eigenvalues ascending, negatives clamped to 0) and the eigencomponent
+ * sampler E_k (Alg. 2 line 5).  Each sample then descends E_k and Z_k for
+ * each k (two-stage draw, Eqs. first_dist and second_conditional_dist).
+ *
+ * Uniforms: Philox4x32-10 with key (seed lo32, seed hi32) and counter
+ * (sample index d, draw_id lo32, position of k among included factors, 0);
+ * word 0 drives the eigencomponent stage and word 1 the row stage, each
+ * mapped to (2*(x>>9)+1)*2^-24.
+ *
+ * Outputs (device):
+ *   idx     int32 [N][J] (row k holds the index into U_k; row exclude_j is
+ *           left untouched).
+ *   weight  float [J], w_s = 1/sqrt(J q_s) with q_s = ℓ_s / rank(A) (Sec. 2.1).
+ *   logq    float [J] or NULL: log q_s.
+ *   SA      float [J][R] or NULL: the sketched design rows w_s ⊛_k U_k[s_k,:]
+ *           (fused gather; same values as krp_gather).
+ * Requires every included factor set (else KRP_ESTATE).  J >= 1, J < 2^31.
+ * exclude_j = -1 includes every factor.  Device-side failures (zero or
+ * non-finite mass) are reported by krp_sync_status.
+ * ---------------------------------------------------------------------- */
+krp_status krp_sample(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed,
+                      uint64_t draw_id, int32_t* idx, float* weight, float* logq, float* SA);
+
+/* krp_sample split in two, for callers that time or overlap the phases:
+ * krp_sample_prepare does the per-draw work that does not depend on the
+ * samples (Alg. 2 lines 1-5: G, G⁺, G_{>k}, eigendecompositions, E_k) for one
+ * exclusion; krp_sample_draw then runs the descent (lines 6-12) and may be
+ * called several times (other J, seed or draw_id) while no factor changes.
+ * krp_sample_draw returns KRP_ESTATE if the last prepare was for another
+ * exclude_j or a factor was set since. */
+krp_status krp_sample_prepare(krp_sampler* s, int exclude_j);
+krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
+                           int32_t* idx, float* weight, float* logq, float* SA);
+
+/* Sampled-row gather: SA[s,:] = weight[s] * ⊛_{k != exclude_j} U_k[idx[k][s], :]
+ * (the rows of S·A, Sec. 2.1).  idx/weight as produced by krp_sample.  Indices
+ * are not range-checked on the device; pass krp_sample's output. */
+krp_status krp_gather(krp_sampler* s, int exclude_j, int64_t J, const int32_t* idx,
+                      const float* weight, float* SA);
+
+/* Dense sketched solve X = argmin ||SA X - SB||_F (Thm 2.1) by the normal
+ * equations: M = SAᵀSA and Z = SAᵀ SB formed in FP32 with an FP64 final
+ * reduction, FP64 Cholesky of M, X = M⁻¹ Z.  SB[s,:] = weight[s] * B_rows[s,:]
+ * where B_rows (J x nrhs) are the caller's unweighted rows of B at the sampled
+ * tuples.  X is R x nrhs (device).  1 <= nrhs <= 64.  If M is not positive
+ * definite: with flags & KRP_PINV_FALLBACK, X = M⁺ Z (FP64 eigen-pseudo-inverse);
+ * otherwise the device status becomes KRP_ESINGULAR and X is zero.  The first
+ * call with a larger J or nrhs than any before may allocate scratch. */
+krp_status krp_solve_dense(krp_sampler* s, int64_t J, const float* SA, const float* weight,
+                           const float* B_rows, int nrhs, float* X, int flags);
+
+/* ------------------------------------------------------------------------
+ * Sparse tensors and STS-CP (Sec. 3.3; Alg. 6 CP-ALS; App. A.9).
+ *
+ * krp_sptensor_create: an N-mode sparse tensor with dims I_host and nnz
+ * nonzeros; coords_host[k] (host, int32, nnz entries each) and vals_host
+ * (host, FP32).  Builds, for every mode j, an index of the mode-j fibers:
+ * nonzeros sorted by a key packing the other modes' coordinates, with the
+ * fiber start offsets.  Duplicated coordinates must not occur.  The index
+ * lives on the device; the sort runs on the host (as in the paper's
+ * preprocessing).  Requires Σ_{k != j} ceil(log2 I_k) <= 63 for every j.
+ * ---------------------------------------------------------------------- */
+krp_status krp_sptensor_create(krp_sptensor** out, int N, const int64_t* I_host, int64_t nnz,
+                               const int32_t* const* coords_host, const float* vals_host,
+                               void* stream);
+void krp_sptensor_destroy(krp_sptensor* t);
+
+/* Sketched mode-j solve of Alg. 6 line 6 against the tensor's matricization:
+ * Y = SBᵀ SA (I_j x R; each sampled tuple's mode-j fiber is looked up in the
+ * index and its nonzeros scattered with weight w_s), M = SAᵀSA, U_out = Y M⁻¹
+ * (M⁻¹ from FP64 Cholesky).  idx/weight/SA from krp_sample(exclude_j = j).
+ * U_out: I_j x R (device).  Allocates scratch on first use. */
+krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* t, int j, int64_t J,
+                            const int32_t* idx, const float* weight, const float* SA,
+                            float* U_out, int flags);
+
+/* One STS-CP sweep (Alg. 6 lines 5-9) over all modes j = 0..N-1: draw J
+ * samples excluding j (draw id draw_base + j), solve for U_j, set
+ * sigma[i] = ||U_j[:,i]||_2, normalise U_j's columns, and rebuild Z_j.
+ * sigma: R floats (device), holds the last mode's norms.  The sampler's
+ * factors are the ALS state. */
+krp_status krp_cp_als_sweep(krp_sampler* s, const krp_sptensor* t, int64_t J, uint64_t seed,
+                            uint64_t draw_base, float* sigma);
+
+/* CP fit 1 - ||T~ - T||_F / ||T||_F (Sec. 4.3) of the sampler's factors
+ * with weights sigma (device, R floats) against tensor t.  Result written to
+ * *fit_host after an internal stream synchronisation. */
+krp_status krp_cp_fit(krp_sampler* s, const krp_sptensor* t, const float* sigma, double* fit_host);
+
+/* ------------------------------------------------------------------------
+ * Status, inspection.
+ * ---------------------------------------------------------------------- */
+/* Synchronise the sampler's stream, return and clear the device status word
+ * (KRP_OK if no device-side failure), or KRP_ECUDA if the sync failed. */
+krp_status krp_sync_status(krp_sampler* s);
+
+/* Number of CUDA kernels this library has launched in the process so far
+ * (all samplers; for accounting in benchmarks). */
+int64_t krp_launch_count(void);
+
+/* Message for the most recent failure on this sampler; never NULL. */
+const char* krp_last_error(const krp_sampler* s);
+
+/* krp_sample (without logq/SA) that also records, for samples 0..n_trace-1,
+ * every branch the descent evaluated (Alg. 4 lines 12-17): trace (device,
+ * float) is laid out [n_trace][n_included][2 stages: eigencomponent, row][66]
+ * with [0] = root mass C and, for level l = 0..depth-1, [2+2l] = mass of the
+ * left child m(L(c)) and [3+2l] = mass of the current node m(c) (the right
+ * child inherits m(c) - m(L(c))).  The left-branch probability at level l is
+ * [2+2l]/[3+2l].  For tests; same draws as krp_sample with the same
+ * arguments. */
+krp_status krp_debug_trace(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
+                           int32_t* idx, float* weight, float* trace, int64_t n_trace);
+
+/* Tree geometry of factor j: padded leaf count L, depth d = log2 L, and the
+ * node stride (floats) of the stored upper triangles. */
+krp_status krp_tree_info(const krp_sampler* s, int j, int64_t* L_host, int* depth_host,
+                         int* node_stride_host);
+
+/* Copy factor j's segment tree to host memory (L * node_stride floats).
+ * Slot 0 is the root G_j; slot v/2 holds the left child v (v even) in heap
+ * numbering (root 1, children 2v, 2v+1, leaf b = node L + b).  Each slot is
+ * the upper triangle of G^v packed row by row, then zero padding.  Synchronous. */
+krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_floats);
+
+/* After krp_sample: copy the FP64 eigendecomposition of G_{>k} used for
+ * included factor k (lam: R values ascending, V: R x R row-major with
+ * eigenvector u in column u), the FP64 G⁺ (R x R) and rank(A).  Any pointer
+ * may be NULL.  Synchronous. */
+krp_status krp_get_prep(const krp_sampler* s, int k, double* lam_host, double* V_host,
+                        double* Gplus_host, int* rank_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KRPLS_H */

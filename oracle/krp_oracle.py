@@ -212,7 +212,7 @@ class SamplerPrep:
 
 
 def krp_sample(Us, exclude, J, seed, draw_id, d0=0, eig_override=None,
-               chunk=65536, record=False):
+               chunk=65536, record=False, prep=None):
     """Draw samples d0..d0+J-1 by Alg. 2 with Philox uniforms.
 
     Returns dict with idx (n_incl, J) int64, weight (J,), q (J,), logq (J,),
@@ -220,8 +220,10 @@ def krp_sample(Us, exclude, J, seed, draw_id, d0=0, eig_override=None,
     shaped (n_incl, 2, J) with stage 0 = eigencomponent, 1 = row.
     The weight is 1/sqrt(J_total * q) with q = ℓ_s / rank (Sec. 2.1), where
     J_total is `J` (callers drawing a sub-range pass their own scaling).
+    A SamplerPrep built for the same factors may be passed to skip lines 1-5.
     """
-    prep = SamplerPrep(Us, exclude, eig_override)
+    if prep is None:
+        prep = SamplerPrep(Us, exclude, eig_override)
     incl = prep.incl
     ni = len(incl)
     R = prep.R

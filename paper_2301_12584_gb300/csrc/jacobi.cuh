@@ -1,0 +1,111 @@
+// One-CTA symmetric eigendecomposition by cyclic Jacobi (shared by the
+// sampler preparation and the pseudo-inverse fallback of the solves).
+#pragma once
+
+#include "common.cuh"
+
+namespace krp {
+
+// ---------------------------------------------------------------------------
+// One-CTA cyclic Jacobi (Golub & Van Loan, Algorithms 8.5.2-8.5.3, with the
+// round-robin ordering of Sec. 8.5.4 so that n/2 disjoint rotations run at
+// once).  A (n x n, row-major, symmetric) is overwritten; on exit its diagonal
+// holds the eigenvalues and V (n x n) the eigenvectors in its columns.
+// Scalar = float or double.  work: 4 * (n/2 + 1) Scalars, pair: 2*(n/2+1) ints.
+// ---------------------------------------------------------------------------
+template <typename Scalar>
+__device__ void jacobi_eig(Scalar* A, Scalar* V, int n, Scalar* cs, int* pr, double* red,
+                           int max_sweeps, double tol) {
+    const int m = n + (n & 1);  // players, a dummy when n is odd
+    const int npair = m / 2;
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? Scalar(1) : Scalar(0);
+    __syncthreads();
+    for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+        // convergence test: off(A)^2 <= tol^2 * ||A||_F^2
+        double off = 0.0, tot = 0.0;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const double a = (double)A[e];
+            tot += a * a;
+            if (e / n != e % n) off += a * a;
+        }
+        off = warp_sum_d(off);
+        tot = warp_sum_d(tot);
+        if ((threadIdx.x & 31) == 0) {
+            red[2 * (threadIdx.x >> 5)] = off;
+            red[2 * (threadIdx.x >> 5) + 1] = tot;
+        }
+        __syncthreads();
+        double OFF = 0.0, TOT = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            OFF += red[2 * w];
+            TOT += red[2 * w + 1];
+        }
+        __syncthreads();
+        if (OFF <= tol * tol * TOT || OFF == 0.0) break;
+        for (int step = 0; step < m - 1; ++step) {
+            for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+                auto player = [&](int pos) { return pos == 0 ? 0 : ((pos - 1 + step) % (m - 1)) + 1; };
+                int p = player(k), q = player(m - 1 - k);
+                if (p > q) {
+                    const int t = p;
+                    p = q;
+                    q = t;
+                }
+                Scalar c = 1, sn = 0;
+                if (q < n) {
+                    const Scalar apq = A[p * n + q];
+                    if (apq != Scalar(0)) {
+                        const Scalar tau = (A[q * n + q] - A[p * n + p]) / (Scalar(2) * apq);
+                        const Scalar t = (tau >= Scalar(0) ? Scalar(1) : Scalar(-1)) /
+                                         (fabs(tau) + hypot(Scalar(1), tau));
+                        c = Scalar(1) / sqrt(Scalar(1) + t * t);
+                        sn = t * c;
+                    }
+                } else {
+                    p = -1;
+                }
+                pr[2 * k] = p;
+                pr[2 * k + 1] = q;
+                cs[2 * k] = c;
+                cs[2 * k + 1] = sn;
+            }
+            __syncthreads();
+            // rows: A <- Jᵀ A
+            for (int w = threadIdx.x; w < npair * n; w += blockDim.x) {
+                const int k = w / n, col = w % n;
+                const int p = pr[2 * k], q = pr[2 * k + 1];
+                if (p < 0 || cs[2 * k + 1] == Scalar(0)) continue;
+                const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
+                const Scalar ap = A[p * n + col], aq = A[q * n + col];
+                A[p * n + col] = c * ap - sn * aq;
+                A[q * n + col] = sn * ap + c * aq;
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J
+            for (int w = threadIdx.x; w < npair * n; w += blockDim.x) {
+                const int k = w / n, row = w % n;
+                const int p = pr[2 * k], q = pr[2 * k + 1];
+                if (p < 0 || cs[2 * k + 1] == Scalar(0)) continue;
+                const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
+                const Scalar ap = A[row * n + p], aq = A[row * n + q];
+                A[row * n + p] = c * ap - sn * aq;
+                A[row * n + q] = sn * ap + c * aq;
+                const Scalar vp = V[row * n + p], vq = V[row * n + q];
+                V[row * n + p] = c * vp - sn * vq;
+                V[row * n + q] = sn * vp + c * vq;
+            }
+            __syncthreads();
+            // the rotated pair is now decoupled
+            for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+                const int p = pr[2 * k], q = pr[2 * k + 1];
+                if (p >= 0 && cs[2 * k + 1] != Scalar(0)) {
+                    A[p * n + q] = Scalar(0);
+                    A[q * n + p] = Scalar(0);
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+}  // namespace krp

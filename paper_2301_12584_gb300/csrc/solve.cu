@@ -1,0 +1,257 @@
+// a8: sketched least-squares solve by the normal equations (Thm 2.1; the
+// O(JR^2) solve of App. A.9):  M = SAᵀSA,  Z = SAᵀ SB with SB = diag(w) B,
+// FP64 Cholesky M = L Lᵀ, X = M⁻¹ Z.  If Cholesky fails, optionally the FP64
+// eigen-pseudo-inverse (cutoff R * 2^-52 * lam_max): X = M⁺ Z.
+//
+// normal_partial: grid-strided CTAs each reduce a contiguous chunk of rows
+// into FP32 partial sums of the upper triangle of M and of Z (rows staged in
+// shared memory, one output per thread slot).  normal_solve (one CTA): FP64
+// sum of the partials in a fixed order, Cholesky, triangular solves.
+#include "common.cuh"
+#include "internal.h"
+#include "jacobi.cuh"
+
+#include <math.h>
+
+#include <algorithm>
+
+namespace krp {
+
+constexpr int SOLVE_ROWS = 32;  // rows per shared-memory tile
+
+// Z columns: B_rows (J x nrhs) weighted by w; with B_rows == nullptr Z is not formed.
+__global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ SA, const float* __restrict__ w,
+                                                      const float* __restrict__ B, int64_t J, int R, int nrhs,
+                                                      int64_t rows_per_cta, float* __restrict__ part) {
+    extern __shared__ __align__(16) float sm[];
+    float* sA = sm;                          // SOLVE_ROWS x R
+    float* sB = sA + SOLVE_ROWS * R;         // SOLVE_ROWS x nrhs
+    const int T = tri_size(R);
+    const int nout = T + R * nrhs;
+    constexpr int MAXO = 8;                  // outputs per thread; blockIdx.y selects the output chunk
+    float acc[MAXO];
+    int oi[MAXO], oj[MAXO];
+#pragma unroll
+    for (int o = 0; o < MAXO; ++o) {
+        acc[o] = 0.f;
+        const int id = (blockIdx.y * MAXO + o) * blockDim.x + threadIdx.x;
+        oi[o] = -1;
+        oj[o] = 0;
+        if (id < T) {
+            int i = 0, rem = id;
+            while (rem >= R - i) {
+                rem -= R - i;
+                ++i;
+            }
+            oi[o] = i;
+            oj[o] = i + rem;
+        } else if (id < nout) {
+            oi[o] = (id - T) / nrhs;
+            oj[o] = -1 - (id - T) % nrhs;  // negative: a column of Z
+        }
+    }
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r1 = min(J, r0 + rows_per_cta);
+    for (int64_t base = r0; base < r1; base += SOLVE_ROWS) {
+        const int nr = (int)min((int64_t)SOLVE_ROWS, r1 - base);
+        __syncthreads();
+        for (int e = threadIdx.x; e < SOLVE_ROWS * R; e += blockDim.x)
+            sA[e] = (e / R < nr) ? SA[(base + e / R) * R + e % R] : 0.f;
+        if (B)
+            for (int e = threadIdx.x; e < SOLVE_ROWS * nrhs; e += blockDim.x) {
+                const int r = e / nrhs;
+                sB[e] = (r < nr) ? w[base + r] * B[(base + r) * nrhs + e % nrhs] : 0.f;
+            }
+        __syncthreads();
+#pragma unroll
+        for (int o = 0; o < MAXO; ++o) {
+            if (oi[o] < 0) continue;
+            const int i = oi[o], j = oj[o];
+            float a = acc[o];
+            if (j >= 0) {
+                for (int r = 0; r < nr; ++r) a = fmaf(sA[r * R + i], sA[r * R + j], a);
+            } else {
+                const int c = -1 - j;
+                for (int r = 0; r < nr; ++r) a = fmaf(sA[r * R + i], sB[r * nrhs + c], a);
+            }
+            acc[o] = a;
+        }
+    }
+#pragma unroll
+    for (int o = 0; o < MAXO; ++o) {
+        const int id = (blockIdx.y * MAXO + o) * blockDim.x + threadIdx.x;
+        if (id < nout) part[(size_t)blockIdx.x * nout + id] = acc[o];
+    }
+}
+
+// One CTA.  mode 0: X = M⁻¹ Z (R x nrhs) written as FP32 to X;
+// mode 1: M⁻¹ (R x R) written as FP64 to Xd (sparse path).
+// Work matrices: shared memory when gbuf == nullptr, else gbuf (global).
+__global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ part, int nparts, int R, int nrhs,
+                                                    int mode, int flags, float* __restrict__ X,
+                                                    double* __restrict__ Xd, int* __restrict__ status,
+                                                    double* __restrict__ gbuf) {
+    extern __shared__ __align__(16) double smd[];
+    const int RR = R * R;
+    const int T = tri_size(R);
+    const int ncol = mode == 1 ? R : nrhs;
+    const int nout = T + R * nrhs;
+    double* red = smd;
+    double* cs = red + 64;
+    int* pr = (int*)(cs + 2 * (R / 2 + 1));
+    double* M = gbuf ? gbuf : (double*)(pr + 2 * (R / 2 + 1) + 2);  // R x R
+    double* Lm = M + RR;                                            // R x R
+    double* Z = Lm + RR;                                            // R x ncol
+    __shared__ int flag;
+    if (threadIdx.x == 0) flag = 0;
+    // FP64 reduction of the partials, fixed order
+    for (int id = threadIdx.x; id < T; id += blockDim.x) {
+        double a = 0.0;
+        for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id];
+        int i = 0, rem = id;
+        while (rem >= R - i) {
+            rem -= R - i;
+            ++i;
+        }
+        M[i * R + i + rem] = a;
+        M[(i + rem) * R + i] = a;
+    }
+    for (int id = threadIdx.x; id < R * ncol; id += blockDim.x) {
+        double a;
+        if (mode == 1) {
+            a = (id / ncol == id % ncol) ? 1.0 : 0.0;
+        } else {
+            a = 0.0;
+            for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + T + id];
+        }
+        Z[id] = a;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) Lm[e] = M[e];
+    __syncthreads();
+    for (int c = 0; c < R; ++c) {
+        if (threadIdx.x == 0) {
+            const double d = Lm[c * R + c];
+            if (!(d > 0.0)) flag = 1;
+            Lm[c * R + c] = d > 0.0 ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        const double dc = Lm[c * R + c];
+        for (int i = c + 1 + threadIdx.x; i < R; i += blockDim.x) Lm[i * R + c] /= dc;
+        __syncthreads();
+        const int n = R - c - 1;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = c + 1 + e / n, j = c + 1 + e % n;
+            if (j <= i) Lm[i * R + j] -= Lm[i * R + c] * Lm[j * R + c];
+        }
+        __syncthreads();
+    }
+    if (!flag) {
+        // forward then backward substitution, one thread per right-hand side
+        for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+            for (int i = 0; i < R; ++i) {
+                double a = Z[i * ncol + col];
+                for (int k = 0; k < i; ++k) a -= Lm[i * R + k] * Z[k * ncol + col];
+                Z[i * ncol + col] = a / Lm[i * R + i];
+            }
+            for (int i = R - 1; i >= 0; --i) {
+                double a = Z[i * ncol + col];
+                for (int k = i + 1; k < R; ++k) a -= Lm[k * R + i] * Z[k * ncol + col];
+                Z[i * ncol + col] = a / Lm[i * R + i];
+            }
+        }
+        __syncthreads();
+    } else if (flags & KRP_PINV_FALLBACK) {
+        // M⁺ Z by the FP64 eigendecomposition of M (Lm becomes eigenvectors)
+        __syncthreads();
+        double* A = M;  // overwritten by Jacobi; diagonal = eigenvalues
+        jacobi_eig<double>(A, Lm, R, cs, pr, red, 30, 1e-14);
+        __shared__ double lam_max;
+        if (threadIdx.x == 0) {
+            double mx = 0.0;
+            for (int i = 0; i < R; ++i) mx = fmax(mx, A[i * R + i]);
+            lam_max = mx;
+        }
+        __syncthreads();
+        const double cut = R * 2.220446049250313e-16 * lam_max;
+        // Y = Vᵀ Z scaled by 1/λ, then X = V Y; one thread per column
+        for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+            double y[128];
+            for (int u = 0; u < R; ++u) {
+                double a = 0.0;
+                const double l = A[u * R + u];
+                if (l > cut)
+                    for (int i = 0; i < R; ++i) a += Lm[i * R + u] * Z[i * ncol + col];
+                y[u] = l > cut ? a / l : 0.0;
+            }
+            for (int i = 0; i < R; ++i) {
+                double a = 0.0;
+                for (int u = 0; u < R; ++u) a += Lm[i * R + u] * y[u];
+                Z[i * ncol + col] = a;
+            }
+        }
+        __syncthreads();
+    } else {
+        for (int e = threadIdx.x; e < R * ncol; e += blockDim.x) Z[e] = 0.0;
+        if (threadIdx.x == 0) set_status(status, KRP_ESINGULAR);
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < R * ncol; e += blockDim.x) {
+        if (mode == 1)
+            Xd[e] = Z[e];
+        else
+            X[e] = (float)Z[e];
+    }
+}
+
+namespace {
+krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float* weight, const float* B,
+                         int nrhs, int mode, int flags, float* X) {
+    const int R = s->R;
+    const int T = tri_size(R);
+    const int nout = T + R * nrhs;
+    int nparts = (int)std::min<int64_t>((J + 255) / 256, (int64_t)s->num_sms * 2);
+    nparts = nparts < 1 ? 1 : nparts;
+    const int64_t rows_per_cta = (J + nparts - 1) / nparts;
+    const int ncol = mode == 1 ? R : nrhs;
+    const size_t need = (size_t)nparts * nout;
+    const size_t need64 = (size_t)2 * R * R + (size_t)R * ncol + (size_t)R * R;
+    if (need > s->solve_scratch_floats) {
+        if (s->solve_scratch) cudaFree(s->solve_scratch);
+        s->solve_scratch = nullptr;
+        s->solve_scratch_floats = 0;
+        if (cudaMalloc(&s->solve_scratch, need * sizeof(float)) != cudaSuccess)
+            return fail(s, KRP_ENOMEM, "solve scratch allocation failed");
+        s->solve_scratch_floats = need;
+    }
+    const size_t smem1 = (size_t)SOLVE_ROWS * (R + nrhs) * 4;
+    const dim3 grid1(nparts, (nout + 256 * 8 - 1) / (256 * 8));
+    normal_partial<<<grid1, 256, smem1, s->stream>>>(SA, weight, B, J, R, nrhs, rows_per_cta, s->solve_scratch); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "normal_partial launch");
+    const size_t small = 64 * 8 + 2 * (R / 2 + 1) * 8 + 2 * (R / 2 + 1) * 4 + 16;
+    const size_t mats = (size_t)(2 * R * R + R * ncol) * 8;
+    const bool in_smem = small + mats <= 160 * 1024;
+    const size_t smem2 = small + (in_smem ? mats : 0);
+    if (smem2 > 48 * 1024)
+        cudaFuncSetAttribute(normal_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    normal_solve<<<1, 256, smem2, s->stream>>>(s->solve_scratch, nparts, R, nrhs, mode, flags, X,
+                                              s->solve64 + (size_t)(2 * R * R + R * 128), s->status,
+                                              in_smem ? nullptr : s->solve64); count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "normal_solve launch");
+    (void)need64;
+    return KRP_OK;
+}
+}  // namespace
+
+krp_status dense_solve(krp_sampler* s, int64_t J, const float* SA, const float* weight, const float* B_rows,
+                       int nrhs, float* X, int flags) {
+    return normal_common(s, J, SA, weight, B_rows, nrhs, 0, flags, X);
+}
+
+krp_status normal_inverse(krp_sampler* s, int64_t J, const float* SA, int flags) {
+    return normal_common(s, J, SA, nullptr, nullptr, 0, 1, flags, nullptr);
+}
+
+}  // namespace krp

@@ -1,0 +1,423 @@
+// a7 + a8 (sparse) + a9: sampled-fiber lookup, scatter SpMM, Y M⁻¹, column
+// normalisation, and the STS-CP sweep (Sec. 3.3; Alg. 6; App. A.9; fit of
+// Sec. 4.3).
+//
+// Mode-j index (built once, host sort as in the paper's preprocessing): every
+// nonzero gets the key packing its coordinates in the modes k != j (ascending
+// k, ceil(log2 I_k) bits each); nonzeros are sorted by key, equal keys form a
+// mode-j fiber (one row of mat(T, j)ᵀ restricted to its nonzeros).
+// Lookup: a warp per sampled tuple binary-searches its key among the fiber
+// keys, then scatters every nonzero (i_j, v) of the fiber into
+// Y[i_j, :] += w_s v SA[s, :]  (Y = SBᵀ SA, I_j x R).
+// Then U_j = Y M⁻¹ with M = SAᵀ SA (FP64 Cholesky inverse, applied in FP32).
+#include "common.cuh"
+#include "internal.h"
+
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+namespace krp {
+
+struct LookupParams {
+    const uint64_t* fkeys;
+    const int64_t* fptr;
+    const int32_t* fidx;
+    const float* fval;
+    int64_t nfib;
+    int other[16];
+    int kbits[16];
+    int n_other;
+    const int32_t* idx;  // N x J
+    const float* weight;
+    const float* SA;     // J x R
+    int64_t J;
+    int R;
+    float* Y;            // I_j x R
+};
+
+__global__ void __launch_bounds__(256) fiber_scatter(LookupParams P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.J; s += warps) {
+        uint64_t key = 0;
+        for (int q = 0; q < P.n_other; ++q)
+            key = (key << P.kbits[q]) | (uint64_t)(uint32_t)P.idx[(int64_t)P.other[q] * P.J + s];
+        // lower_bound over the sorted fiber keys (every lane computes the same)
+        int64_t lo = 0, hi = P.nfib;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (__ldg(P.fkeys + mid) < key)
+                lo = mid + 1;
+            else
+                hi = mid;
+        }
+        if (lo >= P.nfib || __ldg(P.fkeys + lo) != key) continue;  // empty fiber: SB row is zero
+        const int64_t b = __ldg(P.fptr + lo), e = __ldg(P.fptr + lo + 1);
+        const float ws = P.weight[s];
+        for (int64_t n = b; n < e; ++n) {
+            const int64_t ij = __ldg(P.fidx + n);
+            const float v = ws * __ldg(P.fval + n);
+            for (int a = lane; a < P.R; a += 32) atomicAdd(P.Y + ij * P.R + a, v * P.SA[s * P.R + a]);
+        }
+    }
+}
+
+// U[i, :] = Y[i, :] M⁻¹  (M⁻¹ FP64 -> FP32 in shared memory).
+__global__ void __launch_bounds__(256) apply_minv(const float* __restrict__ Y, const double* __restrict__ Minv,
+                                                  int64_t I, int R, float* __restrict__ U) {
+    extern __shared__ __align__(16) float sm[];
+    float* sM = sm;            // R x R
+    float* sY = sM + R * R;    // 32 x R
+    for (int e = threadIdx.x; e < R * R; e += blockDim.x) sM[e] = (float)Minv[e];
+    for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < I; r0 += (int64_t)gridDim.x * 32) {
+        const int nr = (int)min((int64_t)32, I - r0);
+        __syncthreads();
+        for (int e = threadIdx.x; e < 32 * R; e += blockDim.x) sY[e] = (e / R < nr) ? Y[r0 * R + e] : 0.f;
+        __syncthreads();
+        for (int e = threadIdx.x; e < nr * R; e += blockDim.x) {
+            const int r = e / R, c = e % R;
+            float a = 0.f;
+            for (int k = 0; k < R; ++k) a = fmaf(sY[r * R + k], sM[k * R + c], a);
+            U[(r0 + r) * R + c] = a;
+        }
+    }
+}
+
+// σ²[c] += Σ_i U[i, c]² (FP64 atomics, one partial per CTA and column).
+__global__ void __launch_bounds__(256) col_sumsq(const float* __restrict__ U, int64_t I, int R,
+                                                 double* __restrict__ out) {
+    __shared__ double part[256];
+    const int c = threadIdx.x % R;
+    const int lanes = (blockDim.x / R) * R;
+    double a = 0.0;
+    if ((int)threadIdx.x < lanes)
+        for (int64_t i = (int64_t)blockIdx.x * (blockDim.x / R) + threadIdx.x / R; i < I;
+             i += (int64_t)gridDim.x * (blockDim.x / R)) {
+            const double v = U[i * R + c];
+            a += v * v;
+        }
+    part[threadIdx.x] = (int)threadIdx.x < lanes ? a : 0.0;
+    __syncthreads();
+    if ((int)threadIdx.x < R) {
+        double t = 0.0;
+        for (int q = threadIdx.x; q < lanes; q += R) t += part[q];
+        atomicAdd(out + threadIdx.x, t);
+    }
+}
+
+__global__ void col_scale(float* __restrict__ U, int64_t I, int R, const double* __restrict__ sumsq,
+                          float* __restrict__ sigma) {
+    const int64_t n = I * R;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const double sg = sqrt(sumsq[e % R]);
+        U[e] = sg > 0.0 ? (float)((double)U[e] / sg) : U[e];
+    }
+    if (blockIdx.x == 0)
+        for (int c = threadIdx.x; c < R; c += blockDim.x) sigma[c] = (float)sqrt(sumsq[c]);
+}
+
+// ⟨T, T̃⟩ = Σ_nnz v Σ_r σ_r Π_k U_k[i_k, r]  (FP64 accumulation).
+struct FitParams {
+    const float* U[16];
+    const int32_t* coords;  // N x nnz
+    const float* vals;
+    const float* sigma;
+    int64_t nnz;
+    int N, R;
+    double* out;
+};
+
+__global__ void __launch_bounds__(256) fit_inner(FitParams P) {
+    __shared__ double red[8];
+    double a = 0.0;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < P.nnz; e += (int64_t)gridDim.x * blockDim.x) {
+        float m = 0.f;
+        for (int r = 0; r < P.R; ++r) {
+            float p = P.sigma[r];
+            for (int k = 0; k < P.N; ++k) p *= __ldg(P.U[k] + (int64_t)P.coords[(int64_t)k * P.nnz + e] * P.R + r);
+            m += p;
+        }
+        a += (double)P.vals[e] * (double)m;
+    }
+    a = warp_sum_d(a);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        atomicAdd(P.out, t);
+    }
+}
+
+}  // namespace krp
+
+using namespace krp;
+
+namespace {
+
+// Stable LSD radix sort of (key, perm) by key, 16-bit digits over `bits` bits.
+void radix_sort(std::vector<uint64_t>& key, std::vector<uint32_t>& perm, int bits) {
+    const size_t n = key.size();
+    std::vector<uint64_t> k2(n);
+    std::vector<uint32_t> p2(n);
+    std::vector<size_t> cnt(65537);
+    for (int shift = 0; shift < bits; shift += 16) {
+        std::fill(cnt.begin(), cnt.end(), 0);
+        for (size_t i = 0; i < n; ++i) ++cnt[((key[i] >> shift) & 0xffff) + 1];
+        for (int d = 0; d < 65536; ++d) cnt[d + 1] += cnt[d];
+        for (size_t i = 0; i < n; ++i) {
+            const size_t dst = cnt[(key[i] >> shift) & 0xffff]++;
+            k2[dst] = key[i];
+            p2[dst] = perm[i];
+        }
+        key.swap(k2);
+        perm.swap(p2);
+    }
+}
+
+int bits_for(int64_t I) {
+    int b = 1;
+    while (b < 62 && ((int64_t)1 << b) < I) ++b;
+    return b;
+}
+
+template <typename T>
+bool dmalloc(T** p, size_t n) {
+    return cudaMalloc((void**)p, std::max<size_t>(n, 1) * sizeof(T)) == cudaSuccess;
+}
+
+thread_local std::string g_tensor_error;
+
+}  // namespace
+
+extern "C" krp_status krp_sptensor_create(krp_sptensor** out, int N, const int64_t* I_host, int64_t nnz,
+                                          const int32_t* const* coords_host, const float* vals_host,
+                                          void* stream) {
+    if (!out) return KRP_EINVAL;
+    *out = nullptr;
+    if (N < 2 || N > 16 || !I_host || !coords_host || !vals_host || nnz < 1 || nnz >= ((int64_t)1 << 32))
+        return KRP_EINVAL;
+    for (int k = 0; k < N; ++k)
+        if (I_host[k] < 1 || I_host[k] >= ((int64_t)1 << 31) || !coords_host[k]) return KRP_EINVAL;
+    for (int j = 0; j < N; ++j) {
+        int b = 0;
+        for (int k = 0; k < N; ++k)
+            if (k != j) b += bits_for(I_host[k]);
+        if (b > 63) return KRP_EINVAL;
+    }
+    for (int k = 0; k < N; ++k)
+        for (int64_t e = 0; e < nnz; ++e)
+            if (coords_host[k][e] < 0 || coords_host[k][e] >= I_host[k]) return KRP_EINVAL;
+    krp_sptensor* t = new krp_sptensor();
+    t->N = N;
+    t->nnz = nnz;
+    t->stream = (cudaStream_t)stream;
+    t->I.assign(I_host, I_host + N);
+    t->kbits.resize(N);
+    for (int k = 0; k < N; ++k) t->kbits[k] = bits_for(I_host[k]);
+    double n2 = 0.0;
+    for (int64_t e = 0; e < nnz; ++e) n2 += (double)vals_host[e] * (double)vals_host[e];
+    t->normT2 = n2;
+    bool ok = dmalloc(&t->coords, (size_t)N * nnz) && dmalloc(&t->vals, (size_t)nnz);
+    for (int k = 0; ok && k < N; ++k)
+        ok = cudaMemcpy(t->coords + (size_t)k * nnz, coords_host[k], nnz * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    ok = ok && cudaMemcpy(t->vals, vals_host, nnz * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    t->fkeys.assign(N, nullptr);
+    t->fptr.assign(N, nullptr);
+    t->fidx.assign(N, nullptr);
+    t->fval.assign(N, nullptr);
+    t->nfib.assign(N, 0);
+    std::vector<uint64_t> key(nnz);
+    std::vector<uint32_t> perm(nnz);
+    for (int j = 0; ok && j < N; ++j) {
+        int bits = 0;
+        for (int64_t e = 0; e < nnz; ++e) {
+            uint64_t kk = 0;
+            for (int k = 0; k < N; ++k)
+                if (k != j) kk = (kk << t->kbits[k]) | (uint64_t)(uint32_t)coords_host[k][e];
+            key[e] = kk;
+            perm[e] = (uint32_t)e;
+        }
+        for (int k = 0; k < N; ++k)
+            if (k != j) bits += t->kbits[k];
+        radix_sort(key, perm, bits);
+        std::vector<uint64_t> fk;
+        std::vector<int64_t> fp;
+        std::vector<int32_t> fi(nnz);
+        std::vector<float> fv(nnz);
+        for (int64_t e = 0; e < nnz; ++e) {
+            if (e == 0 || key[e] != key[e - 1]) {
+                fk.push_back(key[e]);
+                fp.push_back(e);
+            }
+            fi[e] = coords_host[j][perm[e]];
+            fv[e] = vals_host[perm[e]];
+        }
+        fp.push_back(nnz);
+        t->nfib[j] = (int64_t)fk.size();
+        ok = dmalloc(&t->fkeys[j], fk.size()) && dmalloc(&t->fptr[j], fp.size()) && dmalloc(&t->fidx[j], (size_t)nnz) &&
+             dmalloc(&t->fval[j], (size_t)nnz);
+        ok = ok && cudaMemcpy(t->fkeys[j], fk.data(), fk.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(t->fptr[j], fp.data(), fp.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(t->fidx[j], fi.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+             cudaMemcpy(t->fval[j], fv.data(), (size_t)nnz * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+    }
+    if (!ok) {
+        krp_sptensor_destroy(t);
+        return KRP_ENOMEM;
+    }
+    *out = t;
+    return KRP_OK;
+}
+
+extern "C" void krp_sptensor_destroy(krp_sptensor* t) {
+    if (!t) return;
+    cudaStreamSynchronize(t->stream);
+    cudaFree(t->coords);
+    cudaFree(t->vals);
+    for (int j = 0; j < (int)t->fkeys.size(); ++j) {
+        cudaFree(t->fkeys[j]);
+        cudaFree(t->fptr[j]);
+        cudaFree(t->fidx[j]);
+        cudaFree(t->fval[j]);
+    }
+    cudaFree(t->Y);
+    delete t;
+}
+
+extern "C" krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* tc, int j, int64_t J,
+                                       const int32_t* idx, const float* weight, const float* SA, float* U_out,
+                                       int flags) {
+    if (!s || !tc || !idx || !weight || !SA || !U_out) return s ? fail(s, KRP_EINVAL, "null argument") : KRP_EINVAL;
+    krp_sptensor* t = const_cast<krp_sptensor*>(tc);
+    if (t->N != s->N || j < 0 || j >= s->N || J < 1 || J >= ((int64_t)1 << 31))
+        return fail(s, KRP_EINVAL, "krp_solve_sparse: bad mode, J or tensor order");
+    for (int k = 0; k < s->N; ++k)
+        if (t->I[k] != s->I[k]) return fail(s, KRP_EINVAL, "krp_solve_sparse: tensor dims differ from the factors");
+    const int R = s->R;
+    const size_t ny = (size_t)s->I[j] * R;
+    if (ny > t->Y_floats) {
+        cudaFree(t->Y);
+        t->Y = nullptr;
+        t->Y_floats = 0;
+        if (!dmalloc(&t->Y, ny)) return fail(s, KRP_ENOMEM, "sparse Y scratch allocation failed");
+        t->Y_floats = ny;
+    }
+    cudaError_t e = cudaMemsetAsync(t->Y, 0, ny * sizeof(float), s->stream);
+    if (e != cudaSuccess) return cuda_check(s, e, "Y memset");
+    LookupParams P{};
+    P.fkeys = t->fkeys[j];
+    P.fptr = t->fptr[j];
+    P.fidx = t->fidx[j];
+    P.fval = t->fval[j];
+    P.nfib = t->nfib[j];
+    for (int k = 0; k < s->N; ++k)
+        if (k != j) {
+            P.other[P.n_other] = k;
+            P.kbits[P.n_other] = t->kbits[k];
+            ++P.n_other;
+        }
+    P.idx = idx;
+    P.weight = weight;
+    P.SA = SA;
+    P.J = J;
+    P.R = R;
+    P.Y = t->Y;
+    const int64_t grid = std::min<int64_t>((J + 7) / 8, (int64_t)s->num_sms * 16);
+    fiber_scatter<<<(unsigned)grid, 256, 0, s->stream>>>(P); count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "fiber_scatter launch");
+    krp_status st = normal_inverse(s, J, SA, flags);
+    if (st != KRP_OK) return st;
+    const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
+    const size_t sm = (size_t)(R * R + 32 * R) * 4;
+    if (sm > 48 * 1024) cudaFuncSetAttribute(apply_minv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const int64_t g2 = std::min<int64_t>((s->I[j] + 31) / 32, (int64_t)s->num_sms * 4);
+    apply_minv<<<(unsigned)g2, 256, sm, s->stream>>>(t->Y, Minv, s->I[j], R, U_out); count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "apply_minv launch");
+    return KRP_OK;
+}
+
+namespace krp {
+krp_status als_buffers(krp_sampler* s, int64_t J, int32_t** idx, float** w, float** SA, double** sumsq);
+}
+
+extern "C" krp_status krp_cp_als_sweep(krp_sampler* s, const krp_sptensor* t, int64_t J, uint64_t seed,
+                                       uint64_t draw_base, float* sigma) {
+    if (!s || !t || !sigma) return s ? fail(s, KRP_EINVAL, "null argument") : KRP_EINVAL;
+    int32_t* idx;
+    float *w, *SA;
+    double* sumsq;
+    krp_status st = als_buffers(s, J, &idx, &w, &SA, &sumsq);
+    if (st != KRP_OK) return st;
+    const int R = s->R;
+    for (int j = 0; j < s->N; ++j) {
+        st = krp_sample(s, j, J, seed, draw_base + (uint64_t)j, idx, w, nullptr, SA);
+        if (st != KRP_OK) return st;
+        st = krp_solve_sparse(s, t, j, J, idx, w, SA, s->U[j], KRP_PINV_FALLBACK);
+        if (st != KRP_OK) return st;
+        cudaError_t e = cudaMemsetAsync(sumsq, 0, R * sizeof(double), s->stream);
+        if (e != cudaSuccess) return cuda_check(s, e, "sumsq memset");
+        const int64_t rows_per = 256 / R;
+        const int64_t g = std::min<int64_t>((s->I[j] + rows_per - 1) / rows_per, (int64_t)s->num_sms * 4);
+        col_sumsq<<<(unsigned)g, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq); count_launch();
+        const int64_t g2 = std::min<int64_t>((s->I[j] * R + 255) / 256, (int64_t)s->num_sms * 8);
+        col_scale<<<(unsigned)g2, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq, sigma); count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_check(s, e, "normalise launch");
+        st = build_tree(s, j, s->prec);
+        if (st != KRP_OK) return st;
+        s->has_factor[j] = 1;
+    }
+    return KRP_OK;
+}
+
+extern "C" krp_status krp_cp_fit(krp_sampler* s, const krp_sptensor* t, const float* sigma, double* fit_host) {
+    if (!s || !t || !sigma || !fit_host) return s ? fail(s, KRP_EINVAL, "null argument") : KRP_EINVAL;
+    if (t->N != s->N) return fail(s, KRP_EINVAL, "krp_cp_fit: tensor order differs");
+    const int R = s->R, N = s->N;
+    int32_t* idx;
+    float *w, *SA;
+    double* scratch;
+    krp_status st = als_buffers(s, 1, &idx, &w, &SA, &scratch);
+    if (st != KRP_OK) return st;
+    double* inner = scratch + R;
+    cudaMemsetAsync(inner, 0, sizeof(double), s->stream);
+    FitParams P{};
+    for (int k = 0; k < N; ++k) P.U[k] = s->U[k];
+    P.coords = t->coords;
+    P.vals = t->vals;
+    P.sigma = sigma;
+    P.nnz = t->nnz;
+    P.N = N;
+    P.R = R;
+    P.out = inner;
+    const int64_t g = std::min<int64_t>((t->nnz + 255) / 256, (int64_t)s->num_sms * 8);
+    fit_inner<<<(unsigned)g, 256, 0, s->stream>>>(P); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "fit launch");
+    std::vector<float> roots((size_t)N * s->Tp), sg(R);
+    double in_h = 0.0;
+    for (int k = 0; k < N; ++k)
+        cudaMemcpyAsync(roots.data() + (size_t)k * s->Tp, s->tree[k], s->Tp * 4, cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(sg.data(), sigma, R * 4, cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(&in_h, inner, 8, cudaMemcpyDeviceToHost, s->stream);
+    e = cudaStreamSynchronize(s->stream);
+    if (e != cudaSuccess) return cuda_check(s, e, "fit sync");
+    // ||T̃||² = σᵀ (⊛_k G_k) σ from the trees' roots
+    double m2 = 0.0;
+    for (int a = 0; a < R; ++a)
+        for (int b = 0; b < R; ++b) {
+            double g2 = (double)sg[a] * (double)sg[b];
+            for (int k = 0; k < N; ++k)
+                g2 *= (double)roots[(size_t)k * s->Tp + tri_index(std::min(a, b), std::max(a, b), R)];
+            m2 += g2;
+        }
+    const double r2 = std::max(t->normT2 - 2.0 * in_h + m2, 0.0);
+    *fit_host = 1.0 - sqrt(r2) / sqrt(t->normT2);
+    return KRP_OK;
+}

@@ -1,0 +1,233 @@
+"""Thin ctypes binding over libkrpls (include/krpls.h).
+
+Argument marshalling only: every step runs in the CUDA library.  Device
+buffers are passed as torch tensors (their data_ptr()) or raw integers;
+nothing here computes any part of the method.  If the library has not been
+built, lib() raises — there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libkrpls.so")
+
+KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EZERO, KRP_ESINGULAR, KRP_ENUMERIC, KRP_ETIMEOUT, KRP_ESTATE = (
+    0, -1, -2, -3, -4, -5, -6, -7, -8)
+KRP_PREC_FP32, KRP_PREC_BF16X3 = 0, 1
+KRP_PINV_FALLBACK = 1
+
+STATUS_NAMES = {0: "KRP_OK", -1: "KRP_EINVAL", -2: "KRP_ENOMEM", -3: "KRP_ECUDA", -4: "KRP_EZERO",
+                -5: "KRP_ESINGULAR", -6: "KRP_ENUMERIC", -7: "KRP_ETIMEOUT", -8: "KRP_ESTATE"}
+
+# (name, restype, argtypes) for every symbol declared in include/krpls.h
+_P = C.c_void_p
+_I64 = C.c_int64
+_U64 = C.c_uint64
+_INT = C.c_int
+SIGNATURES = [
+    ("krp_create", _INT, [C.POINTER(_P), _INT, C.POINTER(_I64), _INT, _INT, _INT, _P]),
+    ("krp_destroy", None, [_P]),
+    ("krp_set_factor", _INT, [_P, _INT, _P]),
+    ("krp_set_factor_prec", _INT, [_P, _INT, _P, _INT]),
+    ("krp_sample", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
+    ("krp_sample_prepare", _INT, [_P, _INT]),
+    ("krp_sample_draw", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
+    ("krp_launch_count", _I64, []),
+    ("krp_gather", _INT, [_P, _INT, _I64, _P, _P, _P]),
+    ("krp_solve_dense", _INT, [_P, _I64, _P, _P, _P, _INT, _P, _INT]),
+    ("krp_sptensor_create", _INT, [C.POINTER(_P), _INT, C.POINTER(_I64), _I64, C.POINTER(_P), _P, _P]),
+    ("krp_sptensor_destroy", None, [_P]),
+    ("krp_solve_sparse", _INT, [_P, _P, _INT, _I64, _P, _P, _P, _P, _INT]),
+    ("krp_cp_als_sweep", _INT, [_P, _P, _I64, _U64, _U64, _P]),
+    ("krp_cp_fit", _INT, [_P, _P, _P, C.POINTER(C.c_double)]),
+    ("krp_debug_trace", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _I64]),
+    ("krp_sync_status", _INT, [_P]),
+    ("krp_last_error", C.c_char_p, [_P]),
+    ("krp_tree_info", _INT, [_P, _INT, C.POINTER(_I64), C.POINTER(_INT), C.POINTER(_INT)]),
+    ("krp_get_tree", _INT, [_P, _INT, _P, _I64]),
+    ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
+]
+
+_lib = None
+
+
+def lib():
+    """Load libkrpls.so (built by paper_2301_12584_gb300.build); raise if absent."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libkrpls.so not built ({LIB_PATH}); run paper_2301_12584_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class KrpError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return x.data_ptr()
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
+class Sampler:
+    """Owns a krp_sampler.  Mirrors krp_* calls one to one."""
+
+    def __init__(self, I, R, F=0, precision=KRP_PREC_FP32, stream=None):
+        L = lib()
+        self._lib = L
+        self.N = len(I)
+        self.I = [int(x) for x in I]
+        self.R = int(R)
+        arr = (_I64 * self.N)(*self.I)
+        h = _P()
+        code = L.krp_create(C.byref(h), self.N, arr, self.R, int(F), int(precision), _P(_stream_ptr(stream)))
+        if code != KRP_OK:
+            raise KrpError(code, L.krp_last_error(None).decode())
+        self.h = h
+
+    def _check(self, code):
+        if code != KRP_OK:
+            raise KrpError(code, self._lib.krp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.krp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # --- calls -----------------------------------------------------------
+    def set_factor(self, j, U, precision=None):
+        """U: device tensor or pinned/pageable host pointer (int) or CPU tensor."""
+        if precision is None:
+            self._check(self._lib.krp_set_factor(self.h, int(j), _P(_ptr(U))))
+        else:
+            self._check(self._lib.krp_set_factor_prec(self.h, int(j), _P(_ptr(U)), int(precision)))
+
+    def sample(self, exclude_j, J, seed, draw_id, idx, weight, logq=None, SA=None):
+        self._check(self._lib.krp_sample(self.h, int(exclude_j), int(J), int(seed), int(draw_id),
+                                         _P(_ptr(idx)), _P(_ptr(weight)), _P(_ptr(logq)), _P(_ptr(SA))))
+
+    def sample_prepare(self, exclude_j):
+        self._check(self._lib.krp_sample_prepare(self.h, int(exclude_j)))
+
+    def sample_draw(self, exclude_j, J, seed, draw_id, idx, weight, logq=None, SA=None):
+        self._check(self._lib.krp_sample_draw(self.h, int(exclude_j), int(J), int(seed), int(draw_id),
+                                              _P(_ptr(idx)), _P(_ptr(weight)), _P(_ptr(logq)), _P(_ptr(SA))))
+
+    def debug_trace(self, exclude_j, J, seed, draw_id, idx, weight, trace, n_trace):
+        self._check(self._lib.krp_debug_trace(self.h, int(exclude_j), int(J), int(seed), int(draw_id),
+                                              _P(_ptr(idx)), _P(_ptr(weight)), _P(_ptr(trace)), int(n_trace)))
+
+    def gather(self, exclude_j, J, idx, weight, SA):
+        self._check(self._lib.krp_gather(self.h, int(exclude_j), int(J), _P(_ptr(idx)), _P(_ptr(weight)),
+                                         _P(_ptr(SA))))
+
+    def solve_dense(self, J, SA, weight, B_rows, nrhs, X, flags=0):
+        self._check(self._lib.krp_solve_dense(self.h, int(J), _P(_ptr(SA)), _P(_ptr(weight)), _P(_ptr(B_rows)),
+                                              int(nrhs), _P(_ptr(X)), int(flags)))
+
+    def solve_sparse(self, tensor, j, J, idx, weight, SA, U_out, flags=KRP_PINV_FALLBACK):
+        self._check(self._lib.krp_solve_sparse(self.h, tensor.h, int(j), int(J), _P(_ptr(idx)), _P(_ptr(weight)),
+                                               _P(_ptr(SA)), _P(_ptr(U_out)), int(flags)))
+
+    def cp_als_sweep(self, tensor, J, seed, draw_base, sigma):
+        self._check(self._lib.krp_cp_als_sweep(self.h, tensor.h, int(J), int(seed), int(draw_base),
+                                               _P(_ptr(sigma))))
+
+    def cp_fit(self, tensor, sigma):
+        out = C.c_double()
+        self._check(self._lib.krp_cp_fit(self.h, tensor.h, _P(_ptr(sigma)), C.byref(out)))
+        return out.value
+
+    def sync_status(self):
+        """Synchronise and return the device status code (0 = OK)."""
+        return int(self._lib.krp_sync_status(self.h))
+
+    def last_error(self):
+        return self._lib.krp_last_error(self.h).decode()
+
+    def tree_info(self, j):
+        L, d, st = _I64(), _INT(), _INT()
+        self._check(self._lib.krp_tree_info(self.h, int(j), C.byref(L), C.byref(d), C.byref(st)))
+        return L.value, d.value, st.value
+
+    def get_tree(self, j):
+        import numpy as np
+        L, _, st = self.tree_info(j)
+        out = np.zeros(L * st, dtype=np.float32)
+        self._check(self._lib.krp_get_tree(self.h, int(j), out.ctypes.data_as(_P), out.size))
+        return out.reshape(L, st)
+
+    def get_prep(self, k):
+        import numpy as np
+        R = self.R
+        lam = np.zeros(R)
+        V = np.zeros((R, R))
+        Gp = np.zeros((R, R))
+        rank = _INT()
+        self._check(self._lib.krp_get_prep(self.h, int(k), lam.ctypes.data_as(_P), V.ctypes.data_as(_P),
+                                           Gp.ctypes.data_as(_P), C.byref(rank)))
+        return lam, V, Gp, rank.value
+
+
+def launch_count():
+    """Kernels launched by libkrpls in this process so far."""
+    return int(lib().krp_launch_count())
+
+
+class SparseTensor:
+    """Owns a krp_sptensor built from host coordinates (N x nnz int32) and values."""
+
+    def __init__(self, dims, coords, vals, stream=None):
+        import numpy as np
+        L = lib()
+        self._lib = L
+        coords = [np.ascontiguousarray(c, dtype=np.int32) for c in coords]
+        vals = np.ascontiguousarray(vals, dtype=np.float32)
+        self._keep = (coords, vals)
+        N = len(dims)
+        arr = (_I64 * N)(*[int(d) for d in dims])
+        cptrs = (_P * N)(*[c.ctypes.data for c in coords])
+        h = _P()
+        code = L.krp_sptensor_create(C.byref(h), N, arr, int(vals.size), cptrs, _P(vals.ctypes.data),
+                                     _P(_stream_ptr(stream)))
+        if code != KRP_OK:
+            raise KrpError(code, "krp_sptensor_create failed")
+        self.h = h
+        self._keep = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.krp_sptensor_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,361 @@
+"""GPU path vs the FP64 CPU oracle, through the C ABI.
+
+Tolerances (derivations in the design notes):
+  * indices: bit-exact, except samples whose first differing factor has a
+    uniform within 1e-5 * C of a CDF boundary of the oracle's chosen bin;
+    fewer than 1e-4 * J such samples;
+  * branch probabilities m_L/m_c: 1e-5 relative when >= 1e-3, else 1e-8 absolute;
+  * trees: |GPU - FP64| <= 2e-5 * (|U|ᵀ|U| over the node's rows), elementwise;
+  * weights 1/sqrt(J q): 1e-4 relative; sketched solve: 1e-4 relative Frobenius.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import krp_oracle as O
+from oracle.philox import sampler_uniforms
+from paper_2301_12584_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import os
+    from paper_2301_12584_gb300 import build as B
+    from paper_2301_12584_gb300 import krpls
+    if not os.path.exists(krpls.LIB_PATH):
+        B.build()
+    krpls.lib()
+
+
+def sampler_for(Us, F=0, prec=0):
+    from paper_2301_12584_gb300.krpls import Sampler
+    s = Sampler([U.shape[0] for U in Us], Us[0].shape[1], F, prec)
+    for k, U in enumerate(Us):
+        s.set_factor(k, torch.from_numpy(np.ascontiguousarray(U, dtype=np.float32)).to(DEV))
+    return s
+
+
+def draw(s, Us, excl, J, seed, draw_id, SA=False, logq=False):
+    N, R = len(Us), Us[0].shape[1]
+    idx = torch.full((N, J), -1, dtype=torch.int32, device=DEV)
+    w = torch.zeros(J, dtype=torch.float32, device=DEV)
+    lq = torch.zeros(J, dtype=torch.float32, device=DEV) if logq else None
+    sa = torch.zeros((J, R), dtype=torch.float32, device=DEV) if SA else None
+    s.sample(excl, J, seed, draw_id, idx, w, lq, sa)
+    assert s.sync_status() == 0, s.last_error()
+    incl = O.included_factors(N, excl)
+    out = dict(idx=idx.cpu().numpy()[incl].astype(np.int64), weight=w.cpu().numpy())
+    if logq:
+        out["logq"] = lq.cpu().numpy()
+    if SA:
+        out["SA"] = sa.cpu().numpy()
+    return out
+
+
+def check_index_parity(gidx, ref, J, tol=1e-5):
+    """Bit parity except near-boundary uniforms; returns mismatch count."""
+    diff = gidx != ref["idx"]
+    bad = np.nonzero(diff.any(axis=0))[0]
+    for s in bad:
+        p = int(np.argmax(diff[:, s]))       # first factor whose index differs
+        near = False
+        for st in (0, 1):
+            tau, lft, rgt, tot = (ref[k][p, st, s] for k in ("tau", "left", "right", "total"))
+            if min(abs(tau - lft), abs(rgt - tau)) <= tol * tot:
+                near = True
+        assert near, f"sample {s}: factor {p} differs away from any CDF boundary"
+    return len(bad)
+
+
+# ----------------------------------------------------------------- trees ----
+def unpack(slot, R):
+    G = np.zeros((R, R))
+    p = 0
+    for i in range(R):
+        for j in range(i, R):
+            G[i, j] = G[j, i] = slot[p]
+            p += 1
+    return G
+
+
+@pytest.mark.parametrize("I,R,F", [(64, 8, 8), (1000, 8, 8), (37, 5, 3), (5, 8, 8), (20000, 32, 32),
+                                   (3001, 25, 25), (700, 64, 64), (300, 128, 128), (100, 3, 1), (4096, 16, 16)])
+def test_tree_matches_partial_grams(I, R, F):
+    rng = np.random.default_rng(I * 7 + R)
+    U = rng.standard_normal((I, R)).astype(np.float32)
+    s = sampler_for([U], F)
+    L, d, Tp = s.tree_info(0)
+    assert L == 2 ** d and L >= -(-I // F) and L < 2 * max(1, -(-I // F))
+    tree = s.get_tree(0)
+    U64 = U.astype(np.float64)
+    T = R * (R + 1) // 2
+    for slot in range(L):
+        h = 1 if slot == 0 else 2 * slot
+        lo, hi = O.node_rows(h, L, F, I)
+        ref = U64[lo:hi].T @ U64[lo:hi]
+        bound = np.abs(U64[lo:hi]).T @ np.abs(U64[lo:hi])
+        got = unpack(tree[slot], R)
+        assert np.all(tree[slot][T:] == 0)
+        assert np.all(np.abs(got - ref) <= 2e-5 * bound + 1e-30), (slot, np.abs(got - ref).max())
+    s.close()
+
+
+# -------------------------------------------------- sampler index parity ----
+@pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1"])
+def test_sampler_index_parity(case):
+    J = 1 << 15
+    excl = -1
+    F = 0
+    if case == "cfg_tiny":      # 3 x (64 x 8), F = 8
+        Us, F = synth.gaussian_factors(3, 64, 8, seed=0), 8
+    elif case == "ragged":
+        Us, F = synth.gaussian_factors(3, [50, 77, 13], 6, seed=3), 4
+    elif case == "excl1":
+        Us, F, excl = synth.gaussian_factors(3, [40, 90, 33], 7, seed=4), 5, 1
+    elif case == "R5_F3":
+        Us, F = synth.skewed_entry_factors(3, 30, 5, seed=5), 3
+    elif case == "N4":
+        Us = synth.uniform_factors(4, 24, 6, seed=6)
+    elif case == "R1":
+        Us = synth.gaussian_factors(3, 20, 1, seed=7)
+    elif case == "N1":
+        Us, F = synth.gaussian_factors(1, 500, 8, seed=8), 8
+    elif case == "R32":
+        Us, F, J = synth.skewed_row_factors(3, 2000, 32, seed=9), 32, 1 << 13
+    elif case == "F1":
+        Us, F = synth.gaussian_factors(2, 40, 4, seed=10), 1
+    s = sampler_for(Us, F)
+    out = draw(s, Us, excl, J, seed=12345, draw_id=3, logq=True)
+    U64 = [U.astype(np.float64) for U in Us]
+    ref = O.krp_sample(U64, excl, J, 12345, 3, record=True)
+    mism = check_index_parity(out["idx"], ref, J)
+    assert mism < max(1.0, 1e-4 * J), f"{mism} boundary mismatches of {J}"
+    same = ~(out["idx"] != ref["idx"]).any(axis=0)
+    np.testing.assert_allclose(out["weight"][same], ref["weight"][same], rtol=1e-4)
+    np.testing.assert_allclose(out["logq"][same], ref["logq"][same], atol=1e-4)
+    s.close()
+    print(f"{case}: {mism} boundary mismatches / {J}")
+
+
+def test_draws_are_reproducible_and_distinct():
+    Us = synth.gaussian_factors(3, 64, 8, seed=0)
+    s = sampler_for(Us, 8)
+    a = draw(s, Us, -1, 4096, 7, 0)
+    b = draw(s, Us, -1, 4096, 7, 0)
+    c = draw(s, Us, -1, 4096, 7, 1)
+    d = draw(s, Us, -1, 4096, 8, 0)
+    assert np.array_equal(a["idx"], b["idx"]) and np.array_equal(a["weight"], b["weight"])
+    assert (a["idx"] != c["idx"]).any(axis=0).mean() > 0.5
+    assert (a["idx"] != d["idx"]).any(axis=0).mean() > 0.5
+    s.close()
+
+
+# -------------------------------------------------- branch probabilities ----
+def test_branch_probabilities_match_fp64_tree():
+    Us = synth.skewed_entry_factors(3, 200, 8, seed=11)
+    F = 8
+    s = sampler_for(Us, F)
+    N, R, J, n_tr = 3, 8, 512, 128
+    idx = torch.zeros((N, J), dtype=torch.int32, device=DEV)
+    w = torch.zeros(J, dtype=torch.float32, device=DEV)
+    tr = torch.zeros(n_tr * N * 2 * 66, dtype=torch.float32, device=DEV)
+    s.debug_trace(-1, J, 99, 5, idx, w, tr, n_tr)
+    assert s.sync_status() == 0
+    trace = tr.cpu().numpy().reshape(n_tr, N, 2, 66)
+    gi = idx.cpu().numpy().astype(np.int64)
+    U64 = [U.astype(np.float64) for U in Us]
+    ref = O.krp_sample(U64, -1, J, 99, 5)
+    prep = ref["prep"]
+    ue, ur = sampler_uniforms(99, 5, n_tr, N)
+    L, dZ = O.tree_shape(200, F)
+    checked = 0
+    for sm in range(n_tr):
+        if (gi[:, sm] != ref["idx"][:, sm]).any():
+            continue
+        h = np.ones(R)
+        for p in range(N):
+            u_k, tr_u = O.eig_tree_row_sample(prep.lam[p], prep.V[p], prep.grams[p], h, ue[sm, p])
+            ht = h * prep.V[p][:, u_k]
+            t_k, tr_t = O.tree_row_sample(U64[p], F, np.ones((R, R)), ht, ur[sm, p])
+            assert t_k == gi[p, sm]
+            for st, trc in ((0, tr_u), (1, tr_t)):
+                for lvl, (ml, mc) in enumerate(trc):
+                    g_ml, g_mc = trace[sm, p, st, 2 + 2 * lvl], trace[sm, p, st, 3 + 2 * lvl]
+                    pl, gpl = ml / mc, g_ml / g_mc
+                    if pl >= 1e-3:
+                        assert abs(gpl - pl) <= 1e-5 * pl, (sm, p, st, lvl, gpl, pl)
+                    else:
+                        assert abs(gpl - pl) <= 1e-8 + 1e-5 * pl, (sm, p, st, lvl, gpl, pl)
+                    checked += 1
+            h = h * U64[p][t_k]
+    assert checked > 1000
+    s.close()
+
+
+# ------------------------------------------------------------ statistics ----
+def test_distribution_tv_config0():
+    """10^6 samples on the 3 x (64 x 8) case vs the exact leverage distribution."""
+    Us = synth.gaussian_factors(3, 64, 8, seed=0)
+    U64 = [U.astype(np.float64) for U in Us]
+    lev, rank = O.krp_leverage(U64)
+    p = lev / rank
+    s = sampler_for(Us, 8)
+    J = 10 ** 6
+    out = draw(s, Us, -1, J, seed=1, draw_id=0)
+    lin = O.linear_index(out["idx"], (64, 64, 64))
+    cnt = np.bincount(lin, minlength=64 ** 3)
+    # (i) single-factor marginals: TV <= 0.01
+    P3 = p.reshape(64, 64, 64)
+    for a in range(3):
+        emp = np.bincount(out["idx"][a], minlength=64) / J
+        ex = P3.sum(axis=tuple(b for b in range(3) if b != a))
+        assert 0.5 * np.abs(emp - ex).sum() <= 0.01
+    # (ii) joint TV within the 99th percentile of exact multinomial draws
+    tv = 0.5 * np.abs(cnt / J - p).sum()
+    rng = np.random.default_rng(0)
+    tvs = [0.5 * np.abs(rng.multinomial(J, p) / J - p).sum() for _ in range(20)]
+    assert tv <= max(tvs) * 1.02, (tv, max(tvs))
+    # (iii) chi-square with pooled cells of expected count >= 5
+    e = J * p
+    order = np.argsort(e)
+    ce, cc = np.cumsum(e[order]), np.cumsum(cnt[order])
+    edges = [0]
+    acc = 0.0
+    for i in range(len(order)):
+        if ce[i] - acc >= 5:
+            edges.append(i + 1)
+            acc = ce[i]
+    edges[-1] = len(order)
+    ebin = np.diff(np.concatenate([[0], ce[np.array(edges[1:]) - 1]]))
+    cbin = np.diff(np.concatenate([[0], cc[np.array(edges[1:]) - 1]]))
+    chi2 = ((cbin - ebin) ** 2 / ebin).sum()
+    from scipy.stats import chi2 as C2
+    assert C2.sf(chi2, len(ebin) - 1) > 1e-3
+    s.close()
+
+
+# ---------------------------------------------------- gather and solves ----
+def test_gather_and_fused_sa_match_oracle():
+    Us = synth.gaussian_factors(3, [70, 64, 90], 16, seed=13)
+    s = sampler_for(Us, 16)
+    J = 5000
+    out = draw(s, Us, 2, J, seed=4, draw_id=1, SA=True)
+    U64 = [U.astype(np.float64) for U in Us]
+    ref = O.sketched_rows(U64, 2, out["idx"], out["weight"].astype(np.float64))
+    np.testing.assert_allclose(out["SA"], ref, rtol=2e-6, atol=1e-6 * np.abs(ref).max())
+    idx = torch.zeros((3, J), dtype=torch.int32, device=DEV)
+    idx[0] = torch.from_numpy(out["idx"][0].astype(np.int32))
+    idx[1] = torch.from_numpy(out["idx"][1].astype(np.int32))
+    w = torch.from_numpy(out["weight"]).to(DEV)
+    SA = torch.zeros((J, 16), device=DEV)
+    s.gather(2, J, idx, w, SA)
+    assert s.sync_status() == 0
+    np.testing.assert_allclose(SA.cpu().numpy(), ref, rtol=2e-6, atol=1e-6 * np.abs(ref).max())
+    s.close()
+
+
+@pytest.mark.parametrize("R,nrhs", [(8, 4), (32, 8), (13, 3)])
+def test_dense_solve_matches_oracle_lstsq(R, nrhs):
+    Us = synth.gaussian_factors(3, 48, R, seed=20 + R)
+    U64 = [U.astype(np.float64) for U in Us]
+    s = sampler_for(Us, 0)
+    J = 20000
+    out = draw(s, Us, -1, J, seed=5, draw_id=2, SA=True)
+    Xt = synth.planted_solution(R, nrhs, seed=3).astype(np.float64)
+    A_rows = O.sketched_rows(U64, -1, out["idx"], np.ones(J))
+    B = (A_rows @ Xt + 0.01 * synth.noise((J, nrhs), 4, 1.0).astype(np.float64)).astype(np.float32)
+    X = torch.zeros((R, nrhs), device=DEV)
+    s.solve_dense(J, torch.from_numpy(out["SA"]).to(DEV), torch.from_numpy(out["weight"]).to(DEV),
+                  torch.from_numpy(B).to(DEV), nrhs, X)
+    assert s.sync_status() == 0
+    SA64 = out["SA"].astype(np.float64)
+    SB = out["weight"].astype(np.float64)[:, None] * B.astype(np.float64)
+    Xo = O.lstsq(SA64, SB)
+    err = np.linalg.norm(X.cpu().numpy() - Xo) / np.linalg.norm(Xo)
+    assert err <= 1e-4, err
+    s.close()
+
+
+def test_dense_solve_singular_flags():
+    R = 6
+    Us = synth.gaussian_factors(3, 30, R, seed=31)
+    for U in Us:
+        U[:, 5] = U[:, 0]                 # rank-deficient KRP
+    s = sampler_for(Us, 0)
+    J = 4000
+    out = draw(s, Us, -1, J, seed=1, draw_id=0, SA=True)
+    B = np.random.default_rng(0).standard_normal((J, 2)).astype(np.float32)
+    SA, w, Bd = (torch.from_numpy(x).to(DEV) for x in (out["SA"], out["weight"], B))
+    X = torch.zeros((R, 2), device=DEV)
+    s.solve_dense(J, SA, w, Bd, 2, X, flags=0)
+    assert s.sync_status() == -5      # KRP_ESINGULAR
+    assert np.all(X.cpu().numpy() == 0)
+    s.solve_dense(J, SA, w, Bd, 2, X, flags=1)
+    assert s.sync_status() == 0
+    Xo = O.lstsq(out["SA"].astype(np.float64), out["weight"][:, None].astype(np.float64) * B)
+    np.testing.assert_allclose(out["SA"] @ X.cpu().numpy(), out["SA"] @ Xo, rtol=1e-3, atol=1e-4)
+    s.close()
+
+
+# ------------------------------------------------------- error handling ----
+def test_errors_are_reported_not_raised_on_device():
+    from paper_2301_12584_gb300.krpls import KrpError, Sampler
+    s = Sampler([10, 10], 4, 0)
+    s.set_factor(0, torch.randn(10, 4, device=DEV))
+    idx = torch.zeros((2, 8), dtype=torch.int32, device=DEV)
+    w = torch.zeros(8, device=DEV)
+    with pytest.raises(KrpError) as e:
+        s.sample(-1, 8, 1, 0, idx, w)          # factor 1 unset
+    assert e.value.code == -8
+    s.set_factor(1, torch.zeros(10, 4, device=DEV))   # A = 0
+    s.sample(-1, 8, 1, 0, idx, w)
+    assert s.sync_status() == -4               # KRP_EZERO
+    bad = torch.randn(10, 4, device=DEV)
+    bad[3, 1] = float("nan")
+    s.set_factor(1, bad)
+    s.sample(-1, 8, 1, 0, idx, w)
+    assert s.sync_status() in (-6, -4)         # NaN mass (or zero rank)
+    with pytest.raises(KrpError):
+        s.sample(5, 8, 1, 0, idx, w)
+    s.close()
+
+
+# ---------------------------------------------- full-size sampled check ----
+def test_full_size_sampler_sampled_outputs():
+    """N=3, I=2^22, R=32, F=32, J=2^16 (1% rows x100): the launch the benchmark
+    times, checked on sampled outputs the oracle computes one by one."""
+    I, R, J = 1 << 22, 32, 1 << 16
+    Us = synth.skewed_row_factors(3, I, R, seed=0)
+    s = sampler_for(Us, 32)
+    out = draw(s, Us, -1, J, seed=1, draw_id=0, SA=True)
+    U64 = [U.astype(np.float64) for U in Us]
+    # roots are the Grams
+    for k in range(3):
+        root = unpack(s.get_tree(k)[0], R)
+        G = U64[k].T @ U64[k]
+        assert np.abs(root - G).max() <= 2e-5 * (np.abs(U64[k]).T @ np.abs(U64[k])).max()
+    # sampled outputs, one by one (counter-based uniforms: sample d alone)
+    picks = np.random.default_rng(1).choice(J, 24, replace=False)
+    mism = 0
+    prep = O.SamplerPrep(U64, -1)
+    for d in picks:
+        ref = O.krp_sample(U64, -1, 1, 1, 0, d0=int(d), record=True, prep=prep)
+        got = out["idx"][:, d:d + 1]
+        if (got != ref["idx"]).any():
+            check_index_parity(got, ref, 1)
+            mism += 1
+            continue
+        assert abs(out["weight"][d] * np.sqrt(J) - ref["weight"][0]) <= 1e-4 * ref["weight"][0]
+    assert mism <= 1
+    # sketch property at full size: SAᵀSA ≈ AᵀA in the G⁻¹ᐟ² metric
+    G = O.hadamard_gram(U64)
+    lam, V = np.linalg.eigh(G)
+    Gi = V @ np.diag(lam ** -0.5) @ V.T
+    SA = out["SA"].astype(np.float64)
+    E = Gi @ (SA.T @ SA) @ Gi - np.eye(R)
+    assert np.linalg.norm(E, 2) < 0.25
+    s.close()
