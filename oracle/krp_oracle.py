@@ -212,7 +212,7 @@ class SamplerPrep:
 
 
 def krp_sample(Us, exclude, J, seed, draw_id, d0=0, eig_override=None,
-               chunk=65536, record=False, prep=None):
+               chunk=16384, record=False, prep=None):
     """Draw samples d0..d0+J-1 by Alg. 2 with Philox uniforms.
 
     Returns dict with idx (n_incl, J) int64, weight (J,), q (J,), logq (J,),
@@ -464,3 +464,104 @@ def cp_als_exact(coords, vals, dims, Us0, sweeps):
             Us[j], sigma = column_normalize(Uj)
         fits.append(cp_fit(coords, vals, sigma, Us))
     return sigma, Us, fits
+
+
+# ---------------------------------------------------------------------------
+# Batched FP64 replay of Alg. 3 (BuildSampler) + Alg. 4 (RowSample) for many
+# samples at once, for factors too tall for the linear inverse CDF.  In exact
+# arithmetic it returns the same indices as krp_sample (Sec. 3.1); the pin
+# test checks that on small cases.
+# ---------------------------------------------------------------------------
+class TreeFP64:
+    """All node Grams of T_{I,F} in FP64, heap-numbered (root 1, children 2v, 2v+1;
+    leaf b = node L + b), built bottom-up by Alg. 3 (leaf Grams, then parent =
+    left + right).  Empty padding leaves hold zero."""
+
+    def __init__(self, U, F):
+        U = np.asarray(U, dtype=np.float64)
+        self.I, self.R = U.shape
+        self.F = F
+        self.L, self.d = tree_shape(self.I, F)
+        nleaf_rows = self.L * F
+        Up = np.zeros((nleaf_rows, self.R))
+        Up[: self.I] = U
+        blocks = Up.reshape(self.L, F, self.R)
+        nodes = np.zeros((2 * self.L, self.R, self.R))
+        nodes[self.L:] = np.matmul(np.transpose(blocks, (0, 2, 1)), blocks)      # leaf Grams
+        for v in range(self.L - 1, 0, -1):
+            nodes[v] = nodes[2 * v] + nodes[2 * v + 1]
+        self.nodes = nodes
+        self.U = U
+
+    def masses(self, v, Y_h):
+        """m(v) = ⟨hhᵀ, G^v, Y⟩ for node ids v (J,) and matrices Y_h = hhᵀ ∘ Y (J,R,R)."""
+        return np.einsum("sab,sab->s", self.nodes[v], Y_h)
+
+
+def tree_sample_batch(tree, Y, H, u):
+    """Alg. 4 for J history vectors H (J,R) and uniforms u (J,), Y p.s.d.
+    Returns (rows, tau, left_edges, right_edges, C) — edges of the chosen bin."""
+    J = H.shape[0]
+    M = H[:, :, None] * H[:, None, :] * Y[None, :, :]
+    C = tree.masses(np.ones(J, dtype=np.int64), M)
+    tau = u * C
+    c = np.ones(J, dtype=np.int64)
+    low = np.zeros(J)
+    L, d, F, I = tree.L, tree.d, tree.F, tree.I
+    for lvl in range(d):
+        mL = tree.masses(2 * c, M)
+        cutoff = low + mL
+        span = 1 << (d - lvl - 1)
+        right_first_row = ((2 * c + 1) * span - L) * F
+        go_left = (tau <= cutoff) | (right_first_row >= I)
+        low = np.where(go_left, low, cutoff)
+        c = np.where(go_left, 2 * c, 2 * c + 1)
+    b = c - L
+    rows = np.zeros(J, dtype=np.int64)
+    left = np.zeros(J)
+    right = np.zeros(J)
+    for s in range(J):
+        lo, hi = b[s] * F, min(b[s] * F + F, I)
+        Ub = tree.U[lo:hi]
+        q = np.einsum("sa,ab,sb->s", Ub, M[s], Ub)
+        cum = low[s] + np.cumsum(q)
+        hit = np.nonzero(cum >= tau[s])[0]
+        t = hit[0] if hit.size else np.nonzero(q > 0)[0][-1]
+        rows[s] = lo + t
+        right[s] = cum[t]
+        left[s] = cum[t] - q[t]
+    return rows, tau, left, right, C
+
+
+def krp_sample_tree(Us, exclude, J, seed, draw_id, F, d0=0, prep=None, trees=None):
+    """Alg. 2 with every stage drawn through Alg. 4 on FP64 segment trees
+    (E_k with F = 1 and Y = G_k; Z_k with leaf size F and Y = [1]).
+    Returns the same dict fields as krp_sample(record=True)."""
+    if prep is None:
+        prep = SamplerPrep(Us, exclude)
+    incl = prep.incl
+    R = prep.R
+    if trees is None:
+        trees = {k: TreeFP64(prep.Us[k], F) for k in incl}
+    u_eig, u_row = sampler_uniforms(seed, draw_id, J, len(incl), d0=d0)
+    H = np.ones((J, R))
+    out = {key: np.zeros((len(incl), 2, J)) for key in ("tau", "left", "right", "total")}
+    idx = np.zeros((len(incl), J), dtype=np.int64)
+    uidx = np.zeros((len(incl), J), dtype=np.int64)
+    for p, k in enumerate(incl):
+        Wk = np.sqrt(np.maximum(prep.lam[k], 0.0))[:, None] * prep.V[k].T
+        etree = TreeFP64(Wk, 1)
+        u_k, tau, lft, rgt, C = tree_sample_batch(etree, prep.grams[k], H, u_eig[:, p])
+        uidx[p] = u_k
+        for key, val in zip(("tau", "left", "right", "total"), (tau, lft, rgt, C)):
+            out[key][p, 0] = val
+        Ht = H * prep.V[k][:, u_k].T
+        t_k, tau, lft, rgt, C = tree_sample_batch(trees[k], np.ones((R, R)), Ht, u_row[:, p])
+        idx[p] = t_k
+        for key, val in zip(("tau", "left", "right", "total"), (tau, lft, rgt, C)):
+            out[key][p, 1] = val
+        H = H * prep.Us[k][t_k, :]
+    lev = np.einsum("sa,ab,sb->s", H, prep.Gplus, H)
+    q = lev / prep.rank
+    out.update(idx=idx, uidx=uidx, q=q, logq=np.log(q), weight=1.0 / np.sqrt(J * q), rank=prep.rank, prep=prep)
+    return out

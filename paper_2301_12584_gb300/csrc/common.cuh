@@ -71,4 +71,58 @@ __device__ __forceinline__ double warp_sum_d(double v) {
     return v;
 }
 
+// ---------------------------------------------------------------------------
+// Double-float arithmetic: a value is an unevaluated pair hi + lo of FP32
+// numbers with |lo| <= ulp(hi)/2 (about 48 significant bits).  Error-free
+// transformations: TwoSum (Knuth) and TwoProduct via FMA.
+// ---------------------------------------------------------------------------
+struct df {
+    float hi, lo;
+};
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+    float s, e;
+    two_sum(a.hi, b.hi, s, e);
+    e += a.lo + b.lo;
+    df r;
+    r.hi = s + e;
+    r.lo = e - (r.hi - s);
+    return r;
+}
+__device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+// (float) x (double-float)
+__device__ __forceinline__ df df_mul_f(df a, float b) {
+    const float p = a.hi * b;
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    df r;
+    r.hi = p + e;
+    r.lo = e - (r.hi - p);
+    return r;
+}
+// a <= b
+__device__ __forceinline__ bool df_le(df a, df b) {
+    const df d = df_add(a, df_neg(b));
+    return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
+}
+// Butterfly sum of a double-float over the warp; every lane gets the same pair
+// (TwoSum gives the same exact error for either operand order).
+__device__ __forceinline__ df warp_sum_df(df v) {
+#pragma unroll
+    for (int m = 16; m > 0; m >>= 1) {
+        const float oh = __shfl_xor_sync(0xffffffffu, v.hi, m);
+        const float ol = __shfl_xor_sync(0xffffffffu, v.lo, m);
+        float s, e;
+        two_sum(v.hi, oh, s, e);
+        e += v.lo + ol;
+        v.hi = s + e;
+        v.lo = e - (v.hi - s);
+    }
+    return v;
+}
+
 }  // namespace krp

@@ -343,6 +343,9 @@ cudaError_t launch_descent_t(const DescentParams& P, int num_sms, cudaStream_t s
 
 krp_status launch_descent(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
                           int32_t* idx, float* weight, float* logq, float* SA, float* trace, int64_t n_trace) {
+    cudaError_t fe = cudaSuccess;
+    if (launch_descent_fast(s, exclude_j, J, seed, draw_id, idx, weight, logq, SA, trace, n_trace, &fe))
+        return fe == cudaSuccess ? KRP_OK : cuda_check(s, fe, "descent launch");
     DescentParams P{};
     P.n_incl = 0;
     for (int k = 0; k < s->N; ++k) {

@@ -19,6 +19,7 @@ struct krp_sampler {
     std::vector<int> depth;     // log2 L
     std::vector<float*> U;      // factor copies, I_k x R
     std::vector<float*> tree;   // L_k slots x Tp
+    std::vector<double*> root64;  // FP64 root Gram G_k (packed upper, Tp) per factor
     std::vector<char> has_factor;
     // per-draw sampler state (written by the prep kernels)
     double* G64 = nullptr;      // N x R x R : FP64 copies of the root Grams
@@ -29,6 +30,7 @@ struct krp_sampler {
     float* Gplus32 = nullptr;   // Tp packed upper triangle of G⁺
     float* etree = nullptr;     // N x Rp x Tp : eigencomponent trees E_k
     float* V32 = nullptr;       // N x R x R : row u = eigenvector u of G_{>k}
+    float* V32lo = nullptr;     // N x R x R : FP32 residual V - V32 (double-float eigenvectors)
     int* rank_dev = nullptr;    // rank(A) of the last prep
     int* status = nullptr;      // device status word
     // scratch
@@ -82,6 +84,9 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j);
 krp_status launch_descent(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed,
                           uint64_t draw_id, int32_t* idx, float* weight, float* logq, float* SA,
                           float* trace = nullptr, int64_t n_trace = 0);
+// R <= 32 path of the descent (descent_fast.cu); false if R is out of range.
+bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
+                         float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
 // a6: gather
 krp_status launch_gather(krp_sampler* s, int exclude_j, int64_t J, const int32_t* idx,
                          const float* weight, float* SA);

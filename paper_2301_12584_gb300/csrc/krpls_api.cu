@@ -86,6 +86,7 @@ void krp_destroy(krp_sampler* s) {
     cudaStreamSynchronize(s->stream);
     for (float* p : s->U) cudaFree(p);
     for (float* p : s->tree) cudaFree(p);
+    for (double* p : s->root64) cudaFree(p);
     cudaFree(s->G64);
     cudaFree(s->Gplus64);
     cudaFree(s->lam64);
@@ -94,6 +95,7 @@ void krp_destroy(krp_sampler* s) {
     cudaFree(s->Gplus32);
     cudaFree(s->etree);
     cudaFree(s->V32);
+    cudaFree(s->V32lo);
     cudaFree(s->rank_dev);
     cudaFree(s->status);
     cudaFree(s->build_scratch);
@@ -142,20 +144,22 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     s->depth.resize(N);
     s->U.assign(N, nullptr);
     s->tree.assign(N, nullptr);
+    s->root64.assign(N, nullptr);
     s->has_factor.assign(N, 0);
     bool ok = true;
     for (int k = 0; k < N && ok; ++k) {
         const int64_t nleaf = (s->I[k] + F - 1) / F;
         s->L[k] = next_pow2(nleaf);
         s->depth[k] = log2i(s->L[k]);
-        ok = dalloc(&s->U[k], (size_t)s->I[k] * R) && dalloc(&s->tree[k], (size_t)s->L[k] * s->Tp);
+        ok = dalloc(&s->U[k], (size_t)s->I[k] * R) && dalloc(&s->tree[k], (size_t)s->L[k] * s->Tp) &&
+             dalloc(&s->root64[k], (size_t)s->Tp);
         if (ok) ok = cudaMemsetAsync(s->tree[k], 0, (size_t)s->L[k] * s->Tp * 4, s->stream) == cudaSuccess;
     }
     const size_t RR = (size_t)R * R;
     ok = ok && dalloc(&s->G64, N * RR) && dalloc(&s->Gplus64, RR) && dalloc(&s->lam64, (size_t)N * R) &&
          dalloc(&s->V64, N * RR) && dalloc(&s->work64, std::max<size_t>(3 * RR, 2 * N * RR) + 256) &&
          dalloc(&s->Gplus32, (size_t)s->Tp) && dalloc(&s->etree, (size_t)N * s->Rp * s->Tp) &&
-         dalloc(&s->V32, N * RR) && dalloc(&s->rank_dev, 1) && dalloc(&s->status, 1) &&
+         dalloc(&s->V32, N * RR) && dalloc(&s->V32lo, N * RR) && dalloc(&s->rank_dev, 1) && dalloc(&s->status, 1) &&
          dalloc(&s->solve64, 3 * RR + 128 * (size_t)R);
     if (ok) ok = cudaMemsetAsync(s->status, 0, sizeof(int), s->stream) == cudaSuccess;
     if (ok) ok = cudaMemsetAsync(s->etree, 0, (size_t)N * s->Rp * s->Tp * 4, s->stream) == cudaSuccess;

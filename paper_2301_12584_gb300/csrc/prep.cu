@@ -30,7 +30,7 @@ __device__ void ascending_positions(const double* lam, int n, int* pos) {
 }
 
 struct PrepParams {
-    const float* roots[16];  // slot 0 of each factor's tree = root Gram G_k
+    const double* roots[16];  // FP64 root Gram G_k of each factor (packed upper)
     int incl[16];            // included factors, ascending
     int n_incl;
 };
@@ -56,10 +56,10 @@ __global__ void __launch_bounds__(256) prep_pinv(PrepParams P, int N, int exclud
     // G_k in FP64 (full symmetric) for every factor; G = Hadamard of included
     for (int e = threadIdx.x; e < RR; e += blockDim.x) G[e] = 1.0;
     for (int k = 0; k < N; ++k) {
-        const float* rt = P.roots[k];
+        const double* rt = P.roots[k];
         for (int e = threadIdx.x; e < RR; e += blockDim.x) {
             const int i = e / R, j = e % R;
-            const double v = rt ? (double)rt[tri_index(min(i, j), max(i, j), R)] : 0.0;
+            const double v = rt ? rt[tri_index(min(i, j), max(i, j), R)] : 0.0;
             G64[(size_t)k * RR + e] = v;
             if (k != exclude) G[e] *= v;
         }
@@ -178,7 +178,7 @@ __global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int 
                                                 int dE, int Tp, const double* __restrict__ G64,
                                                 const double* __restrict__ Gplus64, double* __restrict__ lam64,
                                                 double* __restrict__ V64, float* __restrict__ V32,
-                                                float* __restrict__ etree) {
+                                                float* __restrict__ V32lo, float* __restrict__ etree) {
     extern __shared__ __align__(16) double sm[];
     const int RR = R * R;
     const int p = blockIdx.x;
@@ -207,7 +207,10 @@ __global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int 
         const int row = e / R, u = e % R;   // V[row][u], eigenvector u in column u
         const int o = pos[u];
         V64[(size_t)k * RR + row * R + o] = (double)V[e];
-        V32[(size_t)k * RR + o * R + row] = (float)V[e];   // row o = eigenvector
+        const double v = (double)V[e];
+        const float vh = (float)v;
+        V32[(size_t)k * RR + o * R + row] = vh;   // row o = eigenvector
+        V32lo[(size_t)k * RR + o * R + row] = (float)(v - (double)vh);
     }
     for (int u = threadIdx.x; u < R; u += blockDim.x) lam64[(size_t)k * R + pos[u]] = lam[u];
     __syncthreads();
@@ -254,7 +257,7 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j) {
     PrepParams P{};
     P.n_incl = 0;
     for (int k = 0; k < N; ++k) {
-        P.roots[k] = s->tree[k];  // slot 0 = root Gram
+        P.roots[k] = s->root64[k];
         if (k != exclude_j) P.incl[P.n_incl++] = k;
     }
     const size_t mats = (size_t)3 * R * R * 8;
@@ -276,12 +279,12 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j) {
         if (sm2 > 48 * 1024)
             cudaFuncSetAttribute(prep_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
         prep_eig<double><<<P.n_incl, 256, sm2, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64,
-                                                           s->lam64, s->V64, s->V32, s->etree); count_launch();
+                                                           s->lam64, s->V64, s->V32, s->V32lo, s->etree); count_launch();
     } else {
         if (sm2 > 48 * 1024)
             cudaFuncSetAttribute(prep_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
         prep_eig<float><<<P.n_incl, 256, sm2, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64,
-                                                          s->lam64, s->V64, s->V32, s->etree); count_launch();
+                                                          s->lam64, s->V64, s->V32, s->V32lo, s->etree); count_launch();
     }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_eig launch");

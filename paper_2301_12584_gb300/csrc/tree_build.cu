@@ -111,39 +111,59 @@ __device__ __forceinline__ void store_node(float* __restrict__ tree, int64_t h, 
     if (tree_stored(h)) tree[tree_slot(h) * Tp + e] = v;
 }
 
+// Double-float addition (Knuth TwoSum, then a fast renormalisation): the pair
+// (hi, lo) carries the sum to about 2^-44 relative, so that the sums above the
+// leaves add no rounding error of their own; hi is the FP32-rounded sum.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float s = ah + bh;
+    const float bb = s - ah;
+    const float err = (ah - (s - bb)) + (bh - bb);
+    const float t = err + al + bl;
+    h = s + t;
+    l = t - (h - s);
+}
+
 // Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
-// merge across the CTA's groups.  Stores every left child created.
+// merge across the CTA's groups, all in double-float.  Stores the FP32 value of
+// every left child created; the CTA's subtree root goes to top as (hi, lo).
 template <int LB>
 __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
                                              float* __restrict__ top, int64_t L, int64_t first_leaf,
                                              int g, int G, int Tp) {
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
-        float v[LB];
+        float vh[LB], vl[LB];
 #pragma unroll
-        for (int l = 0; l < LB; ++l) v[l] = sG[l * Tp + e];
+        for (int l = 0; l < LB; ++l) {
+            vh[l] = sG[l * Tp + e];
+            vl[l] = 0.f;
+        }
         int64_t h = L + first_leaf;
 #pragma unroll
-        for (int l = 0; l < LB; ++l) store_node(tree, h + l, Tp, e, v[l]);
+        for (int l = 0; l < LB; ++l) store_node(tree, h + l, Tp, e, vh[l]);
 #pragma unroll
         for (int n = LB; n > 1; n >>= 1) {
             h >>= 1;
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
-                v[l] = v[2 * l] + v[2 * l + 1];
-                store_node(tree, h + l, Tp, e, v[l]);
+                df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
+                store_node(tree, h + l, Tp, e, vh[l]);
             }
         }
-        float val = v[0];
+        float hi = vh[0], lo = vl[0];
         int idx = g, lvl = 0;
         while (idx & 1) {
-            val = stk[lvl * Tp + e] + val;
+            df_add(stk[(2 * lvl) * Tp + e], stk[(2 * lvl + 1) * Tp + e], hi, lo, hi, lo);
             h >>= 1;
             idx >>= 1;
             ++lvl;
-            store_node(tree, h, Tp, e, val);
+            store_node(tree, h, Tp, e, hi);
         }
-        stk[lvl * Tp + e] = val;
-        if (g == G - 1) top[(size_t)blockIdx.x * Tp + e] = val;
+        stk[(2 * lvl) * Tp + e] = hi;
+        stk[(2 * lvl + 1) * Tp + e] = lo;
+        if (g == G - 1) {
+            top[((size_t)blockIdx.x * 2) * Tp + e] = hi;
+            top[((size_t)blockIdx.x * 2 + 1) * Tp + e] = lo;
+        }
     }
 }
 
@@ -185,16 +205,21 @@ __global__ void __launch_bounds__(512) tree_leaves_fp32(const float* __restrict_
     }
 }
 
-// Levels above the leaf kernel: LBB nodes per CTA from `in` (a full tree level
-// with n_in nodes, heap ids n_in..2 n_in - 1) to one node per CTA in `out`.
-template <int LBB>
-__global__ void tree_up(const float* __restrict__ in, int64_t n_in, int Tp, float* __restrict__ tree,
-                        float* __restrict__ out) {
+// Levels above the leaf kernel, summed in FP64: LBB nodes per CTA from `in`
+// (a full tree level with n_in nodes, heap ids n_in..2 n_in - 1; either the
+// leaf kernel's (hi, lo) FP32 pairs or FP64 values) to one FP64 node per CTA
+// in `out`.  Stores the FP32 rounding of every left child created.
+template <int LBB, bool FROM_PAIRS>
+__global__ void tree_up(const float* __restrict__ in_pairs, const double* __restrict__ in64, int64_t n_in, int Tp,
+                        float* __restrict__ tree, double* __restrict__ out) {
     const int64_t first = (int64_t)blockIdx.x * LBB;
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
-        float v[LBB];
+        double v[LBB];
 #pragma unroll
-        for (int l = 0; l < LBB; ++l) v[l] = in[(first + l) * Tp + e];
+        for (int l = 0; l < LBB; ++l)
+            v[l] = FROM_PAIRS ? (double)in_pairs[((first + l) * 2) * Tp + e] +
+                                    (double)in_pairs[((first + l) * 2 + 1) * Tp + e]
+                              : in64[(first + l) * Tp + e];
         int64_t h = n_in + first;
 #pragma unroll
         for (int n = LBB; n > 1; n >>= 1) {
@@ -202,10 +227,54 @@ __global__ void tree_up(const float* __restrict__ in, int64_t n_in, int Tp, floa
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
                 v[l] = v[2 * l] + v[2 * l + 1];
-                store_node(tree, h + l, Tp, e, v[l]);
+                store_node(tree, h + l, Tp, e, (float)v[l]);
             }
         }
         out[(size_t)blockIdx.x * Tp + e] = v[0];
+    }
+}
+
+// Exact FP64 Gram UᵀU for small factors (products of FP32 values are exact in
+// FP64; sums in FP64): CTA (x, y) reduces row chunk x for packed entries
+// y*256 .. y*256+255, one entry per thread, into partial x.
+__global__ void __launch_bounds__(256) gram64_partial(const float* __restrict__ U, int64_t I, int R,
+                                                      int64_t rows_per_cta, double* __restrict__ part) {
+    extern __shared__ __align__(16) float sU[];  // 64 x R
+    const int T = tri_size(R);
+    const int Tp = tri_stride(R);
+    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r1 = min(I, r0 + rows_per_cta);
+    const int e = blockIdx.y * blockDim.x + threadIdx.x;
+    int ei = 0, ej = 0;
+    if (e < T) {
+        int rem = e;
+        while (rem >= R - ei) {
+            rem -= R - ei;
+            ++ei;
+        }
+        ej = ei + rem;
+    }
+    double acc = 0.0;
+    for (int64_t b = r0; b < r1; b += 64) {
+        const int nr = (int)min((int64_t)64, r1 - b);
+        __syncthreads();
+        for (int x = threadIdx.x; x < 64 * R; x += blockDim.x) sU[x] = (x / R < nr) ? U[b * R + x] : 0.f;
+        __syncthreads();
+        if (e < T)
+            for (int r = 0; r < nr; ++r) acc = fma((double)sU[r * R + ei], (double)sU[r * R + ej], acc);
+    }
+    if (e < Tp) part[(size_t)blockIdx.x * Tp + e] = e < T ? acc : 0.0;
+}
+
+// Sum the partials in a fixed order into the FP64 root; also refresh the
+// stored FP32 root (slot 0) with the rounding of the exact value.
+__global__ void gram64_finish(const double* __restrict__ part, int nparts, int Tp, double* __restrict__ root64,
+                              float* __restrict__ slot0) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Tp; e += gridDim.x * blockDim.x) {
+        double a = 0.0;
+        for (int p = 0; p < nparts; ++p) a += part[(size_t)p * Tp + e];
+        root64[e] = a;
+        slot0[e] = (float)a;
     }
 }
 
@@ -248,7 +317,7 @@ void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* 
     auto smem_of = [&](int g) {
         int lv = 0;
         while ((1 << lv) < g) ++lv;
-        return (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)LB * Tp * 4 + (size_t)(lv + 1) * Tp * 4;
+        return (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)LB * Tp * 4 + (size_t)2 * (lv + 1) * Tp * 4;
     };
     while (G < 8 && (int64_t)G * 2 <= groups && smem_of(G * 2) <= 160 * 1024) G *= 2;
     *LB_out = LB;
@@ -265,7 +334,14 @@ krp_status build_tree(krp_sampler* s, int j, int precision) {
     size_t smem;
     tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem);
     const int64_t ctas = L / ((int64_t)LB * G);
-    const size_t need = (size_t)(ctas + ctas / 2 + 2) * Tp;
+    const int T = tri_size(R);
+    const bool exact_root = (double)I * T <= (double)(1 << 22);
+    const int nparts = exact_root ? (int)std::min<int64_t>((I + 255) / 256, 512) : 0;
+    // scratch (floats): leaf-kernel roots as (hi, lo) pairs, then FP64 space for
+    // two ping-pong levels or the exact-root partials
+    const size_t pairs = (size_t)ctas * 2 * Tp;
+    const size_t f64 = std::max<size_t>((size_t)2 * (ctas / 2 + 2) * Tp, (size_t)nparts * Tp);
+    const size_t need = pairs + 2 * f64;
     if (need > s->build_scratch_floats) {
         if (s->build_scratch) cudaFree(s->build_scratch);
         s->build_scratch = nullptr;
@@ -275,7 +351,8 @@ krp_status build_tree(krp_sampler* s, int j, int precision) {
         s->build_scratch_floats = need;
     }
     float* top = s->build_scratch;
-    float* top2 = top + (size_t)ctas * Tp;
+    double* up0 = reinterpret_cast<double*>(s->build_scratch + pairs);  // pairs is even: 8-byte aligned
+    double* up1 = up0 + (size_t)(ctas / 2 + 2) * Tp;
     bool done = false;
     if (precision == KRP_PREC_BF16X3) done = launch_tree_leaves_tc(s, j, LB, G, ctas, top, smem);
     if (!done) {
@@ -289,21 +366,46 @@ krp_status build_tree(krp_sampler* s, int j, int precision) {
         }
         if (e != cudaSuccess) return cuda_check(s, e, "tree leaf kernel launch");
     }
+    // levels above the leaf kernel, in FP64, down to the FP64 root
     int64_t n = ctas;
     const int up_threads = std::min(512, std::max(64, ((Tp + 31) / 32) * 32));
-    while (n > 1) {
+    bool first = true;
+    const double* in64 = nullptr;
+    double* outs[2] = {up0, up1};
+    int which = 0;
+    do {
         const int64_t lbb = std::min<int64_t>(16, n);
         const unsigned grid = (unsigned)(n / lbb);
+        double* out = (n / lbb == 1) ? s->root64[j] : outs[which];
+#define KRP_UP(LBBV)                                                                                          \
+    if (first)                                                                                                \
+        tree_up<LBBV, true><<<grid, up_threads, 0, s->stream>>>(top, nullptr, n, Tp, s->tree[j], out);       \
+    else                                                                                                      \
+        tree_up<LBBV, false><<<grid, up_threads, 0, s->stream>>>(nullptr, in64, n, Tp, s->tree[j], out);
         switch (lbb) {
-            case 2: tree_up<2><<<grid, up_threads, 0, s->stream>>>(top, n, Tp, s->tree[j], top2); count_launch(); break;
-            case 4: tree_up<4><<<grid, up_threads, 0, s->stream>>>(top, n, Tp, s->tree[j], top2); count_launch(); break;
-            case 8: tree_up<8><<<grid, up_threads, 0, s->stream>>>(top, n, Tp, s->tree[j], top2); count_launch(); break;
-            default: tree_up<16><<<grid, up_threads, 0, s->stream>>>(top, n, Tp, s->tree[j], top2); count_launch(); break;
+            case 1: KRP_UP(1) break;
+            case 2: KRP_UP(2) break;
+            case 4: KRP_UP(4) break;
+            case 8: KRP_UP(8) break;
+            default: KRP_UP(16) break;
         }
+#undef KRP_UP
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(s, e, "tree up kernel launch");
-        std::swap(top, top2);
+        in64 = out;
+        which ^= 1;
+        first = false;
         n /= lbb;
+    } while (n > 1);
+    // small factors: exact FP64 root Gram (replaces the summed one)
+    if (exact_root) {
+        const int64_t rpc = (I + nparts - 1) / nparts;
+        const dim3 grid(nparts, (Tp + 255) / 256);
+        gram64_partial<<<grid, 256, 64 * R * 4, s->stream>>>(s->U[j], I, R, rpc, up0); count_launch();
+        gram64_finish<<<(Tp + 255) / 256, 256, 0, s->stream>>>(up0, nparts, Tp, s->root64[j], s->tree[j]); count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_check(s, e, "exact root Gram launch");
     }
     return KRP_OK;
 }

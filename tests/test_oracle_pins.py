@@ -425,3 +425,15 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
                         lambda H, lam, V, Gk: good_w(H, lam, V.T, Gk))
     P, _ = _enumerate_two_stage(Us)
     assert np.abs(P - lev / rank).max() > 1e-4
+
+
+@pytest.mark.parametrize("I,F,excl", [(37, 4, -1), (64, 8, 1), (50, 7, -1)])
+def test_batched_tree_replay_equals_inverse_cdf_sampler(I, F, excl):
+    """Alg. 3/4 replay gives the same tuples as the plain inverse-CDF replay."""
+    Us = synth.skewed_entry_factors(3, I, 5, seed=I)
+    U64 = [U.astype(np.float64) for U in Us]
+    a = O.krp_sample(U64, excl, 3000, seed=3, draw_id=2, record=True)
+    b = O.krp_sample_tree(U64, excl, 3000, seed=3, draw_id=2, F=F)
+    assert np.array_equal(a["idx"], b["idx"]) and np.array_equal(a["uidx"], b["uidx"])
+    np.testing.assert_allclose(b["total"], a["total"], rtol=1e-12)
+    np.testing.assert_allclose(b["tau"], a["tau"], rtol=1e-12)
