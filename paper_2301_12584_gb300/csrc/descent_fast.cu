@@ -59,17 +59,61 @@ struct FastCfg {
     static constexpr int NCH = (NC4 + 31) / 32;     // chunks per lane
     static constexpr int WARPS = 8;
     static constexpr int RPT = (4 * RMAX + 31) / 32;  // leaf rows per lane (F <= 4R)
+    // per-warp shared memory: 3 staged nodes (slots c, 2c, 2c+1; also the leaf
+    // rows), h (hi, lo), h̃, mbarrier
+    static constexpr int STAGE = 3 * TPMAX;
+    static constexpr int WARP_BYTES = ((STAGE + 3 * RMAX) * 4 + 16 + 127) & ~127;
+    static constexpr int SMEM = WARPS * WARP_BYTES + 2 * TPMAX;
 };
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* m) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(m)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+// Bounded wait for the mbarrier phase `parity`; false if it did not complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
+    for (int it = 0; it < (1 << 24); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(m)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b),
+                   uc = *reinterpret_cast<uint64_t*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
+    return *reinterpret_cast<float2*>(&d);
+}
+
 template <int RMAX>
-__global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
+__global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
     using C = FastCfg<RMAX>;
     constexpr int NCH = C::NCH;
-    __shared__ __align__(16) float4 s_w[C::WARPS][NCH * 32];
-    __shared__ __align__(16) float s_hh[C::WARPS][RMAX];   // h, high parts
-    __shared__ __align__(16) float s_hl[C::WARPS][RMAX];   // h, low parts
-    __shared__ __align__(16) float s_th[C::WARPS][RMAX];   // FP32 h̃ for the leaf scan
-    __shared__ uint8_t s_i[C::TPMAX], s_j[C::TPMAX];
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char* wbase = smem + warp * C::WARP_BYTES;
+    float* stage = reinterpret_cast<float*>(wbase);                 // 3 x Tp (or leaf rows)
+    float* hh = stage + C::STAGE;
+    float* hl = hh + RMAX;
+    float* th = hl + RMAX;
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(th + RMAX);
+    uint8_t* s_i = smem + C::WARPS * C::WARP_BYTES;
+    uint8_t* s_j = s_i + C::TPMAX;
 
     const int R = P.R, T = P.T, Tp = P.Tp;
     const int nc4 = Tp >> 2;
@@ -83,15 +127,34 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
         s_i[p] = (uint8_t)(p < T ? i : 0);
         s_j[p] = (uint8_t)(p < T ? i + rem : 0);
     }
+    if (lane == 0) {
+        mbar_init(mbar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
     __syncthreads();
+    uint32_t phase = 0;
+    bool alive = true;
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float4* sw = s_w[warp];
-    float* hh = s_hh[warp];
-    float* hl = s_hl[warp];
-    float* th = s_th[warp];
+    // Stage up to two contiguous global ranges into `stage` (bytes multiple of 16).
+    auto fetch = [&](const float* a, uint32_t abytes, const float* b, uint32_t bbytes) -> bool {
+        __syncwarp();
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(mbar, abytes + bbytes);
+            tma_load_1d(stage, a, abytes, mbar);
+            if (bbytes) tma_load_1d(stage + Tp, b, bbytes, mbar);
+        }
+        const bool ok = mbar_wait(mbar, phase);
+        phase ^= 1u;
+        if (!ok) {
+            if (lane == 0) set_status(P.status, KRP_ETIMEOUT);
+            alive = false;
+        }
+        return ok;
+    };
 
-    // weights of the packed entries for history vector x (FP32 values in smem)
+    float4 w4[NCH];
+    // weights of the packed entries for history vector x (smem, FP32)
     auto make_weights = [&](const float* x) {
 #pragma unroll
         for (int m = 0; m < NCH; ++m) {
@@ -108,97 +171,89 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
                 }
                 wv[q] = w;
             }
-            sw[c] = make_float4(wv[0], wv[1], wv[2], wv[3]);
+            w4[m] = make_float4(wv[0], wv[1], wv[2], wv[3]);
         }
-        __syncwarp();
     };
-    // masses of up to three nodes loaded together (each a double-float)
-    auto mass3 = [&](const float* __restrict__ a, const float* __restrict__ b, const float* __restrict__ d, int nn,
-                     df& ma, df& mb, df& md) {
-        float4 va[NCH], vb[NCH], vd[NCH];
+    // lane partial of the mass of the staged node at `node` (smem)
+    auto partial = [&](const float* node) -> float {
+        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 0; m < NCH; ++m) {
             const int c = lane + 32 * m;
-            const bool ok = c < nc4;
-            va[m] = ok ? __ldg(reinterpret_cast<const float4*>(a) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-            if (nn > 1) {
-                vb[m] = ok ? __ldg(reinterpret_cast<const float4*>(b) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
-                vd[m] = ok ? __ldg(reinterpret_cast<const float4*>(d) + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < nc4) {
+                const float4 v = reinterpret_cast<const float4*>(node)[c];
+                acc = ffma2(make_float2(w4[m].x, w4[m].y), make_float2(v.x, v.y), acc);
+                acc = ffma2(make_float2(w4[m].z, w4[m].w), make_float2(v.z, v.w), acc);
             }
         }
-        float sa = 0.f, sb = 0.f, sd = 0.f;
-#pragma unroll
-        for (int m = 0; m < NCH; ++m) {
-            const float4 w = sw[lane + 32 * m];
-            sa = fmaf(w.x, va[m].x, sa);
-            sa = fmaf(w.y, va[m].y, sa);
-            sa = fmaf(w.z, va[m].z, sa);
-            sa = fmaf(w.w, va[m].w, sa);
-            if (nn > 1) {
-                sb = fmaf(w.x, vb[m].x, sb);
-                sb = fmaf(w.y, vb[m].y, sb);
-                sb = fmaf(w.z, vb[m].z, sb);
-                sb = fmaf(w.w, vb[m].w, sb);
-                sd = fmaf(w.x, vd[m].x, sd);
-                sd = fmaf(w.y, vd[m].y, sd);
-                sd = fmaf(w.z, vd[m].z, sd);
-                sd = fmaf(w.w, vd[m].w, sd);
-            }
-        }
-        ma = warp_sum_df(df{sa, 0.f});
-        if (nn > 1) {
-            mb = warp_sum_df(df{sb, 0.f});
-            md = warp_sum_df(df{sd, 0.f});
-        }
+        return acc.x + acc.y;
     };
-
-    // One descent of Alg. 4 (row stage adds the leaf scan): returns the leaf
-    // heap index; low is the double-float left edge of that leaf.
-    auto descend = [&](const float* __restrict__ tr, int depth, int64_t Lk, int64_t nreal_rows, int F,
-                       df tau, df& low, float* trc, float croot) -> int64_t {
+    auto refine = [&](float part) -> df { return warp_sum_df(df{part, 0.f}); };
+    // Decision "tau <= low + m" (Alg. 4): FP32 mass when tau is more than
+    // `margin` away from the cutoff, else the double-float mass.
+    auto go_left = [&](df tau, df low, float m, float part, float margin, df& cut) -> bool {
+        cut = df_add(low, df{m, 0.f});
+        const df gap = df_add(tau, df_neg(cut));
+        if (fabsf(gap.hi) > margin) return gap.hi < 0.f;
+        cut = df_add(low, refine(part));
+        return df_le(tau, cut);
+    };
+    // root mass of a tree, double-float
+    auto root_mass = [&](const float* tr) -> df {
+        if (!fetch(tr, Tp * 4, nullptr, 0)) return df{0.f, 0.f};
+        return refine(partial(stage));
+    };
+    // One descent of Alg. 4; returns the leaf heap index, low = its left edge.
+    auto descend = [&](const float* __restrict__ tr, int depth, int64_t Lk, int64_t nreal_rows, int F, df tau,
+                       df& low, float* trc, float croot, float margin) -> int64_t {
         int64_t c = 1;
         int lvl = 0;
         float mnode = croot;
-        while (lvl < depth) {
+        while (lvl < depth && alive) {
             const bool two = lvl + 2 <= depth;
-            df mA, mB, mD;
-            mass3(tr + c * Tp, tr + 2 * c * Tp, tr + (2 * c + 1) * Tp, two ? 3 : 1, mA, mB, mD);
-            // level lvl at node c
+            if (!fetch(tr + c * Tp, Tp * 4, two ? tr + 2 * c * Tp : nullptr, two ? 2 * Tp * 4 : 0)) break;
+            float pA = partial(stage), pB = 0.f, pD = 0.f;
+            if (two) {
+                pB = partial(stage + Tp);
+                pD = partial(stage + 2 * Tp);
+            }
+            float mA = warp_sum(pA), mB = two ? warp_sum(pB) : 0.f, mD = two ? warp_sum(pD) : 0.f;
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
-                const df cut = df_add(low, mA);
+                df cut;
                 if (trc) {
-                    trc[2 + 2 * lvl] = mA.hi + mA.lo;
+                    trc[2 + 2 * lvl] = mA;
                     trc[3 + 2 * lvl] = mnode;
                 }
-                if (df_le(tau, cut) || rfirst * F >= nreal_rows) {
+                if (rfirst * F >= nreal_rows || go_left(tau, low, mA, pA, margin, cut)) {
                     c = 2 * c;
-                    mnode = mA.hi + mA.lo;
+                    mnode = mA;
                     mA = mB;
+                    pA = pB;
                 } else {
                     c = 2 * c + 1;
                     low = cut;
-                    mnode = mnode - (mA.hi + mA.lo);
+                    mnode = mnode - mA;
                     mA = mD;
+                    pA = pD;
                 }
                 ++lvl;
             }
             if (!two) break;
-            // level lvl at the chosen child, its left-child mass already loaded
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
-                const df cut = df_add(low, mA);
+                df cut;
                 if (trc) {
-                    trc[2 + 2 * lvl] = mA.hi + mA.lo;
+                    trc[2 + 2 * lvl] = mA;
                     trc[3 + 2 * lvl] = mnode;
                 }
-                if (df_le(tau, cut) || rfirst * F >= nreal_rows) {
+                if (rfirst * F >= nreal_rows || go_left(tau, low, mA, pA, margin, cut)) {
                     c = 2 * c;
-                    mnode = mA.hi + mA.lo;
+                    mnode = mA;
                 } else {
                     c = 2 * c + 1;
                     low = cut;
-                    mnode = mnode - (mA.hi + mA.lo);
+                    mnode = mnode - mA;
                 }
                 ++lvl;
             }
@@ -206,8 +261,9 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
         return c;
     };
 
+    const bool leaf_tma = (R & 3) == 0 && P.F * R <= C::STAGE;
     const int64_t warps_total = (int64_t)gridDim.x * C::WARPS;
-    for (int64_t s = (int64_t)blockIdx.x * C::WARPS + warp; s < P.J; s += warps_total) {
+    for (int64_t s = (int64_t)blockIdx.x * C::WARPS + warp; s < P.J && alive; s += warps_total) {
         if (lane < RMAX) {
             hh[lane] = lane < R ? 1.f : 0.f;
             hl[lane] = 0.f;
@@ -227,9 +283,9 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
             __syncwarp();
             make_weights(th);
             const float* et = P.etree[k];
-            df Cm, dummy1, dummy2;
-            mass3(et, nullptr, nullptr, 1, Cm, dummy1, dummy2);
+            df Cm = root_mass(et);
             float cf = Cm.hi + Cm.lo;
+            if (!alive) break;
             if (!(cf > 0.f) || !isfinite(cf)) {
                 if (lane == 0) set_status(P.status, isfinite(cf) ? KRP_EZERO : KRP_ENUMERIC);
                 ok = false;
@@ -237,7 +293,8 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
             }
             if (trc) trc[0] = cf;
             df low{0.f, 0.f};
-            int64_t c = descend(et, P.dE, P.Rp, R, 1, df_mul_f(Cm, u_eig), low, trc, cf);
+            int64_t c = descend(et, P.dE, P.Rp, R, 1, df_mul_f(Cm, u_eig), low, trc, cf, 1e-6f * cf);
+            if (!alive) break;
             const int u = (int)(c - P.Rp);
             // ------------------------------------------------ row stage
             if (lane < RMAX) {
@@ -246,15 +303,15 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
                     vh = __ldg(P.Vhi[k] + (size_t)u * R + lane);
                     vl = __ldg(P.Vlo[k] + (size_t)u * R + lane);
                 }
-                // h̃ = h ∘ V[:,u] in double-float, rounded once to FP32
                 const df t = df_add(df_mul_f(df{hh[lane], hl[lane]}, vh), df_mul_f(df{hh[lane], hl[lane]}, vl));
-                th[lane] = t.hi + t.lo;
+                th[lane] = t.hi + t.lo;   // h̃ = h ∘ V[:,u], rounded once
             }
             __syncwarp();
             make_weights(th);
             const float* tr = P.tree[k];
-            mass3(tr, nullptr, nullptr, 1, Cm, dummy1, dummy2);
+            Cm = root_mass(tr);
             cf = Cm.hi + Cm.lo;
+            if (!alive) break;
             if (!(cf > 0.f) || !isfinite(cf)) {
                 if (lane == 0) set_status(P.status, isfinite(cf) ? KRP_EZERO : KRP_ENUMERIC);
                 ok = false;
@@ -268,57 +325,88 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
             low = df{0.f, 0.f};
             const int64_t Lk = P.L[k], Ik = P.I[k];
             const int F = P.F;
-            c = descend(tr, P.depth[k], Lk, Ik, F, tau, low, trc, cf);
+            const float margin = 1e-6f * cf;
+            c = descend(tr, P.depth[k], Lk, Ik, F, tau, low, trc, cf, margin);
+            if (!alive) break;
             // ------------------------------------------------ leaf scan
             const int64_t row0 = (c - Lk) * F;
             const int nrows = (int)min((int64_t)F, Ik - row0);
             const int rpt = (F + 31) >> 5;
             const float* Uk = P.U[k];
+            if (leaf_tma && !fetch(Uk + row0 * R, (uint32_t)(nrows * R * 4), nullptr, 0)) break;
             float q[C::RPT];
-            df run{0.f, 0.f};
+            float run = 0.f;
 #pragma unroll
             for (int r = 0; r < C::RPT; ++r) {
                 const int t = lane * rpt + r;
                 float d = 0.f;
                 if (r < rpt && t < nrows) {
-                    const float* row = Uk + (row0 + t) * R;
-                    if ((R & 3) == 0) {
-#pragma unroll 8
-                        for (int a = 0; a < R; a += 4) {
-                            const float4 x = __ldg(reinterpret_cast<const float4*>(row + a));
-                            const float4 y = *reinterpret_cast<const float4*>(th + a);
-                            d = fmaf(x.x, y.x, d);
-                            d = fmaf(x.y, y.y, d);
-                            d = fmaf(x.z, y.z, d);
-                            d = fmaf(x.w, y.w, d);
+                    if (leaf_tma) {
+                        const float4* row = reinterpret_cast<const float4*>(stage + t * R);
+                        const float4* hv = reinterpret_cast<const float4*>(th);
+                        const int nq = R >> 2;
+                        float2 acc = make_float2(0.f, 0.f);
+                        for (int a = 0; a < nq; ++a) {
+                            const int j = (a + t) % nq;   // rotate chunks: conflict-free banks
+                            const float4 x = row[j], y = hv[j];
+                            acc = ffma2(make_float2(x.x, x.y), make_float2(y.x, y.y), acc);
+                            acc = ffma2(make_float2(x.z, x.w), make_float2(y.z, y.w), acc);
                         }
+                        d = acc.x + acc.y;
                     } else {
+                        const float* row = Uk + (row0 + t) * R;
                         for (int a = 0; a < R; ++a) d = fmaf(__ldg(row + a), th[a], d);
                     }
                 }
                 q[r] = d * d;
-                run = df_add(run, df{q[r], 0.f});
+                run += q[r];
             }
-            // inclusive warp scan of the per-lane totals in double-float
-            df inc = run;
+            const df rel = df_add(tau, df_neg(low));
+            const float target = rel.hi + rel.lo;
+            float inc = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const float vh = __shfl_up_sync(0xffffffffu, inc.hi, o);
-                const float vl = __shfl_up_sync(0xffffffffu, inc.lo, o);
-                if (lane >= o) inc = df_add(df{vh, vl}, inc);
+                const float v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
             }
-            df cum{__shfl_up_sync(0xffffffffu, inc.hi, 1), __shfl_up_sync(0xffffffffu, inc.lo, 1)};
-            if (lane == 0) cum = df{0.f, 0.f};
-            cum = df_add(cum, low);
-            // first row whose right edge low + cum reaches tau; else last row with weight
+            float cum = __shfl_up_sync(0xffffffffu, inc, 1);
+            if (lane == 0) cum = 0.f;
             int first = 0x7fffffff, lastpos = -1;
+            bool near = false;
 #pragma unroll
             for (int r = 0; r < C::RPT; ++r) {
                 const int t = lane * rpt + r;
                 if (r < rpt && t < nrows) {
-                    cum = df_add(cum, df{q[r], 0.f});
-                    if (first == 0x7fffffff && df_le(tau, cum)) first = t;
+                    cum += q[r];
+                    if (first == 0x7fffffff && target <= cum) first = t;
+                    if (fabsf(cum - target) <= margin) near = true;
                     if (q[r] > 0.f) lastpos = t;
+                }
+            }
+            if (__any_sync(0xffffffffu, near)) {
+                // redo the scan in double-float: edges low + cumulative weights
+                df acc{0.f, 0.f};
+#pragma unroll
+                for (int r = 0; r < C::RPT; ++r)
+                    if (r < rpt && lane * rpt + r < nrows) acc = df_add(acc, df{q[r], 0.f});
+                df incd = acc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float vh = __shfl_up_sync(0xffffffffu, incd.hi, o);
+                    const float vl = __shfl_up_sync(0xffffffffu, incd.lo, o);
+                    if (lane >= o) incd = df_add(df{vh, vl}, incd);
+                }
+                df cd{__shfl_up_sync(0xffffffffu, incd.hi, 1), __shfl_up_sync(0xffffffffu, incd.lo, 1)};
+                if (lane == 0) cd = df{0.f, 0.f};
+                cd = df_add(cd, low);
+                first = 0x7fffffff;
+#pragma unroll
+                for (int r = 0; r < C::RPT; ++r) {
+                    const int t = lane * rpt + r;
+                    if (r < rpt && t < nrows) {
+                        cd = df_add(cd, df{q[r], 0.f});
+                        if (first == 0x7fffffff && df_le(tau, cd)) first = t;
+                    }
                 }
             }
 #pragma unroll
@@ -333,19 +421,32 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
             }
             const int64_t trow = row0 + t_sel;
             if (lane < R) {
-                const df nh = df_mul_f(df{hh[lane], hl[lane]}, __ldg(Uk + trow * R + lane));
+                const float x = leaf_tma ? stage[t_sel * R + lane] : __ldg(Uk + trow * R + lane);
+                const df nh = df_mul_f(df{hh[lane], hl[lane]}, x);
                 hh[lane] = nh.hi;
                 hl[lane] = nh.lo;
             }
             if (lane == 0) P.idx[(int64_t)k * P.J + s] = (int32_t)trow;
             __syncwarp();
         }
+        if (!alive) break;
         // ------------------------------------------------ epilogue
         if (lane < RMAX) th[lane] = hh[lane] + hl[lane];
         __syncwarp();
         make_weights(th);
-        df lev, d1, d2;
-        mass3(P.Gplus32, nullptr, nullptr, 1, lev, d1, d2);
+        float part = 0.f;
+#pragma unroll
+        for (int m = 0; m < NCH; ++m) {
+            const int c4 = lane + 32 * m;
+            if (c4 < nc4) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(P.Gplus32) + c4);
+                part = fmaf(w4[m].x, v.x, part);
+                part = fmaf(w4[m].y, v.y, part);
+                part = fmaf(w4[m].z, v.z, part);
+                part = fmaf(w4[m].w, v.w, part);
+            }
+        }
+        const df lev = refine(part);
         const float qs = (lev.hi + lev.lo) / (float)(*P.rank);
         const float w = ok ? 1.0f / sqrtf((float)P.J * qs) : 0.f;
         if (lane == 0) {
@@ -355,17 +456,24 @@ __global__ void __launch_bounds__(256, 2) krp_descent_fast(FastParams P) {
         if (P.SA && lane < R) P.SA[s * R + lane] = w * th[lane];
         __syncwarp();
     }
+    if (!alive) {
+        // a staged copy never completed: wait once more (bounded) so that no
+        // copy into this CTA's shared memory is left in flight, then return
+        mbar_wait(mbar, phase ^ 1u);
+    }
 }
 
 namespace {
 template <int RMAX>
 cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
+    using C = FastCfg<RMAX>;
+    cudaFuncSetAttribute(krp_descent_fast<RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, krp_descent_fast<RMAX>, 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, krp_descent_fast<RMAX>, 256, C::SMEM);
     per_sm = per_sm > 0 ? per_sm : 1;
     const int64_t need = (P.J + 7) / 8;
     const int64_t grid = need < (int64_t)num_sms * per_sm ? need : (int64_t)num_sms * per_sm;
-    krp_descent_fast<RMAX><<<(unsigned)grid, 256, 0, st>>>(P); count_launch();
+    krp_descent_fast<RMAX><<<(unsigned)grid, 256, C::SMEM, st>>>(P); count_launch();
     return cudaGetLastError();
 }
 }  // namespace

@@ -77,7 +77,7 @@ int64_t launch_counter();
 krp_status cuda_check(krp_sampler* s, cudaError_t e, const char* what);
 
 // a1: build factor j's segment tree from s->U[j] (FP32 or BF16x3 Grams).
-krp_status build_tree(krp_sampler* s, int j, int precision);
+krp_status build_tree(krp_sampler* s, int j, int precision, const float* src = nullptr);
 // a2 + a3: G, G⁺, G_{>k}, eigendecompositions, E_k trees for the given exclusion.
 krp_status sampler_prep(krp_sampler* s, int exclude_j);
 // a4 + a5 (+a6 fused): the batched conditional descent.

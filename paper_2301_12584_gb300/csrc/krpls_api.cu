@@ -157,7 +157,7 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     }
     const size_t RR = (size_t)R * R;
     ok = ok && dalloc(&s->G64, N * RR) && dalloc(&s->Gplus64, RR) && dalloc(&s->lam64, (size_t)N * R) &&
-         dalloc(&s->V64, N * RR) && dalloc(&s->work64, std::max<size_t>(3 * RR, 2 * N * RR) + 256) &&
+         dalloc(&s->V64, N * RR) && dalloc(&s->work64, (size_t)6 * RR * (N + 1) + 256) &&
          dalloc(&s->Gplus32, (size_t)s->Tp) && dalloc(&s->etree, (size_t)N * s->Rp * s->Tp) &&
          dalloc(&s->V32, N * RR) && dalloc(&s->V32lo, N * RR) && dalloc(&s->rank_dev, 1) && dalloc(&s->status, 1) &&
          dalloc(&s->solve64, 3 * RR + 128 * (size_t)R);
@@ -177,10 +177,21 @@ krp_status krp_set_factor_prec(krp_sampler* s, int j, const float* U, int precis
     if (j < 0 || j >= s->N || !U) return fail(s, KRP_EINVAL, "krp_set_factor: bad factor index or NULL U");
     if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3)
         return fail(s, KRP_EINVAL, "krp_set_factor: unknown precision");
-    cudaError_t e = cudaMemcpyAsync(s->U[j], U, (size_t)s->I[j] * s->R * sizeof(float), cudaMemcpyDefault,
-                                    s->stream);
-    if (e != cudaSuccess) return cuda_check(s, e, "krp_set_factor copy");
-    krp_status st = build_tree(s, j, precision);
+    // Device-resident rows are read once by the build, which also writes the
+    // sampler's copy; host rows are copied first.
+    cudaPointerAttributes attr{};
+    const bool on_device = cudaPointerGetAttributes(&attr, U) == cudaSuccess &&
+                           (attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged);
+    cudaGetLastError();
+    krp_status st;
+    if (on_device) {
+        st = build_tree(s, j, precision, U);
+    } else {
+        cudaError_t e = cudaMemcpyAsync(s->U[j], U, (size_t)s->I[j] * s->R * sizeof(float), cudaMemcpyDefault,
+                                        s->stream);
+        if (e != cudaSuccess) return cuda_check(s, e, "krp_set_factor copy");
+        st = build_tree(s, j, precision);
+    }
     if (st != KRP_OK) return st;
     s->has_factor[j] = 1;
     s->last_exclude = -2;  // Grams changed: the next draw needs a fresh prepare

@@ -31,121 +31,272 @@ __device__ void ascending_positions(const double* lam, int n, int* pos) {
 
 struct PrepParams {
     const double* roots[16];  // FP64 root Gram G_k of each factor (packed upper)
-    int incl[16];            // included factors, ascending
+    int incl[16];             // included factors, ascending
     int n_incl;
 };
 
+// Block-wide sum of one double per thread (fixed order, every thread gets it).
+__device__ double block_sum(double v, double* red) {
+    v = warp_sum_d(v);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
 // ---------------------------------------------------------------------------
-// prep_pinv: G, G⁺, rank.  The three R x R FP64 work matrices live in shared
-// memory when they fit (R <= 64), else in the global buffer gbuf.
+// Symmetric eigendecomposition of an n x n FP64 matrix A (row-major), one CTA:
+// cyclic Jacobi in FP32 on A / max|A| (fast on GB300, whose FP64 rate is low),
+// then one FP64 refinement step of Ogita & Aishima ("Iterative refinement for
+// symmetric eigenvalue decomposition", Japan J. Indust. Appl. Math. 35, 2018):
+//   Rm = I - XᵀX, S = Xᵀ A X, λ_i = S_ii / (1 - Rm_ii),
+//   E_ij = (S_ij + λ_j Rm_ij) / (λ_j - λ_i) if |λ_i - λ_j| > δ else Rm_ij / 2,
+//   δ = 2 (||S - diag λ||_F + ||A||_F ||Rm||_F),  X <- X + X E,
+// which takes FP32-accurate eigenpairs to about 1e-14.
+// On exit X holds the eigenvectors in its columns and lam the eigenvalues
+// (unsorted).  Work: Af, Vf (n*n floats), As, S, T, Rm (n*n doubles), cs/pr.
+// ---------------------------------------------------------------------------
+struct EigWork {
+    float* Af;
+    float* Vf;
+    double* As;
+    double* S;
+    double* T;
+    double* Rm;
+    float* csf;
+    int* pr;
+    double* red;
+};
+
+__device__ void eig_fp32_refined(const double* __restrict__ A, int n, double* __restrict__ X, double* __restrict__ lam,
+                                 EigWork w) {
+    const int nn = n * n;
+    double mx = 0.0;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) mx = fmax(mx, fabs(A[e]));
+    __shared__ double s_mx;
+    if (threadIdx.x == 0) s_mx = 0.0;
+    __syncthreads();
+    // block max through atomics on a shared double (as bits; values are >= 0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&s_mx), __double_as_longlong(mx));
+    __syncthreads();
+    const double scale = s_mx > 0.0 ? s_mx : 1.0;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const double a = A[e] / scale;
+        w.As[e] = a;
+        w.Af[e] = (float)a;
+    }
+    __syncthreads();
+    jacobi_eig<float>(w.Af, w.Vf, n, w.csf, w.pr, w.red, 30, 4e-7);
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) X[e] = (double)w.Vf[e];
+    __syncthreads();
+    // Rm = I - XᵀX ; T = As X
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        double r = (i == j) ? 1.0 : 0.0, t = 0.0;
+        for (int k = 0; k < n; ++k) {
+            r -= X[k * n + i] * X[k * n + j];
+            t += w.As[i * n + k] * X[k * n + j];
+        }
+        w.Rm[e] = r;
+        w.T[e] = t;
+    }
+    __syncthreads();
+    // S = Xᵀ T
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) acc += X[k * n + i] * w.T[k * n + j];
+        w.S[e] = acc;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = w.S[i * n + i] / (1.0 - w.Rm[i * n + i]);
+    __syncthreads();
+    double off = 0.0, an = 0.0, rn = 0.0;
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        const double sd = w.S[e] - (i == j ? lam[i] : 0.0);
+        off += sd * sd;
+        an += w.As[e] * w.As[e];
+        rn += w.Rm[e] * w.Rm[e];
+    }
+    off = block_sum(off, w.red);
+    an = block_sum(an, w.red);
+    rn = block_sum(rn, w.red);
+    const double delta = 2.0 * (sqrt(off) + sqrt(an) * sqrt(rn));
+    // E into T
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        double E;
+        if (i == j)
+            E = 0.5 * w.Rm[e];
+        else if (fabs(lam[i] - lam[j]) > delta)
+            E = (w.S[e] + lam[j] * w.Rm[e]) / (lam[j] - lam[i]);
+        else
+            E = 0.5 * w.Rm[e];
+        w.T[e] = E;
+    }
+    __syncthreads();
+    // X <- X + X E (into S, then copy)
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+        const int i = e / n, j = e % n;
+        double acc = X[e];
+        for (int k = 0; k < n; ++k) acc += X[i * n + k] * w.T[k * n + j];
+        w.S[e] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nn; e += blockDim.x) X[e] = w.S[e];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] *= scale;
+    __syncthreads();
+}
+
+// Shared-memory carve-up for eig_fp32_refined plus extras; FP64 matrices go to
+// `gwork` (global) when `gwork` is non-null.
+__device__ EigWork carve(char* base, int n, double* gwork, double** X, double** A64, double** lam, int** pos) {
+    const int nn = n * n;
+    EigWork w;
+    char* p = base;
+    w.red = reinterpret_cast<double*>(p);
+    p += 64 * 8;
+    *lam = reinterpret_cast<double*>(p);
+    p += (size_t)n * 8;
+    *pos = reinterpret_cast<int*>(p);
+    p += (size_t)((n + 1) & ~1) * 4;
+    w.pr = reinterpret_cast<int*>(p);
+    p += (size_t)2 * (n / 2 + 1) * 4 + 8;
+    w.csf = reinterpret_cast<float*>(p);
+    p += (size_t)2 * (n / 2 + 1) * 4 + 8;
+    p = reinterpret_cast<char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    w.Af = reinterpret_cast<float*>(p);
+    p += (size_t)nn * 4;
+    w.Vf = reinterpret_cast<float*>(p);
+    p += (size_t)nn * 4;
+    p = reinterpret_cast<char*>(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    double* d = gwork ? gwork : reinterpret_cast<double*>(p);
+    w.As = d;
+    w.S = d + nn;
+    w.T = d + 2 * (size_t)nn;
+    w.Rm = d + 3 * (size_t)nn;
+    *X = d + 4 * (size_t)nn;
+    *A64 = d + 5 * (size_t)nn;
+    return w;
+}
+
+__host__ size_t carve_smem_bytes(int n, bool fp64_in_smem) {
+    const size_t nn = (size_t)n * n;
+    size_t b = 64 * 8 + (size_t)n * 8 + (size_t)((n + 1) & ~1) * 4 + 2 * ((size_t)2 * (n / 2 + 1) * 4 + 8) + 32;
+    b += 2 * nn * 4 + 16;
+    if (fp64_in_smem) b += 6 * nn * 8;
+    return b;
+}
+
+// ---------------------------------------------------------------------------
+// prep_pinv (one CTA): G = ⊛ G_k (FP64), G⁺ and rank.
+// Well-conditioned G (exact 1-norm condition number <= 1e10, so no eigenvalue
+// is near the cutoff): G⁺ = G⁻¹ from an FP64 Cholesky factor.  Otherwise the
+// eigen-pseudo-inverse with cutoff R * 2^-52 * lam_max.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) prep_pinv(PrepParams P, int N, int exclude, int R, int Tp,
                                                  double* __restrict__ G64, double* __restrict__ Gplus64,
                                                  float* __restrict__ Gplus32, int* __restrict__ rank_out,
-                                                 int* __restrict__ status, double* __restrict__ gbuf) {
-    extern __shared__ __align__(16) double sm[];
+                                                 int* __restrict__ status, double* __restrict__ gwork) {
+    extern __shared__ __align__(16) char smp[];
     const int RR = R * R;
-    double* red = sm;                        // 64
-    double* cs = red + 64;                   // 2*(R/2+1)
-    int* pr = (int*)(cs + 2 * (R / 2 + 1));  // 2*(R/2+1)
-    double* G = gbuf ? gbuf : (double*)(pr + 2 * (R / 2 + 1) + 2);  // R x R
-    double* W = G + RR;                      // R x R  (Cholesky factor / eigenvectors)
-    double* Ginv = W + RR;                   // R x R
+    double *X, *A64, *lam;
+    int* pos;
+    EigWork w = carve(smp, R, gwork, &X, &A64, &lam, &pos);
+    double* G = A64;        // R x R
+    double* Lm = w.S;       // Cholesky factor (lower)
+    double* Li = w.T;       // L⁻¹ (lower)
+    double* Gi = w.Rm;      // G⁻¹
+    __shared__ double s_inv[128];
+    __shared__ double s_c1[128], s_c2[128];
     __shared__ int flag;
-    __shared__ double s_norm, s_inorm;
-    // G_k in FP64 (full symmetric) for every factor; G = Hadamard of included
     for (int e = threadIdx.x; e < RR; e += blockDim.x) G[e] = 1.0;
     for (int k = 0; k < N; ++k) {
         const double* rt = P.roots[k];
         for (int e = threadIdx.x; e < RR; e += blockDim.x) {
             const int i = e / R, j = e % R;
-            const double v = rt ? rt[tri_index(min(i, j), max(i, j), R)] : 0.0;
+            const double v = rt[tri_index(min(i, j), max(i, j), R)];
             G64[(size_t)k * RR + e] = v;
             if (k != exclude) G[e] *= v;
         }
     }
     if (threadIdx.x == 0) flag = 0;
     __syncthreads();
-    // Cholesky G = L Lᵀ (right-looking, column by column), L in W (lower).
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) W[e] = G[e];
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) Lm[e] = G[e];
     __syncthreads();
     for (int c = 0; c < R; ++c) {
         if (threadIdx.x == 0) {
-            const double d = W[c * R + c];
+            const double d = Lm[c * R + c];
             if (!(d > 0.0)) flag = 1;
-            W[c * R + c] = d > 0.0 ? sqrt(d) : 1.0;
+            const double l = d > 0.0 ? sqrt(d) : 1.0;
+            Lm[c * R + c] = l;
+            s_inv[c] = 1.0 / l;
         }
         __syncthreads();
-        const double dc = W[c * R + c];
-        for (int i = c + 1 + threadIdx.x; i < R; i += blockDim.x) W[i * R + c] /= dc;
+        const double ic = s_inv[c];
+        for (int i = c + 1 + threadIdx.x; i < R; i += blockDim.x) Lm[i * R + c] *= ic;
         __syncthreads();
-        for (int e = threadIdx.x; e < (R - c - 1) * (R - c - 1); e += blockDim.x) {
-            const int i = c + 1 + e / (R - c - 1), j = c + 1 + e % (R - c - 1);
-            if (j <= i) W[i * R + j] -= W[i * R + c] * W[j * R + c];
+        const int n = R - c - 1;
+        for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+            const int i = c + 1 + e / n, j = c + 1 + e % n;
+            if (j <= i) Lm[i * R + j] -= Lm[i * R + c] * Lm[j * R + c];
         }
         __syncthreads();
     }
     if (!flag) {
-        // L⁻¹ column by column (forward substitution), into Ginv (lower).
-        for (int col = threadIdx.x; col < R; col += blockDim.x) {
+        for (int col = threadIdx.x; col < R; col += blockDim.x) {   // L⁻¹, column by column
             for (int i = 0; i < R; ++i) {
                 double acc = (i == col) ? 1.0 : 0.0;
-                for (int k = col; k < i; ++k) acc -= W[i * R + k] * Ginv[k * R + col];
-                Ginv[i * R + col] = (i >= col) ? acc / W[i * R + i] : 0.0;
+                for (int k = col; k < i; ++k) acc -= Lm[i * R + k] * Li[k * R + col];
+                Li[i * R + col] = (i >= col) ? acc * s_inv[i] : 0.0;
             }
         }
         __syncthreads();
-        // G⁻¹ = L⁻ᵀ L⁻¹ ; reuse W as output
-        for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) {        // G⁻¹ = L⁻ᵀ L⁻¹
             const int i = e / R, j = e % R;
             double acc = 0.0;
-            for (int k = max(i, j); k < R; ++k) acc += Ginv[k * R + i] * Ginv[k * R + j];
-            W[e] = acc;
+            for (int k = max(i, j); k < R; ++k) acc += Li[k * R + i] * Li[k * R + j];
+            Gi[e] = acc;
         }
         __syncthreads();
-        // exact 1-norm condition number ||G||_1 ||G⁻¹||_1
+        for (int j = threadIdx.x; j < R; j += blockDim.x) {         // column abs sums
+            double ca = 0.0, cb = 0.0;
+            for (int i = 0; i < R; ++i) {
+                ca += fabs(G[i * R + j]);
+                cb += fabs(Gi[i * R + j]);
+            }
+            s_c1[j] = ca;
+            s_c2[j] = cb;
+        }
+        __syncthreads();
         if (threadIdx.x == 0) {
             double a = 0.0, b = 0.0;
             for (int j = 0; j < R; ++j) {
-                double ca = 0.0, cb = 0.0;
-                for (int i = 0; i < R; ++i) {
-                    ca += fabs(G[i * R + j]);
-                    cb += fabs(W[i * R + j]);
-                }
-                a = fmax(a, ca);
-                b = fmax(b, cb);
+                a = fmax(a, s_c1[j]);
+                b = fmax(b, s_c2[j]);
             }
-            s_norm = a;
-            s_inorm = b;
             if (!(a * b <= 1e10)) flag = 1;
         }
         __syncthreads();
     }
     int rank = R;
     if (!flag) {
-        for (int e = threadIdx.x; e < RR; e += blockDim.x) Gplus64[e] = W[e];
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) Gplus64[e] = Gi[e];
     } else {
-        // eigen-pseudo-inverse in FP64
-        for (int e = threadIdx.x; e < RR; e += blockDim.x) Ginv[e] = G[e];
-        __syncthreads();
-        jacobi_eig<double>(Ginv, W, R, cs, pr, red, 30, 1e-14);
-        __shared__ double lam_max;
-        if (threadIdx.x == 0) {
-            double mx = 0.0;
-            for (int i = 0; i < R; ++i) mx = fmax(mx, Ginv[i * R + i]);
-            lam_max = mx;
-        }
-        __syncthreads();
-        const double cut = R * 2.220446049250313e-16 * lam_max;
+        eig_fp32_refined(G, R, X, lam, w);
+        double lmax = 0.0;
+        for (int i = 0; i < R; ++i) lmax = fmax(lmax, lam[i]);
+        const double cut = R * 2.220446049250313e-16 * lmax;
         rank = 0;
-        for (int i = 0; i < R; ++i) rank += Ginv[i * R + i] > cut;
+        for (int i = 0; i < R; ++i) rank += lam[i] > cut;
         for (int e = threadIdx.x; e < RR; e += blockDim.x) {
             const int i = e / R, j = e % R;
             double acc = 0.0;
-            for (int u = 0; u < R; ++u) {
-                const double l = Ginv[u * R + u];
-                if (l > cut) acc += W[i * R + u] * W[j * R + u] / l;
-            }
+            for (int u = 0; u < R; ++u)
+                if (lam[u] > cut) acc += X[i * R + u] * X[j * R + u] / lam[u];
             Gplus64[e] = acc;
         }
     }
@@ -153,14 +304,12 @@ __global__ void __launch_bounds__(256) prep_pinv(PrepParams P, int N, int exclud
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         float v = 0.f;
         if (e < tri_size(R)) {
-            // row i, column j of packed entry e
             int i = 0, rem = e;
             while (rem >= R - i) {
                 rem -= R - i;
                 ++i;
             }
-            const int j = i + rem;
-            v = (float)Gplus64[i * R + j];
+            v = (float)Gplus64[i * R + i + rem];
         }
         Gplus32[e] = v;
     }
@@ -171,43 +320,39 @@ __global__ void __launch_bounds__(256) prep_pinv(PrepParams P, int N, int exclud
 }
 
 // ---------------------------------------------------------------------------
-// prep_eig: one CTA per included factor.
+// prep_eig: one CTA per included factor k: G_{>k}, its eigendecomposition
+// (eig_fp32_refined), eigenvalues ascending with negatives clamped to zero,
+// eigenvectors as FP64 columns, FP32 rows and FP32 residual rows, and E_k.
 // ---------------------------------------------------------------------------
-template <typename Scalar>
-__global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int Rp,
-                                                int dE, int Tp, const double* __restrict__ G64,
-                                                const double* __restrict__ Gplus64, double* __restrict__ lam64,
-                                                double* __restrict__ V64, float* __restrict__ V32,
-                                                float* __restrict__ V32lo, float* __restrict__ etree) {
-    extern __shared__ __align__(16) double sm[];
+__global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int Rp, int dE, int Tp,
+                                                const double* __restrict__ G64, const double* __restrict__ Gplus64,
+                                                double* __restrict__ lam64, double* __restrict__ V64,
+                                                float* __restrict__ V32, float* __restrict__ V32lo,
+                                                float* __restrict__ etree, double* __restrict__ gwork) {
+    extern __shared__ __align__(16) char smp[];
     const int RR = R * R;
     const int p = blockIdx.x;
     const int n_incl = P.n_incl;
     const int k = P.incl[p];
-    Scalar* A = (Scalar*)sm;            // R x R
-    Scalar* V = A + RR;                 // R x R  (2 R*R Scalars: 8-byte aligned end)
-    double* lam = (double*)(V + RR);
-    int* pos = (int*)(lam + R);
-    double* red = (double*)(pos + R + (R & 1));
-    Scalar* cs = (Scalar*)(red + 64);
-    int* pr = (int*)(cs + 2 * (R / 2 + 1));
-    // G_{>k} = G⁺ ⊛ ⊛_{m>k, m included} G_m
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+    double *X, *A64, *lam;
+    int* pos;
+    EigWork w = carve(smp, R, gwork ? gwork + (size_t)p * 6 * RR : nullptr, &X, &A64, &lam, &pos);
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {     // G_{>k} = G⁺ ⊛ ⊛_{m>k} G_m
         double v = Gplus64[e];
         for (int q = p + 1; q < n_incl; ++q) v *= G64[(size_t)P.incl[q] * RR + e];
-        A[e] = (Scalar)v;
+        A64[e] = v;
     }
     __syncthreads();
-    jacobi_eig<Scalar>(A, V, R, cs, pr, red, 30, sizeof(Scalar) == 8 ? 1e-14 : 1e-6);
-    for (int i = threadIdx.x; i < R; i += blockDim.x) lam[i] = fmax((double)A[i * R + i], 0.0);
+    eig_fp32_refined(A64, R, X, lam, w);
+    for (int i = threadIdx.x; i < R; i += blockDim.x) lam[i] = fmax(lam[i], 0.0);
     __syncthreads();
     ascending_positions(lam, R, pos);
     __syncthreads();
     for (int e = threadIdx.x; e < RR; e += blockDim.x) {
-        const int row = e / R, u = e % R;   // V[row][u], eigenvector u in column u
+        const int row = e / R, u = e % R;   // X[row][u], eigenvector u in column u
         const int o = pos[u];
-        V64[(size_t)k * RR + row * R + o] = (double)V[e];
-        const double v = (double)V[e];
+        const double v = X[e];
+        V64[(size_t)k * RR + row * R + o] = v;
         const float vh = (float)v;
         V32[(size_t)k * RR + o * R + row] = vh;   // row o = eigenvector
         V32lo[(size_t)k * RR + o * R + row] = (float)(v - (double)vh);
@@ -252,6 +397,8 @@ __global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int 
     }
 }
 
+size_t carve_smem_bytes(int n, bool fp64_in_smem);
+
 krp_status sampler_prep(krp_sampler* s, int exclude_j) {
     const int R = s->R, N = s->N;
     PrepParams P{};
@@ -260,32 +407,19 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j) {
         P.roots[k] = s->root64[k];
         if (k != exclude_j) P.incl[P.n_incl++] = k;
     }
-    const size_t mats = (size_t)3 * R * R * 8;
-    const size_t small = 64 * 8 + 2 * (R / 2 + 1) * 8 + 2 * (R / 2 + 1) * 4 + 16;
-    const bool pinv_smem = mats + small <= 200 * 1024;
-    const size_t sm1 = small + (pinv_smem ? mats : 0);
-    if (sm1 > 48 * 1024) cudaFuncSetAttribute(prep_pinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
-    prep_pinv<<<1, 256, sm1, s->stream>>>(P, N, exclude_j, R, s->Tp, s->G64, s->Gplus64, s->Gplus32,
-                                          s->rank_dev, s->status, pinv_smem ? nullptr : s->work64); count_launch();
+    const bool in_smem = carve_smem_bytes(R, true) <= 200 * 1024;
+    const size_t smem = carve_smem_bytes(R, in_smem);
+    if (smem > 48 * 1024) {
+        cudaFuncSetAttribute(prep_pinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(prep_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    }
+    prep_pinv<<<1, 256, smem, s->stream>>>(P, N, exclude_j, R, s->Tp, s->G64, s->Gplus64, s->Gplus32, s->rank_dev,
+                                          s->status, in_smem ? nullptr : s->work64); count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_pinv launch");
-    // Eigendecompositions of G_{>k}: FP64 Jacobi while the two R x R FP64
-    // matrices fit in shared memory (R <= 64), FP32 Jacobi above that.
-    const bool fp64 = (size_t)2 * R * R * 8 <= 96 * 1024;
-    const size_t sc = fp64 ? 8 : 4;
-    const size_t sm2 = 2 * (size_t)R * R * sc + (size_t)R * 8 + (size_t)(R + 2) * 4 + 64 * 8 +
-                       2 * (R / 2 + 1) * sc + 2 * (R / 2 + 1) * 4 + 64;
-    if (fp64) {
-        if (sm2 > 48 * 1024)
-            cudaFuncSetAttribute(prep_eig<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-        prep_eig<double><<<P.n_incl, 256, sm2, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64,
-                                                           s->lam64, s->V64, s->V32, s->V32lo, s->etree); count_launch();
-    } else {
-        if (sm2 > 48 * 1024)
-            cudaFuncSetAttribute(prep_eig<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
-        prep_eig<float><<<P.n_incl, 256, sm2, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64,
-                                                          s->lam64, s->V64, s->V32, s->V32lo, s->etree); count_launch();
-    }
+    prep_eig<<<P.n_incl, 256, smem, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64, s->lam64, s->V64,
+                                                s->V32, s->V32lo, s->etree,
+                                                in_smem ? nullptr : s->work64); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_eig launch");
     s->last_exclude = exclude_j;

@@ -167,10 +167,26 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
     }
 }
 
+// Write the staged rows [row0, row0 + nrows) back out to `dst` (the sampler's
+// own copy of the factor), so that a factor update reads its source once.
+template <bool VEC>
+__device__ __forceinline__ void copy_rows_out(const float* sU, float* __restrict__ dst, int64_t I, int R,
+                                              int64_t row0, int nrows) {
+    const int64_t valid = max((int64_t)0, min((int64_t)nrows * R, (I - row0) * (int64_t)R));
+    float* out = dst + row0 * (int64_t)R;
+    if (VEC) {
+        for (int64_t c = threadIdx.x; c < valid / 4; c += blockDim.x)
+            reinterpret_cast<float4*>(out)[c] = reinterpret_cast<const float4*>(sU)[c];
+        for (int64_t e = (valid / 4) * 4 + threadIdx.x; e < valid; e += blockDim.x) out[e] = sU[e];
+    } else {
+        for (int64_t e = threadIdx.x; e < valid; e += blockDim.x) out[e] = sU[e];
+    }
+}
+
 template <int LB, bool VEC>
-__global__ void __launch_bounds__(512) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
+__global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
                                                         int64_t L, int G, int Tp, float* __restrict__ tree,
-                                                        float* __restrict__ top) {
+                                                        float* __restrict__ top, float* __restrict__ copy_to) {
     extern __shared__ __align__(16) float smem[];
     const int rows = LB * F;
     const int T = tri_size(R);
@@ -195,6 +211,7 @@ __global__ void __launch_bounds__(512) tree_leaves_fp32(const float* __restrict_
             }
         }
         __syncthreads();
+        if (copy_to) copy_rows_out<VEC>(cur, copy_to, I, R, (leaf0 + (int64_t)g * LB) * F, rows);
         leaf_grams_fp32<LB, VEC>(cur, sG, R, F, Tp);
         __syncthreads();
         reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp);
@@ -286,18 +303,19 @@ namespace {
 
 template <int LB, bool VEC>
 cudaError_t launch_leaves(const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree,
-                          float* top, int64_t ctas, int threads, size_t smem, cudaStream_t st) {
+                          float* top, float* copy_to, int64_t ctas, int threads, size_t smem, cudaStream_t st) {
     auto k = tree_leaves_fp32<LB, VEC>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<(unsigned)ctas, threads, smem, st>>>(U, I, R, F, L, G, Tp, tree, top); count_launch();
+    k<<<(unsigned)ctas, threads, smem, st>>>(U, I, R, F, L, G, Tp, tree, top, copy_to); count_launch();
     return cudaGetLastError();
 }
 
 template <int LB>
 cudaError_t dispatch_vec(bool vec, const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp,
-                         float* tree, float* top, int64_t ctas, int threads, size_t smem, cudaStream_t st) {
-    return vec ? launch_leaves<LB, true>(U, I, R, F, L, G, Tp, tree, top, ctas, threads, smem, st)
-               : launch_leaves<LB, false>(U, I, R, F, L, G, Tp, tree, top, ctas, threads, smem, st);
+                         float* tree, float* top, float* copy_to, int64_t ctas, int threads, size_t smem,
+                         cudaStream_t st) {
+    return vec ? launch_leaves<LB, true>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st)
+               : launch_leaves<LB, false>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st);
 }
 
 }  // namespace
@@ -311,7 +329,7 @@ void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* 
     while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * leaf_bytes <= 32 * 1024) LB *= 2;
     const int nt = (R + 3) / 4;
     const int ntile = nt * (nt + 1) / 2;
-    int threads = std::min(512, std::max(64, ((LB * ntile + 31) / 32) * 32));
+    int threads = std::min(288, std::max(64, ((LB * ntile + 31) / 32) * 32));
     const int64_t groups = L / LB;
     int G = 1;
     auto smem_of = [&](int g) {
@@ -326,7 +344,11 @@ void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* 
     *smem_out = smem_of(G);
 }
 
-krp_status build_tree(krp_sampler* s, int j, int precision) {
+krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
+    // src: rows to build from; if it is not the sampler's copy, the leaf kernel
+    // also writes them into s->U[j].
+    float* copy_to = (src && src != s->U[j]) ? s->U[j] : nullptr;
+    if (!src) src = s->U[j];
     const int R = s->R, F = s->F, Tp = s->Tp;
     const int64_t I = s->I[j], L = s->L[j];
     const bool vec = (R % 4) == 0;
@@ -358,11 +380,11 @@ krp_status build_tree(krp_sampler* s, int j, int precision) {
     if (!done) {
         cudaError_t e;
         switch (LB) {
-            case 1: e = dispatch_vec<1>(vec, s->U[j], I, R, F, L, G, Tp, s->tree[j], top, ctas, threads, smem, s->stream); break;
-            case 2: e = dispatch_vec<2>(vec, s->U[j], I, R, F, L, G, Tp, s->tree[j], top, ctas, threads, smem, s->stream); break;
-            case 4: e = dispatch_vec<4>(vec, s->U[j], I, R, F, L, G, Tp, s->tree[j], top, ctas, threads, smem, s->stream); break;
-            case 8: e = dispatch_vec<8>(vec, s->U[j], I, R, F, L, G, Tp, s->tree[j], top, ctas, threads, smem, s->stream); break;
-            default: e = dispatch_vec<16>(vec, s->U[j], I, R, F, L, G, Tp, s->tree[j], top, ctas, threads, smem, s->stream); break;
+            case 1: e = dispatch_vec<1>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
+            case 2: e = dispatch_vec<2>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
+            case 4: e = dispatch_vec<4>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
+            case 8: e = dispatch_vec<8>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
+            default: e = dispatch_vec<16>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
         }
         if (e != cudaSuccess) return cuda_check(s, e, "tree leaf kernel launch");
     }

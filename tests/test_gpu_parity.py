@@ -390,3 +390,40 @@ def test_full_size_index_parity_fp32_band():
     np.testing.assert_allclose(out["weight"][same], ref["weight"][same], rtol=1e-4)
     print(f"full size: {mism} FP32-band mismatches / {J} ({mism / J:.2e})")
     s.close()
+
+
+@pytest.mark.parametrize("I,R,excl,rankdef", [(300, 8, -1, False), (500, 32, 1, False), (200, 13, -1, True),
+                                              (400, 64, -1, False)])
+def test_prepare_matches_fp64_oracle(I, R, excl, rankdef):
+    """G⁺, rank and the eigendecomposition of every G_{>k} (Alg. 2 lines 1-4)
+    against numpy FP64 from the exact Grams: eigenvalues, VΛVᵀ = G_{>k},
+    VᵀV = I, and individual eigenvectors (up to sign) where the eigenvalue
+    gap exceeds 1e-2 of the largest eigenvalue (elsewhere the basis of a
+    near-degenerate cluster is not determined by the matrix)."""
+    Us = synth.skewed_row_factors(3, I, R, seed=I + R)
+    if rankdef:
+        for U in Us:
+            U[:, -1] = U[:, 0]
+    s = sampler_for(Us, 0)
+    J = 64
+    draw(s, Us, excl, J, seed=1, draw_id=0)
+    U64 = [U.astype(np.float64) for U in Us]
+    prep = O.SamplerPrep(U64, excl)
+    for p, k in enumerate(prep.incl):
+        lam, V, Gp, rank = s.get_prep(k)
+        assert rank == prep.rank
+        np.testing.assert_allclose(Gp, prep.Gplus, rtol=0, atol=1e-9 * np.abs(prep.Gplus).max())
+        lmax = prep.lam[k].max()
+        np.testing.assert_allclose(lam, prep.lam[k], rtol=0, atol=1e-9 * lmax)
+        Ggt = prep.Ggt[k]
+        recon = (V * lam) @ V.T
+        assert np.abs(recon - Ggt).max() <= 1e-9 * np.abs(Ggt).max()
+        assert np.abs(V.T @ V - np.eye(R)).max() <= 1e-9
+        gaps = np.diff(prep.lam[k])
+        for u in range(R):
+            left = gaps[u - 1] if u > 0 else np.inf
+            right = gaps[u] if u < R - 1 else np.inf
+            if min(left, right) > 1e-2 * lmax:
+                v, vo = V[:, u], prep.V[k][:, u]
+                assert min(np.abs(v - vo).max(), np.abs(v + vo).max()) < 1e-8, (k, u)
+    s.close()
