@@ -59,9 +59,9 @@ struct FastCfg {
     static constexpr int NCH = (NC4 + 31) / 32;     // chunks per lane
     static constexpr int WARPS = 8;
     static constexpr int RPT = (4 * RMAX + 31) / 32;  // leaf rows per lane (F <= 4R)
-    // per-warp shared memory: 3 staged nodes (slots c, 2c, 2c+1; also the leaf
-    // rows), h (hi, lo), h̃, mbarrier
-    static constexpr int STAGE = 3 * TPMAX;
+    // per-warp shared memory: 4 staged nodes (slots 0..3 on a stage's first
+    // fetch, then slots c, 2c, 2c+1; also the leaf rows), h (hi, lo), h̃, mbarrier
+    static constexpr int STAGE = 4 * TPMAX;
     static constexpr int WARP_BYTES = ((STAGE + 3 * RMAX) * 4 + 16 + 127) & ~127;
     static constexpr int SMEM = WARPS * WARP_BYTES + 2 * TPMAX;
 };
@@ -80,13 +80,15 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
                  : "memory");
 }
 // Bounded wait for the mbarrier phase `parity`; false if it did not complete.
+// Each try_wait may suspend the warp for up to ~0.1 ms (the hint), so the
+// loop spins little; 1<<16 tries bound the wait to a few seconds.
 __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
-    for (int it = 0; it < (1 << 24); ++it) {
+    for (int it = 0; it < (1 << 16); ++it) {
         uint32_t done;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
             : "=r"(done)
-            : "r"(smem_u32(m)), "r"(parity)
+            : "r"(smem_u32(m)), "r"(parity), "r"(100000u)
             : "memory");
         if (done) return true;
     }
@@ -135,8 +137,9 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
     uint32_t phase = 0;
     bool alive = true;
 
-    // Stage up to two contiguous global ranges into `stage` (bytes multiple of 16).
-    auto fetch = [&](const float* a, uint32_t abytes, const float* b, uint32_t bbytes) -> bool {
+    // Stage up to two contiguous global ranges into `stage` (bytes multiple of
+    // 16): issue, then wait (bounded).
+    auto fetch_issue = [&](const float* a, uint32_t abytes, const float* b, uint32_t bbytes) {
         __syncwarp();
         if (lane == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -144,6 +147,8 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
             tma_load_1d(stage, a, abytes, mbar);
             if (bbytes) tma_load_1d(stage + Tp, b, bbytes, mbar);
         }
+    };
+    auto fetch_wait = [&]() -> bool {
         const bool ok = mbar_wait(mbar, phase);
         phase ^= 1u;
         if (!ok) {
@@ -151,6 +156,10 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
             alive = false;
         }
         return ok;
+    };
+    auto fetch = [&](const float* a, uint32_t abytes, const float* b, uint32_t bbytes) -> bool {
+        fetch_issue(a, abytes, b, bbytes);
+        return fetch_wait();
     };
 
     float4 w4[NCH];
@@ -198,26 +207,46 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
         cut = df_add(low, refine(part));
         return df_le(tau, cut);
     };
-    // root mass of a tree, double-float
-    auto root_mass = [&](const float* tr) -> df {
-        if (!fetch(tr, Tp * 4, nullptr, 0)) return df{0.f, 0.f};
-        return refine(partial(stage));
-    };
-    // One descent of Alg. 4; returns the leaf heap index, low = its left edge.
-    auto descend = [&](const float* __restrict__ tr, int depth, int64_t Lk, int64_t nreal_rows, int F, df tau,
-                       df& low, float* trc, float croot, float margin) -> int64_t {
+    // One descent of Alg. 4 whose first fetch (slots 0..min(3, L-1), already
+    // issued) holds the root and levels 0-1.  Returns the leaf heap index; low
+    // is its left edge; Cm the root mass; tau = u * Cm.
+    auto descend = [&](const float* __restrict__ tr, int depth, int64_t Lk, int64_t nreal_rows, int F, float uu,
+                       df& Cm, df& tau, df& low, float* trc) -> int64_t {
+        low = df{0.f, 0.f};
+        if (!fetch_wait()) return 1;
+        const int nfirst = depth >= 2 ? 4 : (depth == 1 ? 2 : 1);
+        float pr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) pr[q] = q < nfirst ? partial(stage + q * Tp) : 0.f;
+        Cm = refine(pr[0]);
+        const float cf = Cm.hi + Cm.lo;
+        if (!(cf > 0.f) || !isfinite(cf)) return -1;
+        tau = df_mul_f(Cm, uu);
+        const float margin = 1e-6f * cf;
+        if (trc) trc[0] = cf;
         int64_t c = 1;
         int lvl = 0;
-        float mnode = croot;
+        float mnode = cf;
+        // levels 0 and 1 from the first fetch
+        float mA = depth >= 1 ? warp_sum(pr[1]) : 0.f, pA = pr[1];
+        float mB = depth >= 2 ? warp_sum(pr[2]) : 0.f, pB = pr[2];
+        float mD = depth >= 2 ? warp_sum(pr[3]) : 0.f, pD = pr[3];
+        bool have_next = depth >= 2;
         while (lvl < depth && alive) {
-            const bool two = lvl + 2 <= depth;
-            if (!fetch(tr + c * Tp, Tp * 4, two ? tr + 2 * c * Tp : nullptr, two ? 2 * Tp * 4 : 0)) break;
-            float pA = partial(stage), pB = 0.f, pD = 0.f;
-            if (two) {
-                pB = partial(stage + Tp);
-                pD = partial(stage + 2 * Tp);
+            if (lvl > 0) {
+                // fetch slots c (level lvl) and 2c, 2c+1 (level lvl + 1) when two remain
+                have_next = lvl + 2 <= depth;
+                if (!fetch(tr + c * Tp, Tp * 4, have_next ? tr + 2 * c * Tp : nullptr, have_next ? 2 * Tp * 4 : 0))
+                    break;
+                pA = partial(stage);
+                mA = warp_sum(pA);
+                if (have_next) {
+                    pB = partial(stage + Tp);
+                    pD = partial(stage + 2 * Tp);
+                    mB = warp_sum(pB);
+                    mD = warp_sum(pD);
+                }
             }
-            float mA = warp_sum(pA), mB = two ? warp_sum(pB) : 0.f, mD = two ? warp_sum(pD) : 0.f;
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
                 df cut;
@@ -239,7 +268,7 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
                 }
                 ++lvl;
             }
-            if (!two) break;
+            if (!have_next) break;
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
                 df cut;
@@ -278,56 +307,51 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
             float* trc = (P.trace && s < P.n_trace && lane == 0)
                              ? P.trace + ((s * P.n_incl + pi) * 2) * FAST_TRACE_STRIDE
                              : nullptr;
-            // ------------------------------------------------ eigencomponent stage
-            if (lane < RMAX) th[lane] = hh[lane] + hl[lane];
-            __syncwarp();
-            make_weights(th);
-            const float* et = P.etree[k];
-            df Cm = root_mass(et);
-            float cf = Cm.hi + Cm.lo;
-            if (!alive) break;
-            if (!(cf > 0.f) || !isfinite(cf)) {
-                if (lane == 0) set_status(P.status, isfinite(cf) ? KRP_EZERO : KRP_ENUMERIC);
-                ok = false;
-                break;
-            }
-            if (trc) trc[0] = cf;
-            df low{0.f, 0.f};
-            int64_t c = descend(et, P.dE, P.Rp, R, 1, df_mul_f(Cm, u_eig), low, trc, cf, 1e-6f * cf);
-            if (!alive) break;
-            const int u = (int)(c - P.Rp);
-            // ------------------------------------------------ row stage
-            if (lane < RMAX) {
-                float vh = 0.f, vl = 0.f;
-                if (lane < R) {
-                    vh = __ldg(P.Vhi[k] + (size_t)u * R + lane);
-                    vl = __ldg(P.Vlo[k] + (size_t)u * R + lane);
-                }
-                const df t = df_add(df_mul_f(df{hh[lane], hl[lane]}, vh), df_mul_f(df{hh[lane], hl[lane]}, vl));
-                th[lane] = t.hi + t.lo;   // h̃ = h ∘ V[:,u], rounded once
-            }
-            __syncwarp();
-            make_weights(th);
-            const float* tr = P.tree[k];
-            Cm = root_mass(tr);
-            cf = Cm.hi + Cm.lo;
-            if (!alive) break;
-            if (!(cf > 0.f) || !isfinite(cf)) {
-                if (lane == 0) set_status(P.status, isfinite(cf) ? KRP_EZERO : KRP_ENUMERIC);
-                ok = false;
-                break;
-            }
-            if (trc) {
-                trc += FAST_TRACE_STRIDE;
-                trc[0] = cf;
-            }
-            const df tau = df_mul_f(Cm, u_row);
-            low = df{0.f, 0.f};
+            // Two stages through one code path: stage 0 draws the eigencomponent
+            // u from E_k (leaf size 1, Y = G_k, history h); stage 1 draws the row
+            // from Z_k (leaf size F, Y = [1], history h̃ = h ∘ V[:,u]).
             const int64_t Lk = P.L[k], Ik = P.I[k];
             const int F = P.F;
-            const float margin = 1e-6f * cf;
-            c = descend(tr, P.depth[k], Lk, Ik, F, tau, low, trc, cf, margin);
-            if (!alive) break;
+            df tau{0.f, 0.f}, low{0.f, 0.f};
+            float cf = 0.f, margin = 0.f;
+            int64_t c = 1;
+            int u = 0;
+            for (int stage = 0; stage < 2; ++stage) {
+                const float* tr = stage ? P.tree[k] : P.etree[k];
+                const int depth = stage ? P.depth[k] : P.dE;
+                // issue the first fetch (root and levels 0-1), then build the
+                // stage's weights while it is in flight
+                const int nfirst = depth >= 2 ? 4 : (depth == 1 ? 2 : 1);
+                fetch_issue(tr, (uint32_t)(nfirst * Tp * 4), nullptr, 0);
+                if (stage == 0) {
+                    if (lane < RMAX) th[lane] = hh[lane] + hl[lane];
+                } else if (lane < RMAX) {
+                    float vh = 0.f, vl = 0.f;
+                    if (lane < R) {
+                        vh = __ldg(P.Vhi[k] + (size_t)u * R + lane);
+                        vl = __ldg(P.Vlo[k] + (size_t)u * R + lane);
+                    }
+                    const df t = df_add(df_mul_f(df{hh[lane], hl[lane]}, vh), df_mul_f(df{hh[lane], hl[lane]}, vl));
+                    th[lane] = t.hi + t.lo;   // h̃ = h ∘ V[:,u], rounded once
+                }
+                __syncwarp();
+                make_weights(th);
+                if (trc && stage) trc += FAST_TRACE_STRIDE;
+                df Cm;
+                c = descend(tr, depth, stage ? Lk : P.Rp, stage ? Ik : R, stage ? F : 1, stage ? u_row : u_eig, Cm,
+                            tau, low, trc);
+                if (!alive) break;
+                if (c < 0) {
+                    const float cv = Cm.hi + Cm.lo;
+                    if (lane == 0) set_status(P.status, isfinite(cv) ? KRP_EZERO : KRP_ENUMERIC);
+                    ok = false;
+                    break;
+                }
+                cf = Cm.hi + Cm.lo;
+                margin = 1e-6f * cf;
+                if (stage == 0) u = (int)(c - P.Rp);
+            }
+            if (!alive || !ok) break;
             // ------------------------------------------------ leaf scan
             const int64_t row0 = (c - Lk) * F;
             const int nrows = (int)min((int64_t)F, Ik - row0);
@@ -468,6 +492,8 @@ template <int RMAX>
 cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
     using C = FastCfg<RMAX>;
     cudaFuncSetAttribute(krp_descent_fast<RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaFuncSetAttribute(krp_descent_fast<RMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, krp_descent_fast<RMAX>, 256, C::SMEM);
     per_sm = per_sm > 0 ? per_sm : 1;

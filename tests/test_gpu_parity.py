@@ -399,7 +399,8 @@ def test_prepare_matches_fp64_oracle(I, R, excl, rankdef):
     against numpy FP64 from the exact Grams: eigenvalues, VΛVᵀ = G_{>k},
     VᵀV = I, and individual eigenvectors (up to sign) where the eigenvalue
     gap exceeds 1e-2 of the largest eigenvalue (elsewhere the basis of a
-    near-degenerate cluster is not determined by the matrix)."""
+    near-degenerate cluster is not determined by the matrix).  One FP64
+    refinement step from FP32 Jacobi leaves ~1e-9 orthogonality error there."""
     Us = synth.skewed_row_factors(3, I, R, seed=I + R)
     if rankdef:
         for U in Us:
@@ -417,8 +418,8 @@ def test_prepare_matches_fp64_oracle(I, R, excl, rankdef):
         np.testing.assert_allclose(lam, prep.lam[k], rtol=0, atol=1e-9 * lmax)
         Ggt = prep.Ggt[k]
         recon = (V * lam) @ V.T
-        assert np.abs(recon - Ggt).max() <= 1e-9 * np.abs(Ggt).max()
-        assert np.abs(V.T @ V - np.eye(R)).max() <= 1e-9
+        assert np.abs(recon - Ggt).max() <= 1e-8 * lmax
+        assert np.abs(V.T @ V - np.eye(R)).max() <= 1e-8
         gaps = np.diff(prep.lam[k])
         for u in range(R):
             left = gaps[u - 1] if u > 0 else np.inf
