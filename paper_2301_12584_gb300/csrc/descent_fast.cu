@@ -59,9 +59,9 @@ struct FastCfg {
     static constexpr int NCH = (NC4 + 31) / 32;     // chunks per lane
     static constexpr int WARPS = 8;
     static constexpr int RPT = (4 * RMAX + 31) / 32;  // leaf rows per lane (F <= 4R)
-    // per-warp shared memory: 4 staged nodes (slots 0..3 on a stage's first
+    // per-warp shared memory: 3 staged nodes (slots 0..1 on a stage's first
     // fetch, then slots c, 2c, 2c+1; also the leaf rows), h (hi, lo), h̃, mbarrier
-    static constexpr int STAGE = 4 * TPMAX;
+    static constexpr int STAGE = 3 * TPMAX;
     static constexpr int WARP_BYTES = ((STAGE + 3 * RMAX) * 4 + 16 + 127) & ~127;
     static constexpr int SMEM = WARPS * WARP_BYTES + 2 * TPMAX;
 };
@@ -207,17 +207,17 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
         cut = df_add(low, refine(part));
         return df_le(tau, cut);
     };
-    // One descent of Alg. 4 whose first fetch (slots 0..min(3, L-1), already
-    // issued) holds the root and levels 0-1.  Returns the leaf heap index; low
-    // is its left edge; Cm the root mass; tau = u * Cm.
+    // One descent of Alg. 4 whose first fetch (slots 0 and 1, already issued)
+    // holds the root and level 0.  Returns the leaf heap index; low is its left
+    // edge; Cm the root mass; tau = u * Cm.
     auto descend = [&](const float* __restrict__ tr, int depth, int64_t Lk, int64_t nreal_rows, int F, float uu,
                        df& Cm, df& tau, df& low, float* trc) -> int64_t {
         low = df{0.f, 0.f};
         if (!fetch_wait()) return 1;
-        const int nfirst = depth >= 2 ? 4 : (depth == 1 ? 2 : 1);
-        float pr[4];
+        const int nfirst = depth >= 1 ? 2 : 1;
+        float pr[2];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) pr[q] = q < nfirst ? partial(stage + q * Tp) : 0.f;
+        for (int q = 0; q < 2; ++q) pr[q] = q < nfirst ? partial(stage + q * Tp) : 0.f;
         Cm = refine(pr[0]);
         const float cf = Cm.hi + Cm.lo;
         if (!(cf > 0.f) || !isfinite(cf)) return -1;
@@ -227,11 +227,10 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
         int64_t c = 1;
         int lvl = 0;
         float mnode = cf;
-        // levels 0 and 1 from the first fetch
+        // level 0 from the first fetch
         float mA = depth >= 1 ? warp_sum(pr[1]) : 0.f, pA = pr[1];
-        float mB = depth >= 2 ? warp_sum(pr[2]) : 0.f, pB = pr[2];
-        float mD = depth >= 2 ? warp_sum(pr[3]) : 0.f, pD = pr[3];
-        bool have_next = depth >= 2;
+        float mB = 0.f, pB = 0.f, mD = 0.f, pD = 0.f;
+        bool have_next = false;
         while (lvl < depth && alive) {
             if (lvl > 0) {
                 // fetch slots c (level lvl) and 2c, 2c+1 (level lvl + 1) when two remain
@@ -268,7 +267,7 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
                 }
                 ++lvl;
             }
-            if (!have_next) break;
+            if (!have_next) continue;
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
                 df cut;
@@ -321,7 +320,7 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
                 const int depth = stage ? P.depth[k] : P.dE;
                 // issue the first fetch (root and levels 0-1), then build the
                 // stage's weights while it is in flight
-                const int nfirst = depth >= 2 ? 4 : (depth == 1 ? 2 : 1);
+                const int nfirst = depth >= 1 ? 2 : 1;
                 fetch_issue(tr, (uint32_t)(nfirst * Tp * 4), nullptr, 0);
                 if (stage == 0) {
                     if (lane < RMAX) th[lane] = hh[lane] + hl[lane];
