@@ -100,7 +100,7 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle ----
-def oracle_samples_per_s(Us64, n_samples=24):
+def oracle_samples_per_s(Us64, n_samples=240):
     """The FP64 oracle as it stands on a bounded sample of one step: its
     preparation (Grams, G⁺, eigendecompositions) plus n_samples draws, scaled
     to a full draw of J samples.  Returns (samples/s, seconds, sample text)."""

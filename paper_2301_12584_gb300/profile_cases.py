@@ -1,0 +1,55 @@
+"""Small, fixed workloads for profiling single kernels of libkrpls with ncu.
+
+  python -m paper_2301_12584_gb300.profile_cases descent   # krp_descent_fast, N=3, I=2^20, R=32, J=2^16
+  python -m paper_2301_12584_gb300.profile_cases build     # tree_leaves_*, one factor 2^21 x 32
+  python -m paper_2301_12584_gb300.profile_cases prep      # prep_pinv / prep_eig, R=32, N=3
+
+Each case runs its kernel a few times (the first launches warm up), checks the
+device status and exits 0.  Inputs are the seeded generators of synth.py.
+"""
+import sys
+
+import torch
+
+from . import synth
+from .krpls import Sampler
+
+
+def descent():
+    I, R, J = 1 << 20, 32, 1 << 16
+    Us = synth.skewed_row_factors(3, I, R, seed=0)
+    s = Sampler([I] * 3, R, 32)
+    for k in range(3):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    idx = torch.zeros((3, J), dtype=torch.int32, device="cuda")
+    w = torch.zeros(J, device="cuda")
+    SA = torch.zeros((J, R), device="cuda")
+    for d in range(3):
+        s.sample(-1, J, 1, d, idx, w, None, SA)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def build():
+    I, R = 1 << 21, 32
+    U = torch.from_numpy(synth.skewed_row_factors(1, I, R, seed=0)[0]).cuda()
+    s = Sampler([I], R, 32)
+    for _ in range(3):
+        s.set_factor(0, U)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def prep():
+    I, R = 1 << 16, 32
+    Us = synth.skewed_row_factors(3, I, R, seed=0)
+    s = Sampler([I] * 3, R, 32)
+    for k in range(3):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    for _ in range(4):
+        s.sample_prepare(-1)
+    assert s.sync_status() == 0, s.last_error()
+
+
+if __name__ == "__main__":
+    {"descent": descent, "build": build, "prep": prep}[sys.argv[1]]()
+    torch.cuda.synchronize()
+    print("ok")
