@@ -195,6 +195,13 @@ krp_status krp_sync_status(krp_sampler* s);
  * (all samplers; for accounting in benchmarks). */
 int64_t krp_launch_count(void);
 
+/* Test hook for the device-side wait bound (no counterpart in the paper): the
+ * descent's TMA waits give up after a bounded number of suspending tries and
+ * set KRP_ETIMEOUT instead of hanging.  This launches one warp that waits on a
+ * barrier nothing completes, with `tries` (1..1000) tries of up to ~0.1 ms
+ * each; krp_sync_status then returns KRP_ETIMEOUT and the context stays usable. */
+krp_status krp_debug_wait_timeout(krp_sampler* s, int tries);
+
 /* Message for the most recent failure on this sampler; never NULL. */
 const char* krp_last_error(const krp_sampler* s);
 

@@ -82,8 +82,8 @@ __device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t
 // Bounded wait for the mbarrier phase `parity`; false if it did not complete.
 // Each try_wait may suspend the warp for up to ~0.1 ms (the hint), so the
 // loop spins little; 1<<16 tries bound the wait to a few seconds.
-__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity) {
-    for (int it = 0; it < (1 << 16); ++it) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int max_tries = 1 << 16) {
+    for (int it = 0; it < max_tries; ++it) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -502,6 +502,24 @@ cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 }  // namespace
+
+// Test hook for the bounded wait: one warp waits on an mbarrier that nothing
+// completes, with `tries` suspending tries, and must report KRP_ETIMEOUT.
+__global__ void wait_timeout_probe(int tries, int* status) {
+    __shared__ __align__(8) uint64_t mbar;
+    if (threadIdx.x == 0) {
+        mbar_init(&mbar);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const bool done = mbar_wait(&mbar, 0u, tries);
+    if (!__all_sync(0xffffffffu, done) && threadIdx.x == 0) set_status(status, KRP_ETIMEOUT);
+}
+
+cudaError_t launch_wait_timeout_probe(krp_sampler* s, int tries) {
+    wait_timeout_probe<<<1, 32, 0, s->stream>>>(tries, s->status); count_launch();
+    return cudaGetLastError();
+}
 
 bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
                          float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err) {

@@ -294,6 +294,12 @@ krp_status krp_sync_status(krp_sampler* s) {
 
 int64_t krp_launch_count(void) { return krp::launch_counter(); }
 
+krp_status krp_debug_wait_timeout(krp_sampler* s, int tries) {
+    if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");
+    if (tries < 1 || tries > 1000) return fail(s, KRP_EINVAL, "krp_debug_wait_timeout: need 1 <= tries <= 1000");
+    return cuda_check(s, launch_wait_timeout_probe(s, tries), "wait probe launch");
+}
+
 const char* krp_last_error(const krp_sampler* s) { return s ? s->last_error.c_str() : g_error.c_str(); }
 
 krp_status krp_tree_info(const krp_sampler* s, int j, int64_t* L_host, int* depth_host, int* node_stride_host) {

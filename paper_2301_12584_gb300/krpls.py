@@ -35,6 +35,7 @@ SIGNATURES = [
     ("krp_sample_prepare", _INT, [_P, _INT]),
     ("krp_sample_draw", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_launch_count", _I64, []),
+    ("krp_debug_wait_timeout", _INT, [_P, _INT]),
     ("krp_gather", _INT, [_P, _INT, _I64, _P, _P, _P]),
     ("krp_solve_dense", _INT, [_P, _I64, _P, _P, _P, _INT, _P, _INT]),
     ("krp_sptensor_create", _INT, [C.POINTER(_P), _INT, C.POINTER(_I64), _I64, C.POINTER(_P), _P, _P]),
@@ -163,6 +164,9 @@ class Sampler:
         out = C.c_double()
         self._check(self._lib.krp_cp_fit(self.h, tensor.h, _P(_ptr(sigma)), C.byref(out)))
         return out.value
+
+    def debug_wait_timeout(self, tries):
+        self._check(self._lib.krp_debug_wait_timeout(self.h, int(tries)))
 
     def sync_status(self):
         """Synchronise and return the device status code (0 = OK)."""
