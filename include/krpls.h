@@ -146,6 +146,29 @@ krp_status krp_gather(krp_sampler* s, int exclude_j, int64_t J, const int32_t* i
 krp_status krp_solve_dense(krp_sampler* s, int64_t J, const float* SA, const float* weight,
                            const float* B_rows, int nrhs, float* X, int flags);
 
+/* krp_solve_dense without any device allocation (no counterpart in the paper;
+ * it is the same Thm 2.1 solve, by the same kernels).  For callers that may
+ * not allocate device memory: a host framework that owns all of it through its
+ * own pool, or a loop under a memory budget where an allocation could fail or
+ * stall the device.  Needs no sampler.
+ *   J: sampled rows, 1 <= J < 2^31.  R: 1..32.  nrhs: 1..16.
+ *   SA (J x R), weight (J), B_rows (J x nrhs), X (R x nrhs out): device,
+ *   row-major FP32, caller-owned, as for krp_solve_dense.
+ *   status: caller-owned device int; the call sets it to zero on `stream`
+ *   before its kernels, which raise it to KRP_ESINGULAR (X zero) if M is not
+ *   positive definite and flags lacks KRP_PINV_FALLBACK.
+ *   stream: cudaStream_t (NULL = legacy default stream).
+ * Scratch: a fixed 2.13 MB array in the library's device image (512 partial
+ * sums of SAᵀSA and SAᵀSB), needing no initial value.  R > 32 or nrhs > 16 is
+ * rejected with KRP_EINVAL (message in krp_last_error(NULL)).  The first call
+ * on each device looks up the array's device address (which may load the
+ * library's device code), so make it before capturing any stream.  All calls
+ * on one device share the array: calls that overlap in time (other streams,
+ * other host threads) race on it and must be serialised by the caller.
+ * Returns KRP_OK once both kernels are enqueued. */
+krp_status krp_solve_dense_noalloc(int64_t J, int R, const float* SA, const float* weight, const float* B_rows,
+                                   int nrhs, float* X, int flags, int* status, void* stream);
+
 /* ------------------------------------------------------------------------
  * Sparse tensors and STS-CP (Sec. 3.3; Alg. 6 CP-ALS; App. A.9).
  *

@@ -38,6 +38,7 @@ SIGNATURES = [
     ("krp_debug_wait_timeout", _INT, [_P, _INT]),
     ("krp_gather", _INT, [_P, _INT, _I64, _P, _P, _P]),
     ("krp_solve_dense", _INT, [_P, _I64, _P, _P, _P, _INT, _P, _INT]),
+    ("krp_solve_dense_noalloc", _INT, [_I64, _INT, _P, _P, _P, _INT, _P, _INT, _P, _P]),
     ("krp_sptensor_create", _INT, [C.POINTER(_P), _INT, C.POINTER(_I64), _I64, C.POINTER(_P), _P, _P]),
     ("krp_sptensor_destroy", None, [_P]),
     ("krp_solve_sparse", _INT, [_P, _P, _INT, _I64, _P, _P, _P, _P, _INT]),
@@ -202,6 +203,17 @@ class Sampler:
 def launch_count():
     """Kernels launched by libkrpls in this process so far."""
     return int(lib().krp_launch_count())
+
+
+def solve_dense_noalloc(J, R, SA, weight, B_rows, nrhs, X, status, flags=0, stream=None):
+    """krp_solve_dense_noalloc: the dense solve with the library's fixed device
+    scratch (R <= 32, nrhs <= 16); `status` is a device int32 the call clears
+    and the kernels may raise.  Enqueues only; raises KrpError on a rejected call."""
+    L = lib()
+    rc = L.krp_solve_dense_noalloc(int(J), int(R), _P(_ptr(SA)), _P(_ptr(weight)), _P(_ptr(B_rows)), int(nrhs),
+                                   _P(_ptr(X)), int(flags), _P(_ptr(status)), _P(_stream_ptr(stream)))
+    if rc != 0:
+        raise KrpError(rc, L.krp_last_error(None).decode())
 
 
 class SparseTensor:
