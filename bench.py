@@ -32,6 +32,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 N_FACT, I_ROWS, RANK, LEAF, J_DRAW = 3, 1 << 22, 32, 32, 1 << 16
+# dram__bytes_read.sum + dram__bytes_write.sum of one krp_descent_fast<32> launch of this
+# workload (one-pass ncu capture of the first timed draw); to be re-taken whenever that kernel changes.
+DESCENT_DRAM_BYTES = 3_905_536_256 + 12_346_368
 METRIC = "KRP leverage samples/s (one-factor update + prepare + draw + gather per step)"
 UNIT = "samples/s"
 WORKLOAD = "krp_sampler_N3_I2^22_R32_F32_J2^16_update_per_draw"
@@ -164,9 +167,8 @@ def run_reference(args, rank):
 # ------------------------------------------------------------------ ours ----
 def main():
     args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2301_12584_gb300 import replicas
+    rank, local, world = replicas.rank_env()
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist
@@ -202,7 +204,8 @@ def main():
     idx = torch.zeros((N_FACT, J), dtype=torch.int32, device=dev)
     w = torch.zeros(J, dtype=torch.float32, device=dev)
     SA = torch.zeros((J, RANK), dtype=torch.float32, device=dev)
-    draw_base = rank * 1_000_000
+    draws = replicas.draw_ids(rank, 0, args.warmup + args.steps)          # this rank's own Philox draw ids
+    e2e_draws = replicas.draw_ids(rank, 500_000, max(args.e2e_steps, 0))
 
     ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
     phases = []
@@ -217,7 +220,7 @@ def main():
         s.sample_prepare(-1)
         if timed:
             e[2].record(stream)
-        s.sample_draw(-1, J, 1, draw_base + d, idx, w, None, SA)
+        s.sample_draw(-1, J, 1, draws[d], idx, w, None, SA)
         if timed:
             e[3].record(stream)
             phases.append(e)
@@ -247,13 +250,8 @@ def main():
         n_launch = krpls.launch_count() - n0
         clk = clocks.stop()
     assert s.sync_status() == 0, s.last_error()
-    ms = t_start.elapsed_time(t_end)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    total_samples = J * args.steps * world
-    value = total_samples / (ms / 1e3)
+    ms = replicas.max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
+    value = replicas.whole_job_rate(J * args.steps, world, ms)
     upd = statistics.mean(p[0].elapsed_time(p[1]) for p in phases)
     prep = statistics.mean(p[1].elapsed_time(p[2]) for p in phases)
     drw = statistics.mean(p[2].elapsed_time(p[3]) for p in phases)
@@ -269,11 +267,14 @@ def main():
     depth = (I_ROWS // LEAF - 1).bit_length()
     bytes_per_sample = N_FACT * (4 * T * depth + 4 * LEAF * RANK)     # nominal tree path + leaf block
     achieved = bytes_per_sample * J / (drw / 1e3) / 1e9
-    roof = {"kernel": "krp_descent<32,1>", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": None,
+    roof = {"kernel": "krp_descent_fast<32>", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": DESCENT_DRAM_BYTES,
+            "traffic_frac": DESCENT_DRAM_BYTES / (drw / 1e3) / 1e9 / hbm,
             "algorithmic_bytes_per_launch": bytes_per_sample * J,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
-            "note": "nominal bytes: every sample reads its full root-to-leaf path; upper levels are L2 hits"}
+            "note": ("achieved/frac: nominal bytes (every sample reads its full root-to-leaf path); "
+                     "traffic: ncu DRAM bytes per launch (upper levels are L2 hits); traffic_frac: that "
+                     "traffic over the live launch time, against the same peak")}
     # tree rebuild (update) roofline, informational
     L = 1 << depth
     build_bytes = I_ROWS * RANK * 4 + L * ((T + 7) // 8 * 8) * 4 + 2 * I_ROWS * RANK * 4
@@ -292,17 +293,13 @@ def main():
             for d in range(args.e2e_steps):
                 k = d % N_FACT
                 s.set_factor(k, Fh[k].data_ptr())               # H2D of the step's input from pinned host
-                s.sample(-1, J, 1, draw_base + 500_000 + d, idx, w, None, SA)
+                s.sample(-1, J, 1, e2e_draws[d], idx, w, None, SA)
                 idx_h.copy_(idx, non_blocking=True)            # D2H of the step's result
                 w_h.copy_(w, non_blocking=True)
             b.record(stream)
             torch.cuda.synchronize()
-        e_ms = a.elapsed_time(b)
-        if dist:
-            t = torch.tensor([e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": J * args.e2e_steps * world / (e_ms / 1e3), "unit": UNIT,
+        e_ms = replicas.max_over_ranks(a.elapsed_time(b), dist, dev)
+        e2e = {"value": replicas.whole_job_rate(J * args.e2e_steps, world, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": I_ROWS * RANK * 4, "d2h_bytes_per_step": J * (N_FACT * 4 + 4)}
 
     cpu = None

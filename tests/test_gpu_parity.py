@@ -113,7 +113,8 @@ def test_tree_matches_partial_grams(I, R, F):
 
 
 # -------------------------------------------------- sampler index parity ----
-@pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1"])
+@pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1",
+                                  "R64_N4", "R128"])
 def test_sampler_index_parity(case):
     J = 1 << 15
     excl = -1
@@ -136,10 +137,14 @@ def test_sampler_index_parity(case):
         Us, F, J = synth.skewed_row_factors(3, 2000, 32, seed=9), 32, 1 << 16
     elif case == "F1":
         Us, F = synth.gaussian_factors(2, 40, 4, seed=10), 1
+    elif case == "R64_N4":    # the R sweep's distribution (U(-1,1), N=4, F=R) at small I
+        Us, F, J = synth.uniform_factors(4, 200, 64, seed=11), 64, 1 << 12
+    elif case == "R128":
+        Us, F, J = synth.uniform_factors(3, 300, 128, seed=12), 128, 1 << 11
     s = sampler_for(Us, F)
     out = draw(s, Us, excl, J, seed=12345, draw_id=3, logq=True)
     U64 = [U.astype(np.float64) for U in Us]
-    ref = O.krp_sample(U64, excl, J, 12345, 3, record=True)
+    ref = O.krp_sample(U64, excl, J, 12345, 3, record=True, chunk=2048)
     if case == "R32":
         mism = check_index_parity(out["idx"], ref, J, tol=2e-7)
         assert mism <= 2e-3 * J, f"{mism} mismatches of {J}"
