@@ -19,6 +19,11 @@
 // line 2 with the symmetric triangle read once.
 // Epilogue: ℓ_s = hᵀ G⁺ h, q_s = ℓ_s / rank, w_s = 1/sqrt(J q_s) (Sec. 2.1),
 // and optionally SA[s,:] = w_s h (the gather, fused).
+// Precision: the history h and h̃ are carried as double-float (FP32 pairs); the
+// target tau and the running left edge `low` are double-float; each branch is
+// decided on the FP32 mass unless tau lies within 1e-6 of the stage's root mass
+// of the cutoff, and then on the team's double-float sum of the per-thread
+// partials.  The leaf scan is redone in double-float in the same case.
 #include "common.cuh"
 #include "internal.h"
 
@@ -31,6 +36,7 @@ struct DescentParams {
     const float* tree[16];   // Z_k
     const float* etree[16];  // E_k
     const float* V32[16];    // eigenvectors of G_{>k}, row u
+    const float* V32lo[16];  // their FP32 residuals (double-float eigenvectors)
     int64_t I[16];
     int64_t L[16];
     int depth[16];
@@ -78,8 +84,10 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
     constexpr int NT = C::THREADS;
     __shared__ uint8_t s_i[C::TMAX], s_j[C::TMAX];
     __shared__ __align__(16) float s_h[C::TEAMS_PER_CTA][RMAX];
+    __shared__ __align__(16) float s_hl[C::TEAMS_PER_CTA][RMAX];
     __shared__ __align__(16) float s_ht[C::TEAMS_PER_CTA][RMAX];
     __shared__ float s_red[C::TEAMS_PER_CTA][TEAM];
+    __shared__ float s_red2[C::TEAMS_PER_CTA][TEAM][2];
     __shared__ float s_scan[C::TEAMS_PER_CTA][TEAM];
     __shared__ int s_pick[C::TEAMS_PER_CTA][2];
 
@@ -102,6 +110,7 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
     const int lane = threadIdx.x & 31;
     const int wib = tid >> 5;  // warp in team
     float* h = s_h[team];
+    float* hl = s_hl[team];
     float* ht = s_ht[team];
 
     auto team_sum = [&](float v) -> float {
@@ -130,19 +139,46 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
             wgt[e] = w;
         }
     };
-    auto node_mass = [&](const float* __restrict__ node) -> float {
+    // Team double-float sum of per-thread FP32 partials (identical in every thread).
+    auto team_sum_df = [&](float part) -> df {
+        df v = warp_sum_df(df{part, 0.f});
+        if (TEAM == 1) return v;
+        if (lane == 0) {
+            s_red2[team][wib][0] = v.hi;
+            s_red2[team][wib][1] = v.lo;
+        }
+        TeamSync<TEAM>::sync(team);
+        df t{0.f, 0.f};
+#pragma unroll
+        for (int w = 0; w < TEAM; ++w) t = df_add(t, df{s_red2[team][w][0], s_red2[team][w][1]});
+        TeamSync<TEAM>::sync(team);
+        return t;
+    };
+    auto node_part = [&](const float* __restrict__ node) -> float {
         float acc = 0.f;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int p = tid + NT * e;
             if (p < Tp) acc = fmaf(wgt[e], __ldg(node + p), acc);
         }
-        return team_sum(acc);
+        return acc;
+    };
+    // "tau <= low + m" (Alg. 4): FP32 mass unless tau is within `margin` of the
+    // cutoff, then the double-float mass.  Every operand is team-uniform.
+    auto go_left = [&](df tau, df low, float m, float part, float margin, df& cut) -> bool {
+        cut = df_add(low, df{m, 0.f});
+        const df gap = df_add(tau, df_neg(cut));
+        if (fabsf(gap.hi) > margin) return gap.hi < 0.f;
+        cut = df_add(low, team_sum_df(part));
+        return df_le(tau, cut);
     };
 
     const int64_t total_teams = (int64_t)gridDim.x * C::TEAMS_PER_CTA;
     for (int64_t s = (int64_t)blockIdx.x * C::TEAMS_PER_CTA + team; s < P.J; s += total_teams) {
-        for (int a = tid; a < RMAX; a += NT) h[a] = (a < R) ? 1.f : 0.f;
+        for (int a = tid; a < RMAX; a += NT) {
+            h[a] = (a < R) ? 1.f : 0.f;
+            hl[a] = 0.f;
+        }
         TeamSync<TEAM>::sync(team);
         bool ok = true;
         for (int pi = 0; pi < P.n_incl; ++pi) {
@@ -153,13 +189,15 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
             // ---------------- eigencomponent stage (E_k, leaf size 1)
             make_weights(h);
             const float* et = P.etree[k];
-            float Cm = node_mass(et);
+            df Cd = team_sum_df(node_part(et));
+            float Cm = Cd.hi + Cd.lo;
             if (!(Cm > 0.f) || !isfinite(Cm)) {
                 if (tid == 0) set_status(P.status, isfinite(Cm) ? KRP_EZERO : KRP_ENUMERIC);
                 ok = false;
                 break;
             }
-            float tau = u_eig * Cm, low = 0.f;
+            df tau = df_mul_f(Cd, u_eig), low{0.f, 0.f}, cut;
+            float margin = 1e-6f * Cm;
             int64_t c = 1;
             float* trc = (P.trace && s < P.n_trace && tid == 0)
                              ? P.trace + ((s * P.n_incl + pi) * 2 + 0) * TRACE_STRIDE
@@ -167,14 +205,14 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
             float mnode = Cm;
             if (trc) trc[0] = Cm;
             for (int lvl = 0; lvl < P.dE; ++lvl) {
-                const float mL = node_mass(et + c * Tp);
-                const float cut = low + mL;
+                const float part = node_part(et + c * Tp);
+                const float mL = team_sum(part);
                 if (trc) {
                     trc[2 + 2 * lvl] = mL;
                     trc[3 + 2 * lvl] = mnode;
                 }
                 const int64_t rfirst = ((2 * c + 1) << (P.dE - lvl - 1)) - P.Rp;  // first leaf of right child
-                if (tau <= cut || rfirst >= R) {
+                if (rfirst >= R || go_left(tau, low, mL, part, margin, cut)) {
                     c = 2 * c;
                     mnode = mL;
                 } else {
@@ -186,18 +224,29 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
             const int u = (int)(c - P.Rp);
             // ---------------- row stage (Z_k, leaf size F, Y = [1])
             const float* Vu = P.V32[k] + (size_t)u * R;
-            for (int a = tid; a < RMAX; a += NT) ht[a] = (a < R) ? h[a] * __ldg(Vu + a) : 0.f;
+            const float* Vul = P.V32lo[k] + (size_t)u * R;
+            for (int a = tid; a < RMAX; a += NT) {
+                float v = 0.f;
+                if (a < R) {  // h̃ = h ∘ V[:,u] from double-float factors, rounded once
+                    const df hd{h[a], hl[a]};
+                    const df t = df_add(df_mul_f(hd, __ldg(Vu + a)), df_mul_f(hd, __ldg(Vul + a)));
+                    v = t.hi + t.lo;
+                }
+                ht[a] = v;
+            }
             TeamSync<TEAM>::sync(team);
             make_weights(ht);
             const float* tr = P.tree[k];
-            Cm = node_mass(tr);
+            Cd = team_sum_df(node_part(tr));
+            Cm = Cd.hi + Cd.lo;
             if (!(Cm > 0.f) || !isfinite(Cm)) {
                 if (tid == 0) set_status(P.status, isfinite(Cm) ? KRP_EZERO : KRP_ENUMERIC);
                 ok = false;
                 break;
             }
-            tau = u_row * Cm;
-            low = 0.f;
+            tau = df_mul_f(Cd, u_row);
+            low = df{0.f, 0.f};
+            margin = 1e-6f * Cm;
             c = 1;
             const int64_t Lk = P.L[k], Ik = P.I[k];
             const int dk = P.depth[k];
@@ -206,14 +255,14 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
             mnode = Cm;
             if (trc) trc[0] = Cm;
             for (int lvl = 0; lvl < dk; ++lvl) {
-                const float mL = node_mass(tr + c * Tp);
-                const float cut = low + mL;
+                const float part = node_part(tr + c * Tp);
+                const float mL = team_sum(part);
                 const int64_t rfirst = ((2 * c + 1) << (dk - lvl - 1)) - Lk;
                 if (trc) {
                     trc[2 + 2 * lvl] = mL;
                     trc[3 + 2 * lvl] = mnode;
                 }
-                if (tau <= cut || rfirst * F >= Ik) {
+                if (rfirst * F >= Ik || go_left(tau, low, mL, part, margin, cut)) {
                     c = 2 * c;
                     mnode = mL;
                 } else {
@@ -248,11 +297,10 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
                         for (int a = 0; a < R; ++a) d = fmaf(__ldg(row + a), ht[a], d);
                     }
                 }
-                q[r] = d * d;
+                q[r] = (r < rpt && t < nrows) ? d * d : 0.f;
                 run += q[r];
-                q[r] = run;  // thread-local inclusive prefix
             }
-            // team exclusive scan of the per-thread totals
+            // team exclusive scan of the per-thread totals (FP32)
             float incl_scan = run;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -269,18 +317,66 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
                 base += off;
                 TeamSync<TEAM>::sync(team);
             }
-            // first row with low + cum >= tau; else the last row with weight > 0
+            // first row whose right edge low + cum reaches tau; else the last row with weight > 0
+            const df rel = df_add(tau, df_neg(low));
+            const float target = rel.hi + rel.lo;
             int first = 0x7fffffff, lastpos = -1;
-            float prev = base;
+            bool near = false;
+            float cum = base;
 #pragma unroll
             for (int r = 0; r < C::RPT; ++r) {
                 const int t = tid * rpt + r;
-                const float cum = base + q[r];
                 if (r < rpt && t < nrows) {
-                    if (first == 0x7fffffff && low + cum >= tau) first = t;
-                    if (cum > prev) lastpos = t;
+                    cum += q[r];
+                    if (first == 0x7fffffff && target <= cum) first = t;
+                    if (fabsf(cum - target) <= margin) near = true;
+                    if (q[r] > 0.f) lastpos = t;
                 }
-                prev = cum;
+            }
+            int any_near = __any_sync(0xffffffffu, near) ? 1 : 0;
+            if (TEAM > 1) {
+                if (tid == 0) s_pick[team][0] = 0;
+                TeamSync<TEAM>::sync(team);
+                if (lane == 0 && any_near) atomicOr(&s_pick[team][0], 1);
+                TeamSync<TEAM>::sync(team);
+                any_near = s_pick[team][0];
+                TeamSync<TEAM>::sync(team);
+            }
+            if (any_near) {
+                // redo the scan in double-float: edges low + cumulative weights
+                df acc{0.f, 0.f};
+#pragma unroll
+                for (int r = 0; r < C::RPT; ++r) acc = df_add(acc, df{q[r], 0.f});
+                df incd = acc;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const float vh = __shfl_up_sync(0xffffffffu, incd.hi, o);
+                    const float vl = __shfl_up_sync(0xffffffffu, incd.lo, o);
+                    if (lane >= o) incd = df_add(df{vh, vl}, incd);
+                }
+                df cd{__shfl_up_sync(0xffffffffu, incd.hi, 1), __shfl_up_sync(0xffffffffu, incd.lo, 1)};
+                if (lane == 0) cd = df{0.f, 0.f};
+                if (TEAM > 1) {
+                    if (lane == 31) {
+                        s_red2[team][wib][0] = incd.hi;
+                        s_red2[team][wib][1] = incd.lo;
+                    }
+                    TeamSync<TEAM>::sync(team);
+                    df off{0.f, 0.f};
+                    for (int w = 0; w < wib; ++w) off = df_add(off, df{s_red2[team][w][0], s_red2[team][w][1]});
+                    cd = df_add(off, cd);
+                    TeamSync<TEAM>::sync(team);
+                }
+                cd = df_add(cd, low);
+                first = 0x7fffffff;
+#pragma unroll
+                for (int r = 0; r < C::RPT; ++r) {
+                    const int t = tid * rpt + r;
+                    if (r < rpt && t < nrows) {
+                        cd = df_add(cd, df{q[r], 0.f});
+                        if (first == 0x7fffffff && df_le(tau, cd)) first = t;
+                    }
+                }
             }
 #pragma unroll
             for (int m = 16; m > 0; m >>= 1) {
@@ -308,13 +404,18 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
                 t_sel = 0;
             }
             const int64_t trow = row0 + t_sel;
-            for (int a = tid; a < R; a += NT) h[a] *= __ldg(Uk + trow * R + a);
+            for (int a = tid; a < R; a += NT) {
+                const df nh = df_mul_f(df{h[a], hl[a]}, __ldg(Uk + trow * R + a));
+                h[a] = nh.hi;
+                hl[a] = nh.lo;
+            }
             if (tid == 0) P.idx[(int64_t)k * P.J + s] = (int32_t)trow;
             TeamSync<TEAM>::sync(team);
         }
         // ---------------- epilogue: probability, weight, fused gather
         make_weights(h);
-        const float lev = node_mass(P.Gplus32);
+        const df levd = team_sum_df(node_part(P.Gplus32));
+        const float lev = levd.hi + levd.lo;
         const float qs = lev / (float)(*P.rank);
         const float w = ok ? 1.0f / sqrtf((float)P.J * qs) : 0.f;
         if (tid == 0) {
@@ -353,6 +454,7 @@ krp_status launch_descent(krp_sampler* s, int exclude_j, int64_t J, uint64_t see
         P.tree[k] = s->tree[k];
         P.etree[k] = s->etree + (size_t)k * s->Rp * s->Tp;
         P.V32[k] = s->V32 + (size_t)k * s->R * s->R;
+        P.V32lo[k] = s->V32lo + (size_t)k * s->R * s->R;
         P.I[k] = s->I[k];
         P.L[k] = s->L[k];
         P.depth[k] = s->depth[k];

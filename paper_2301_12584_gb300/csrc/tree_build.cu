@@ -19,6 +19,7 @@
 // levels above, until the root.
 #include "common.cuh"
 #include "internal.h"
+#include "tree_reduce.cuh"
 
 #include <algorithm>
 
@@ -104,66 +105,6 @@ __device__ __forceinline__ void leaf_grams_fp32(const float* sU, float* sG, int 
                 const int i = 4 * ti + x, j = 4 * tj + y;
                 if (i <= j && j < R) g[tri_index(i, j, R)] = acc[x][y];
             }
-    }
-}
-
-__device__ __forceinline__ void store_node(float* __restrict__ tree, int64_t h, int Tp, int e, float v) {
-    if (tree_stored(h)) tree[tree_slot(h) * Tp + e] = v;
-}
-
-// Double-float addition (Knuth TwoSum, then a fast renormalisation): the pair
-// (hi, lo) carries the sum to about 2^-44 relative, so that the sums above the
-// leaves add no rounding error of their own; hi is the FP32-rounded sum.
-__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
-    const float s = ah + bh;
-    const float bb = s - ah;
-    const float err = (ah - (s - bb)) + (bh - bb);
-    const float t = err + al + bl;
-    h = s + t;
-    l = t - (h - s);
-}
-
-// Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
-// merge across the CTA's groups, all in double-float.  Stores the FP32 value of
-// every left child created; the CTA's subtree root goes to top as (hi, lo).
-template <int LB>
-__device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
-                                             float* __restrict__ top, int64_t L, int64_t first_leaf,
-                                             int g, int G, int Tp) {
-    for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
-        float vh[LB], vl[LB];
-#pragma unroll
-        for (int l = 0; l < LB; ++l) {
-            vh[l] = sG[l * Tp + e];
-            vl[l] = 0.f;
-        }
-        int64_t h = L + first_leaf;
-#pragma unroll
-        for (int l = 0; l < LB; ++l) store_node(tree, h + l, Tp, e, vh[l]);
-#pragma unroll
-        for (int n = LB; n > 1; n >>= 1) {
-            h >>= 1;
-#pragma unroll
-            for (int l = 0; l < n / 2; ++l) {
-                df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
-                store_node(tree, h + l, Tp, e, vh[l]);
-            }
-        }
-        float hi = vh[0], lo = vl[0];
-        int idx = g, lvl = 0;
-        while (idx & 1) {
-            df_add(stk[(2 * lvl) * Tp + e], stk[(2 * lvl + 1) * Tp + e], hi, lo, hi, lo);
-            h >>= 1;
-            idx >>= 1;
-            ++lvl;
-            store_node(tree, h, Tp, e, hi);
-        }
-        stk[(2 * lvl) * Tp + e] = hi;
-        stk[(2 * lvl + 1) * Tp + e] = lo;
-        if (g == G - 1) {
-            top[((size_t)blockIdx.x * 2) * Tp + e] = hi;
-            top[((size_t)blockIdx.x * 2 + 1) * Tp + e] = lo;
-        }
     }
 }
 
@@ -295,9 +236,12 @@ __global__ void gram64_finish(const double* __restrict__ part, int nparts, int T
     }
 }
 
-// BF16x3 tensor-core leaf kernel (tree_build_tc.cu); returns false if the
-// shape is not supported there (caller falls back to FP32).
-bool launch_tree_leaves_tc(krp_sampler* s, int j, int LB, int G, int64_t ctas, float* top, size_t smem_fp32);
+// BF16x3 tensor-core leaf kernel (tree_build_tc.cu).
+bool tree_tc_supported(int R, int F);
+void tree_tc_geometry(int R, int F, int64_t L, int Tp, int* LB_out, int* G_out, size_t* smem_out);
+cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
+                                  float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
+                                  cudaStream_t st);
 
 namespace {
 
@@ -352,9 +296,13 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     const int R = s->R, F = s->F, Tp = s->Tp;
     const int64_t I = s->I[j], L = s->L[j];
     const bool vec = (R % 4) == 0;
-    int LB, G, threads;
+    const bool tc = precision == KRP_PREC_BF16X3 && tree_tc_supported(R, F);
+    int LB, G, threads = 128;
     size_t smem;
-    tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem);
+    if (tc)
+        tree_tc_geometry(R, F, L, Tp, &LB, &G, &smem);
+    else
+        tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem);
     const int64_t ctas = L / ((int64_t)LB * G);
     const int T = tri_size(R);
     const bool exact_root = (double)I * T <= (double)(1 << 22);
@@ -375,9 +323,11 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     float* top = s->build_scratch;
     double* up0 = reinterpret_cast<double*>(s->build_scratch + pairs);  // pairs is even: 8-byte aligned
     double* up1 = up0 + (size_t)(ctas / 2 + 2) * Tp;
-    bool done = false;
-    if (precision == KRP_PREC_BF16X3) done = launch_tree_leaves_tc(s, j, LB, G, ctas, top, smem);
-    if (!done) {
+    if (tc) {
+        const cudaError_t e = launch_tree_leaves_tc(src, I, R, F, L, LB, G, Tp, s->tree[j], top, copy_to, s->status,
+                                                    ctas, smem, s->stream);
+        if (e != cudaSuccess) return cuda_check(s, e, "tensor-core tree leaf kernel launch");
+    } else {
         cudaError_t e;
         switch (LB) {
             case 1: e = dispatch_vec<1>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;

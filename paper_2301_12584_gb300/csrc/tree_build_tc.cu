@@ -1,13 +1,305 @@
-// a1 (split precision): leaf Grams on tcgen05 tensor cores, BF16 hi/lo
-// split with three products and FP32 accumulation in TMEM.
+// a1 (split precision): leaf Grams G^v = U[S(v)]ᵀU[S(v)] of the segment tree
+// (Alg. 3, Eq. partial_gram) on the tcgen05 tensor cores.
+//
+// Each FP32 entry x is split into BF16 parts x = hi + lo + O(2^-17 |x|)
+// (hi = bf16(x), lo = bf16(x - hi)); a Gram is formed as
+// hiᵀhi + hiᵀlo + loᵀhi with FP32 accumulation in tensor memory, so each
+// product carries about 16 significant bits against FP32's 24 (the dropped
+// loᵀlo term and the rounding of lo are each below 2^-17 |x||y|).
+//
+// One 128 x 128 x Fp product places 128/RP leaves side by side (RP = R padded
+// to 16, 32, 64 or 128): row block b of both operands holds leaf b transposed
+// (its R columns along M or N, its F rows along K, zero padding), so block
+// (b, b) of the product is leaf b's Gram and the off-diagonal blocks are
+// discarded.  The operand tile is written once, K-major in 8 x 16-byte core
+// matrices without swizzle, and serves as both A and B.  Warp w reads TMEM
+// lanes 32w..32w+31, i.e. rows of the Gram of the leaf those lanes hold, and
+// writes their upper triangles into the group's leaf array; the pairwise
+// double-float sums up the tree are the ones the FP32 kernel uses.
+//
+// Per CTA: 128 threads, 128 TMEM columns; thread 0 issues the MMAs and commits
+// them to an mbarrier that every thread waits on with a bounded number of
+// tries (KRP_ETIMEOUT instead of a hang).  Shared memory is padded to at least
+// 48 KB so that at most four CTAs (4 x 128 = 512 TMEM columns) share an SM.
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 #include "internal.h"
+#include "tree_reduce.cuh"
+
+#include <algorithm>
 
 namespace krp {
+namespace {
 
-bool launch_tree_leaves_tc(krp_sampler* s, int j, int LB, int G, int64_t ctas, float* top, size_t smem_fp32) {
-    (void)s; (void)j; (void)LB; (void)G; (void)ctas; (void)top; (void)smem_fp32;
+constexpr uint32_t TC_COLS = 128;
+// kind::f16 instruction descriptor: D FP32, A and B BF16, both K-major, N = 128, M = 128.
+constexpr uint32_t TC_IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr int TC_WAIT_TRIES = 1 << 16;
+
+__device__ __forceinline__ uint32_t tc_saddr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor, no swizzle: start address, leading-dimension
+// byte offset (between core matrices along K), stride-dimension byte offset
+// (between 8-row groups along M/N), and the fixed version bits 46-48 = 0b001.
+__device__ __forceinline__ uint64_t tc_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(TC_IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc_saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ bool tc_wait(uint64_t* bar, uint32_t parity) {
+    for (int it = 0; it < TC_WAIT_TRIES; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(tc_saddr(bar)), "r"(parity), "r"(100000u)
+            : "memory");
+        if (done) return true;
+    }
     return false;
+}
+
+// 32 lanes x 32 columns of FP32 from TMEM (lane base in bits 31..16 of taddr).
+__device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
+    hi = *reinterpret_cast<const uint32_t*>(&h);
+    lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+template <int RP, int LB>
+__global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ U, int64_t I, int R, int F, int Fp,
+                                                      int64_t L, int G, int Tp, float* __restrict__ tree,
+                                                      float* __restrict__ top, float* __restrict__ copy_to,
+                                                      int* __restrict__ status) {
+    constexpr int NL = 128 / RP;              // leaves side by side in one product
+    constexpr int NCH = (LB + NL - 1) / NL;   // products per group of LB leaves
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int T = tri_size(R);
+    const int nk8 = Fp >> 3;                       // 8-row core-matrix columns along K
+    const uint32_t sbo = (uint32_t)nk8 * 128u;      // bytes per 8-row group along M/N
+    unsigned char* Xh = smem;
+    unsigned char* Xl = smem + 128u * sbo / 8u;     // 128 rows x Fp bf16
+    float* sG = reinterpret_cast<float*>(Xl + 128u * sbo / 8u);
+    float* stk = sG + (size_t)LB * Tp;
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&tmem_base)),
+                     "r"(TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_saddr(&bar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < LB * Tp; e += blockDim.x)
+        if (e % Tp >= T) sG[e] = 0.f;  // packed tail stays zero
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+    bool alive = true;
+    const int64_t leaf0 = (int64_t)blockIdx.x * G * LB;
+
+    for (int g = 0; g < G && alive; ++g) {
+        const int64_t gleaf0 = leaf0 + (int64_t)g * LB;
+        for (int ch = 0; ch < NCH && alive; ++ch) {
+            // operand tile: row p = RP * b + c holds column c of leaf b, K = its rows
+            for (int task = tid; task < 128 * nk8; task += 128) {
+                const int p = task & 127, k8 = task >> 7;
+                const int b = p / RP, c = p % RP;
+                const int ll = ch * NL + b;
+                const int64_t row0 = (gleaf0 + ll) * (int64_t)F + 8 * k8;
+                const bool col_ok = ll < LB && c < R;
+                float v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const int64_t row = row0 + i;
+                    const bool ok = col_ok && 8 * k8 + i < F && row < I;
+                    v[i] = ok ? __ldg(U + row * R + c) : 0.f;
+                    if (ok && copy_to) copy_to[row * R + c] = v[i];
+                }
+                uint4 h, l;
+                split2(v[0], v[1], h.x, l.x);
+                split2(v[2], v[3], h.y, l.y);
+                split2(v[4], v[5], h.z, l.z);
+                split2(v[6], v[7], h.w, l.w);
+                const uint32_t off = (uint32_t)(p >> 3) * sbo + (uint32_t)k8 * 128u + (uint32_t)(p & 7) * 16u;
+                *reinterpret_cast<uint4*>(Xh + off) = h;
+                *reinterpret_cast<uint4*>(Xl + off) = l;
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t xh = tc_saddr(Xh), xl = tc_saddr(Xl);
+                for (int ks = 0; ks < Fp / 16; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256u;  // two 16-byte core-matrix columns per K = 16
+                    tc_mma(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), ks > 0);
+                    tc_mma(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xl + ko, 128u, sbo), 1u);
+                    tc_mma(tmem, tc_desc(xl + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), 1u);
+                }
+                tc_commit(&bar);
+            }
+            const bool ok = tc_wait(&bar, phase);
+            alive = __syncthreads_and(ok) != 0;
+            if (!alive) break;
+            phase ^= 1u;
+            tc_fence_after();
+            const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+            if (RP >= 32) {
+                const int b = (32 * warp) / RP;
+                const int r = (32 * warp + lane) % RP;
+                const int ll = ch * NL + b;
+                float* gr = sG + (size_t)ll * Tp + tri_index(r, r, R) - r;  // &G[r][0] of packed row r
+#pragma unroll 1
+                for (int blk = 0; blk < RP / 32; ++blk) {
+                    float v[32];
+                    tc_ld32(tmem + lane_base + (uint32_t)(b * RP + 32 * blk), v);
+                    if (ll < LB && r < R) {
+#pragma unroll
+                        for (int q = 0; q < 32; ++q) {
+                            const int c = 32 * blk + q;
+                            if (c >= r && c < R) gr[c] = v[q];
+                        }
+                    }
+                }
+            } else {  // RP == 16: lanes 0-15 and 16-31 hold two different leaves
+                float v[32];
+                tc_ld32(tmem + lane_base + (uint32_t)(32 * warp), v);
+                const int half = lane >> 4;
+                const int r = lane & 15;
+                const int ll = ch * NL + 2 * warp + half;
+                if (ll < LB && r < R) {
+                    float* gr = sG + (size_t)ll * Tp + tri_index(r, r, R) - r;
+#pragma unroll
+                    for (int q = 0; q < 32; ++q) {
+                        const int c = q & 15;
+                        if ((q >> 4) == half && c >= r && c < R) gr[c] = v[q];
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncthreads();
+        }
+        if (!alive) break;
+        reduce_group<LB>(sG, stk, tree, top, L, gleaf0, g, G, Tp);
+        __syncthreads();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (!alive) {
+        // an MMA may still be in flight: give it one more bounded wait before freeing TMEM
+        if (tid == 0) tc_wait(&bar, phase);
+        __syncthreads();
+        if (tid == 0) set_status(status, KRP_ETIMEOUT);
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
+    }
+}
+
+int padded_rank(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
+
+size_t tc_smem(int F, int LB, int G, int Tp) {
+    const int Fp = (F + 15) / 16 * 16;
+    int lv = 0;
+    while ((1 << lv) < G) ++lv;
+    const size_t need = (size_t)2 * 128 * Fp * 2 + (size_t)LB * Tp * 4 + (size_t)2 * (lv + 1) * Tp * 4;
+    return std::max<size_t>(need, 48 * 1024);  // at most 4 CTAs (512 TMEM columns) per SM
+}
+
+template <int RP, int LB>
+cudaError_t launch_tc(const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree, float* top,
+                      float* copy_to, int* status, int64_t ctas, size_t smem, cudaStream_t st) {
+    auto k = tree_leaves_tc<RP, LB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int Fp = (F + 15) / 16 * 16;
+    k<<<(unsigned)ctas, 128, smem, st>>>(U, I, R, F, Fp, L, G, Tp, tree, top, copy_to, status); count_launch();
+    return cudaGetLastError();
+}
+
+template <int RP>
+cudaError_t launch_tc_lb(int LB, const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree,
+                         float* top, float* copy_to, int* status, int64_t ctas, size_t smem, cudaStream_t st) {
+    switch (LB) {
+        case 1: return launch_tc<RP, 1>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 2: return launch_tc<RP, 2>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 4: return launch_tc<RP, 4>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 8: return launch_tc<RP, 8>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        default: return launch_tc<RP, 16>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+    }
+}
+
+}  // namespace
+
+bool tree_tc_supported(int R, int F) { return R >= 1 && R <= 128 && F >= 1 && F <= 128; }
+
+// Geometry of the tensor-core leaf kernel: LB leaves per group (power of two,
+// <= 16, <= L, one group's leaf Grams <= 64 KB), G groups per CTA (power of
+// two, <= 8, shared memory <= 200 KB).
+void tree_tc_geometry(int R, int F, int64_t L, int Tp, int* LB_out, int* G_out, size_t* smem_out) {
+    (void)R;
+    int LB = 1;
+    while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * Tp * 4 <= 64 * 1024) LB *= 2;
+    const int64_t groups = L / LB;
+    int G = 1;
+    while (G < 8 && (int64_t)G * 2 <= groups && tc_smem(F, LB, G * 2, Tp) <= 200 * 1024) G *= 2;
+    *LB_out = LB;
+    *G_out = G;
+    *smem_out = tc_smem(F, LB, G, Tp);
+}
+
+cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
+                                  float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
+                                  cudaStream_t st) {
+    switch (padded_rank(R)) {
+        case 16: return launch_tc_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 32: return launch_tc_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 64: return launch_tc_lb<64>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        default: return launch_tc_lb<128>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+    }
 }
 
 }  // namespace krp

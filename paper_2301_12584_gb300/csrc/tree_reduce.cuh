@@ -1,0 +1,70 @@
+// Shared by the leaf kernels of the segment-tree build (Alg. 3): storing a
+// node's packed triangle, double-float addition, and the pairwise sums of one
+// group of leaf Grams continued across groups with a binary-counter stack.
+#pragma once
+
+#include "common.cuh"
+
+namespace krp {
+
+__device__ __forceinline__ void store_node(float* __restrict__ tree, int64_t h, int Tp, int e, float v) {
+    if (tree_stored(h)) tree[tree_slot(h) * Tp + e] = v;
+}
+
+// Double-float addition (Knuth TwoSum, then a fast renormalisation): the pair
+// (hi, lo) carries the sum to about 2^-44 relative, so that the sums above the
+// leaves add no rounding error of their own; hi is the FP32-rounded sum.
+__device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, float& h, float& l) {
+    const float s = ah + bh;
+    const float bb = s - ah;
+    const float err = (ah - (s - bb)) + (bh - bb);
+    const float t = err + al + bl;
+    h = s + t;
+    l = t - (h - s);
+}
+
+// Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
+// merge across the CTA's groups, all in double-float.  Stores the FP32 value of
+// every left child created; the CTA's subtree root goes to top as (hi, lo).
+template <int LB>
+__device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
+                                             float* __restrict__ top, int64_t L, int64_t first_leaf,
+                                             int g, int G, int Tp) {
+    for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
+        float vh[LB], vl[LB];
+#pragma unroll
+        for (int l = 0; l < LB; ++l) {
+            vh[l] = sG[l * Tp + e];
+            vl[l] = 0.f;
+        }
+        int64_t h = L + first_leaf;
+#pragma unroll
+        for (int l = 0; l < LB; ++l) store_node(tree, h + l, Tp, e, vh[l]);
+#pragma unroll
+        for (int n = LB; n > 1; n >>= 1) {
+            h >>= 1;
+#pragma unroll
+            for (int l = 0; l < n / 2; ++l) {
+                df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
+                store_node(tree, h + l, Tp, e, vh[l]);
+            }
+        }
+        float hi = vh[0], lo = vl[0];
+        int idx = g, lvl = 0;
+        while (idx & 1) {
+            df_add(stk[(2 * lvl) * Tp + e], stk[(2 * lvl + 1) * Tp + e], hi, lo, hi, lo);
+            h >>= 1;
+            idx >>= 1;
+            ++lvl;
+            store_node(tree, h, Tp, e, hi);
+        }
+        stk[(2 * lvl) * Tp + e] = hi;
+        stk[(2 * lvl + 1) * Tp + e] = lo;
+        if (g == G - 1) {
+            top[((size_t)blockIdx.x * 2) * Tp + e] = hi;
+            top[((size_t)blockIdx.x * 2 + 1) * Tp + e] = lo;
+        }
+    }
+}
+
+}  // namespace krp

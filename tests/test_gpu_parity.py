@@ -138,15 +138,37 @@ def test_sampler_index_parity(case):
     elif case == "F1":
         Us, F = synth.gaussian_factors(2, 40, 4, seed=10), 1
     elif case == "R64_N4":    # the R sweep's distribution (U(-1,1), N=4, F=R) at small I
-        Us, F, J = synth.uniform_factors(4, 200, 64, seed=11), 64, 1 << 12
+        Us, F, J = synth.uniform_factors(4, 200, 64, seed=11), 64, 1 << 14
     elif case == "R128":
-        Us, F, J = synth.uniform_factors(3, 300, 128, seed=12), 128, 1 << 11
+        Us, F, J = synth.uniform_factors(3, 300, 128, seed=12), 128, 1 << 12
     s = sampler_for(Us, F)
     out = draw(s, Us, excl, J, seed=12345, draw_id=3, logq=True)
     U64 = [U.astype(np.float64) for U in Us]
-    ref = O.krp_sample(U64, excl, J, 12345, 3, record=True, chunk=2048)
+    eig = None
+    if case == "R128":
+        # G_{>k} has 128 eigenvalues within a factor 1.3 (relative gaps down to
+        # 2e-6): the eigenbasis inside such clusters is not pinned (reading C6),
+        # while any decomposition G_{>k} = sum_u lam_u v_u v_uᵀ yields the same
+        # distribution.  The oracle replays the GPU's decomposition after
+        # checking that it reconstructs its own G_{>k} (one FP64 refinement of
+        # the FP32 Jacobi basis leaves up to ~2e-7 of max |G_{>k}| on this
+        # clustered spectrum).
+        prep = O.SamplerPrep(U64, excl)
+        eig = {}
+        for k in prep.incl:
+            lam, V, _, _ = s.get_prep(k)
+            rec = (V * np.maximum(lam, 0.0)) @ V.T
+            assert np.abs(rec - prep.Ggt[k]).max() <= 1e-6 * np.abs(prep.Ggt[k]).max()
+            eig[k] = (lam, V)
+    ref = O.krp_sample(U64, excl, J, 12345, 3, record=True, chunk=2048, eig_override=eig)
     if case == "R32":
         mism = check_index_parity(out["idx"], ref, J, tol=2e-7)
+        assert mism <= 2e-3 * J, f"{mism} mismatches of {J}"
+    elif case in ("R64_N4", "R128"):
+        # FP32 tree storage: a mass is off by ~6e-8 x (sum of |terms|), and with
+        # R^2 terms of both signs that sum exceeds the mass itself; flips stay
+        # within 1e-5 C of an edge, at a rate like the R32 case's
+        mism = check_index_parity(out["idx"], ref, J)
         assert mism <= 2e-3 * J, f"{mism} mismatches of {J}"
     else:
         mism = check_index_parity(out["idx"], ref, J)
