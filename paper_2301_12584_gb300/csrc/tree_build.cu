@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restri
         if (copy_to) copy_rows_out<VEC>(cur, copy_to, I, R, (leaf0 + (int64_t)g * LB) * F, rows);
         leaf_grams_fp32<LB, VEC>(cur, sG, R, F, Tp);
         __syncthreads();
-        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp);
+        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blockIdx.x);
         if (!VEC && g + 1 < G) {
             __syncthreads();
             stage_rows<VEC>(sU0, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);
@@ -238,10 +238,11 @@ __global__ void gram64_finish(const double* __restrict__ part, int nparts, int T
 
 // BF16x3 tensor-core leaf kernel (tree_build_tc.cu).
 bool tree_tc_supported(int R, int F);
-void tree_tc_geometry(int R, int F, int64_t L, int Tp, int* LB_out, int* G_out, size_t* smem_out);
+bool tree_tc_pipelined(int R, int F, const float* U);
+void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out);
 cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
                                   float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
-                                  cudaStream_t st);
+                                  bool pipelined, int num_sms, cudaStream_t st);
 
 namespace {
 
@@ -297,10 +298,11 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     const int64_t I = s->I[j], L = s->L[j];
     const bool vec = (R % 4) == 0;
     const bool tc = precision == KRP_PREC_BF16X3 && tree_tc_supported(R, F);
+    const bool tc_pipe = tc && tree_tc_pipelined(R, F, src);
     int LB, G, threads = 128;
     size_t smem;
     if (tc)
-        tree_tc_geometry(R, F, L, Tp, &LB, &G, &smem);
+        tree_tc_geometry(R, F, L, Tp, tc_pipe, &LB, &G, &smem);
     else
         tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem);
     const int64_t ctas = L / ((int64_t)LB * G);
@@ -325,7 +327,7 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     double* up1 = up0 + (size_t)(ctas / 2 + 2) * Tp;
     if (tc) {
         const cudaError_t e = launch_tree_leaves_tc(src, I, R, F, L, LB, G, Tp, s->tree[j], top, copy_to, s->status,
-                                                    ctas, smem, s->stream);
+                                                    ctas, smem, tc_pipe, s->num_sms, s->stream);
         if (e != cudaSuccess) return cuda_check(s, e, "tensor-core tree leaf kernel launch");
     } else {
         cudaError_t e;

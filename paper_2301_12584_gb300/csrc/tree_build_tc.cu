@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ 
             __syncthreads();
         }
         if (!alive) break;
-        reduce_group<LB>(sG, stk, tree, top, L, gleaf0, g, G, Tp);
+        reduce_group<LB>(sG, stk, tree, top, L, gleaf0, g, G, Tp, blockIdx.x);
         __syncthreads();
     }
 
@@ -236,6 +236,262 @@ __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ 
     if (warp == 0) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TC_COLS) : "memory");
+    }
+}
+
+// Persistent, pipelined form for R <= 32 with R % 4 == 0 and F <= 32 (the
+// sampler-at-scale shape).  A CTA walks blocks of G groups of LB leaves
+// (block v covers leaves [v G LB, (v+1) G LB) and leaves its subtree root in
+// top slot v), in chunks of 128/RP leaves: one chunk's rows are one
+// contiguous run of U (<= 16 KB), brought in by a bulk copy S chunks ahead.
+// Iteration i: wait for chunk i's rows, split them into the operand buffer
+// (i mod 2) and write the factor copy; thread 0 then refills the stage with
+// chunk i+S and issues chunk i's MMAs into TMEM buffer (i mod 2); meanwhile
+// the warps wait for chunk i-1's products, read its leaf Grams, and sum a
+// completed group up the tree.
+constexpr int PIPE_S = 3;
+constexpr int PIPE_STAGE_FLOATS = 4096;  // 128/RP leaves x F <= 32 rows x R <= RP columns
+
+__device__ __forceinline__ void tc_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_saddr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void tc_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc_saddr(bar)) : "memory");
+}
+__device__ __forceinline__ void tc_bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     tc_saddr(dst)),
+                 "l"(src), "r"(bytes), "r"(tc_saddr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+// Position of a chunk in a CTA's walk: block vb, group g, chunk ch of the group.
+struct ChunkPos {
+    int64_t vb;
+    int g, ch;
+};
+template <int NCH>
+__device__ __forceinline__ void chunk_next(ChunkPos& c, int G) {
+    if (++c.ch == NCH) {
+        c.ch = 0;
+        if (++c.g == G) {
+            c.g = 0;
+            c.vb += gridDim.x;
+        }
+    }
+}
+
+constexpr int PIPE_THREADS = 256;
+
+template <int RP, int LB>
+__global__ void __launch_bounds__(PIPE_THREADS, 2)
+    tree_leaves_tc_pipe(const float* __restrict__ U, int64_t I, int R, int F, int Fp, int64_t L, int G, int Tp,
+                        int64_t nvb, float* __restrict__ tree, float* __restrict__ top, float* __restrict__ copy_to,
+                        int* __restrict__ status) {
+    constexpr int NL = 128 / RP;
+    constexpr int NCH = (LB + NL - 1) / NL;
+    constexpr int S = PIPE_S;
+    constexpr int NT = PIPE_THREADS;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ __align__(8) uint64_t mdone[2];
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int T = tri_size(R);
+    const int nk8 = Fp >> 3;
+    const uint32_t sbo = (uint32_t)nk8 * 128u;
+    const uint32_t xbytes = 16u * sbo;  // 128 rows x Fp bf16
+    float* stages = reinterpret_cast<float*>(smem);
+    unsigned char* X = smem + (size_t)S * PIPE_STAGE_FLOATS * 4;  // [buffer][hi, lo]
+    float* sG = reinterpret_cast<float*>(X + 4 * xbytes);
+    float* stk = sG + (size_t)LB * Tp;
+    const bool dense_shape = (F == Fp) && (R == RP);  // no padding inside a full chunk
+
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(tc_saddr(&tmem_base)),
+                     "r"(2 * TC_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (tid == 0) {
+        for (int b = 0; b < S; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_saddr(&full[b])) : "memory");
+        for (int b = 0; b < 2; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_saddr(&mdone[b])) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < LB * Tp; e += NT)
+        if (e % Tp >= T) sG[e] = 0.f;
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    const int64_t my_vb = (int64_t)blockIdx.x < nvb ? (nvb - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nchunks = my_vb * G * NCH;
+    auto rows_of = [&](const ChunkPos& c, int64_t& row0, int& nl, int& nvalid) {
+        nl = min(NL, LB - c.ch * NL);
+        row0 = ((c.vb * G + c.g) * LB + (int64_t)c.ch * NL) * F;
+        nvalid = (int)max((int64_t)0, min((int64_t)nl * F, I - row0));
+    };
+    ChunkPos ahead{(int64_t)blockIdx.x, 0, 0};  // thread 0: next chunk to fetch
+    int64_t issued = 0;
+    auto issue = [&](int64_t i) {
+        int64_t row0;
+        int nl, nvalid;
+        rows_of(ahead, row0, nl, nvalid);
+        uint64_t* b = &full[i % S];
+        const uint32_t bytes = (uint32_t)nvalid * (uint32_t)R * 4u;  // R % 4 == 0: a multiple of 16
+        if (bytes) {
+            tc_expect_tx(b, bytes);
+            tc_bulk_load(stages + (i % S) * PIPE_STAGE_FLOATS, U + row0 * R, bytes, b);
+        } else {
+            tc_arrive(b);
+        }
+        chunk_next<NCH>(ahead, G);
+        issued = i + 1;
+    };
+    if (tid == 0)
+        for (int64_t i = 0; i < nchunks && i < S; ++i) issue(i);
+
+    bool alive = true;
+    int64_t consumed = 0, mma_issued = 0, mma_waited = 0;
+    ChunkPos cur{(int64_t)blockIdx.x, 0, 0}, prev = cur;
+    for (int64_t i = 0; i <= nchunks; ++i) {
+        if (i < nchunks) {
+            const int st = (int)(i % S);
+            const bool ok = tc_wait(&full[st], (uint32_t)((i / S) & 1));
+            alive = __syncthreads_and(ok) != 0;
+            if (!alive) break;
+            consumed = i + 1;
+            int64_t row0;
+            int nl, nvalid;
+            rows_of(cur, row0, nl, nvalid);
+            const float* sU = stages + (size_t)st * PIPE_STAGE_FLOATS;
+            unsigned char* Xh = X + (size_t)(i & 1) * 2 * xbytes;
+            unsigned char* Xl = Xh + xbytes;
+            const bool full_chunk = dense_shape && nl == NL && nvalid == NL * F;
+            for (int task = tid; task < 128 * nk8; task += NT) {
+                const int p = task & 127, k8 = task >> 7;
+                const int b = p / RP, c = p % RP;
+                const int rr0 = b * F + 8 * k8;
+                float v[8];
+                if (full_chunk) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = sU[(rr0 + q) * R + c];
+                } else {
+                    const bool col_ok = b < nl && c < R;
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int rr = rr0 + q;
+                        v[q] = (col_ok && 8 * k8 + q < F && rr < nvalid) ? sU[rr * R + c] : 0.f;
+                    }
+                }
+                uint4 h, l;
+                split2(v[0], v[1], h.x, l.x);
+                split2(v[2], v[3], h.y, l.y);
+                split2(v[4], v[5], h.z, l.z);
+                split2(v[6], v[7], h.w, l.w);
+                const uint32_t off = (uint32_t)(p >> 3) * sbo + (uint32_t)k8 * 128u + (uint32_t)(p & 7) * 16u;
+                *reinterpret_cast<uint4*>(Xh + off) = h;
+                *reinterpret_cast<uint4*>(Xl + off) = l;
+            }
+            if (copy_to) {
+                float4* dst = reinterpret_cast<float4*>(copy_to + row0 * R);
+                const float4* srcv = reinterpret_cast<const float4*>(sU);
+                for (int q = tid; q < nvalid * R / 4; q += NT) dst[q] = srcv[q];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                if (i + S < nchunks) issue(i + S);
+                const uint32_t xh = tc_saddr(Xh), xl = tc_saddr(Xl);
+                const uint32_t d = tmem + (uint32_t)(i & 1) * TC_COLS;
+                for (int ks = 0; ks < Fp / 16; ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256u;
+                    tc_mma(d, tc_desc(xh + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), ks > 0);
+                    tc_mma(d, tc_desc(xh + ko, 128u, sbo), tc_desc(xl + ko, 128u, sbo), 1u);
+                    tc_mma(d, tc_desc(xl + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), 1u);
+                }
+                tc_commit(&mdone[i & 1]);
+            }
+            mma_issued = i + 1;
+        }
+        if (i >= 1) {
+            const int64_t j = i - 1;
+            const bool ok = tc_wait(&mdone[j & 1], (uint32_t)((j >> 1) & 1));
+            alive = __syncthreads_and(ok) != 0;
+            if (!alive) break;
+            mma_waited = j + 1;
+            tc_fence_after();
+            int64_t row0;
+            int nl, nvalid;
+            rows_of(prev, row0, nl, nvalid);
+            // warp w reads lanes 32 (w mod 4).. of TMEM, columns half (w / 4) of its 32-column block
+            const int qd = warp & 3, hf = warp >> 2;
+            const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(j & 1) * TC_COLS +
+                                   (uint32_t)(32 * qd + 16 * hf);
+            float v[16];
+            tc_ld16(taddr, v);
+            int b, r, c0;
+            if (RP == 32) {
+                b = qd;
+                r = lane;
+                c0 = 16 * hf;
+            } else {  // RP == 16: lanes 0-15 hold leaf 2qd, lanes 16-31 leaf 2qd+1; half hf holds leaf 2qd+hf
+                b = 2 * qd + hf;
+                r = lane & 15;
+                c0 = 0;
+            }
+            const bool mine = (RP == 32) || ((lane >> 4) == hf);
+            if (mine && b < nl && r < R) {
+                float* gr = sG + (size_t)(prev.ch * NL + b) * Tp + tri_index(r, r, R) - r;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) {
+                    const int c = c0 + q;
+                    if (c >= r && c < R) gr[c] = v[q];
+                }
+            }
+            tc_fence_before();
+            if (prev.ch == NCH - 1) {
+                __syncthreads();
+                reduce_group<LB>(sG, stk, tree, top, L, (prev.vb * G + prev.g) * LB, prev.g, G, Tp, prev.vb);
+            }
+            chunk_next<NCH>(prev, G);
+        }
+        if (i < nchunks) chunk_next<NCH>(cur, G);
+        __syncthreads();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (!alive) {
+        // let copies and products already in flight land before the CTA exits
+        if (tid == 0) {
+            for (int64_t c = consumed; c < issued; ++c) tc_wait(&full[c % S], (uint32_t)((c / S) & 1));
+            for (int64_t c = mma_waited; c < mma_issued; ++c) tc_wait(&mdone[c & 1], (uint32_t)((c >> 1) & 1));
+            set_status(status, KRP_ETIMEOUT);
+        }
+        __syncthreads();
+    }
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TC_COLS) : "memory");
     }
 }
 
@@ -272,28 +528,74 @@ cudaError_t launch_tc_lb(int LB, const float* U, int64_t I, int R, int F, int64_
     }
 }
 
+template <int RP, int LB>
+cudaError_t launch_pipe(const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree, float* top,
+                        float* copy_to, int* status, int64_t nvb, size_t smem, int num_sms, cudaStream_t st) {
+    auto k = tree_leaves_tc_pipe<RP, LB>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int Fp = (F + 15) / 16 * 16;
+    const int64_t grid = std::min<int64_t>(nvb, (int64_t)2 * num_sms);
+    k<<<(unsigned)grid, PIPE_THREADS, smem, st>>>(U, I, R, F, Fp, L, G, Tp, nvb, tree, top, copy_to, status); count_launch();
+    return cudaGetLastError();
+}
+
+template <int RP>
+cudaError_t launch_pipe_lb(int LB, const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree,
+                           float* top, float* copy_to, int* status, int64_t nvb, size_t smem, int num_sms,
+                           cudaStream_t st) {
+    switch (LB) {
+        case 1: return launch_pipe<RP, 1>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, nvb, smem, num_sms, st);
+        case 2: return launch_pipe<RP, 2>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, nvb, smem, num_sms, st);
+        case 4: return launch_pipe<RP, 4>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, nvb, smem, num_sms, st);
+        default: return launch_pipe<RP, 8>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, nvb, smem, num_sms, st);
+    }
+}
+
 }  // namespace
 
 bool tree_tc_supported(int R, int F) { return R >= 1 && R <= 128 && F >= 1 && F <= 128; }
 
-// Geometry of the tensor-core leaf kernel: LB leaves per group (power of two,
-// <= 16, <= L, one group's leaf Grams <= 64 KB), G groups per CTA (power of
-// two, <= 8, shared memory <= 200 KB).
-void tree_tc_geometry(int R, int F, int64_t L, int Tp, int* LB_out, int* G_out, size_t* smem_out) {
+// The pipelined form needs R <= 32, R % 4 == 0 (bulk copies of whole rows in
+// 16-byte units), F <= 32 (one chunk <= 16 KB) and a 16-byte aligned source.
+bool tree_tc_pipelined(int R, int F, const float* U) {
+    return R <= 32 && R % 4 == 0 && F <= 32 && ((uintptr_t)U & 15u) == 0;
+}
+
+// Geometry of the tensor-core leaf kernels.  Pipelined: LB = min(8, L) leaves
+// per group, G = 2 groups per block when L allows; shared memory padded to
+// 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM.  Else:
+// LB leaves per group (power of two, <= 16, <= L, one group's leaf Grams
+// <= 64 KB), G groups per CTA (power of two, <= 8, shared memory <= 200 KB).
+void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out) {
     (void)R;
-    int LB = 1;
-    while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * Tp * 4 <= 64 * 1024) LB *= 2;
-    const int64_t groups = L / LB;
-    int G = 1;
-    while (G < 8 && (int64_t)G * 2 <= groups && tc_smem(F, LB, G * 2, Tp) <= 200 * 1024) G *= 2;
+    int LB = 1, G = 1;
+    size_t smem;
+    if (pipelined) {
+        while (LB < 8 && (int64_t)LB * 2 <= L) LB *= 2;
+        if (L / LB >= 2) G = 2;
+        const int Fp = (F + 15) / 16 * 16;
+        const size_t need = (size_t)PIPE_S * PIPE_STAGE_FLOATS * 4 + (size_t)4 * 256 * Fp + (size_t)LB * Tp * 4 +
+                            (size_t)2 * (G == 2 ? 2 : 1) * Tp * 4;
+        smem = std::max<size_t>(need, 80 * 1024);
+    } else {
+        while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * Tp * 4 <= 64 * 1024) LB *= 2;
+        const int64_t groups = L / LB;
+        while (G < 8 && (int64_t)G * 2 <= groups && tc_smem(F, LB, G * 2, Tp) <= 200 * 1024) G *= 2;
+        smem = tc_smem(F, LB, G, Tp);
+    }
     *LB_out = LB;
     *G_out = G;
-    *smem_out = tc_smem(F, LB, G, Tp);
+    *smem_out = smem;
 }
 
 cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
                                   float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
-                                  cudaStream_t st) {
+                                  bool pipelined, int num_sms, cudaStream_t st) {
+    if (pipelined)
+        return padded_rank(R) == 16
+                   ? launch_pipe_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st)
+                   : launch_pipe_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
     switch (padded_rank(R)) {
         case 16: return launch_tc_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
         case 32: return launch_tc_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);

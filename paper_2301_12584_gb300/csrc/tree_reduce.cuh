@@ -25,11 +25,12 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
 
 // Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
 // merge across the CTA's groups, all in double-float.  Stores the FP32 value of
-// every left child created; the CTA's subtree root goes to top as (hi, lo).
+// every left child created; the subtree root of the G groups (the CTA's, or
+// the block `top_slot` of a persistent CTA) goes to top as (hi, lo).
 template <int LB>
 __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
                                              float* __restrict__ top, int64_t L, int64_t first_leaf,
-                                             int g, int G, int Tp) {
+                                             int g, int G, int Tp, int64_t top_slot) {
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         float vh[LB], vl[LB];
 #pragma unroll
@@ -61,8 +62,8 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
         stk[(2 * lvl) * Tp + e] = hi;
         stk[(2 * lvl + 1) * Tp + e] = lo;
         if (g == G - 1) {
-            top[((size_t)blockIdx.x * 2) * Tp + e] = hi;
-            top[((size_t)blockIdx.x * 2 + 1) * Tp + e] = lo;
+            top[((size_t)top_slot * 2) * Tp + e] = hi;
+            top[((size_t)top_slot * 2 + 1) * Tp + e] = lo;
         }
     }
 }

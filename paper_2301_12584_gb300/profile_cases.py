@@ -1,7 +1,8 @@
 """Small, fixed workloads for profiling single kernels of libkrpls with ncu.
 
   python -m paper_2301_12584_gb300.profile_cases descent   # krp_descent_fast, N=3, I=2^20, R=32, J=2^16
-  python -m paper_2301_12584_gb300.profile_cases build     # tree_leaves_*, one factor 2^21 x 32
+  python -m paper_2301_12584_gb300.profile_cases build     # tree_leaves_fp32, one factor 2^21 x 32
+  python -m paper_2301_12584_gb300.profile_cases build_tc  # tree_leaves_tc (BF16x3 on tcgen05), same factor
   python -m paper_2301_12584_gb300.profile_cases prep      # prep_pinv / prep_eig, R=32, N=3
 
 Each case runs its kernel a few times (the first launches warm up), checks the
@@ -29,13 +30,17 @@ def descent():
     assert s.sync_status() == 0, s.last_error()
 
 
-def build():
+def build(precision=0):
     I, R = 1 << 21, 32
     U = torch.from_numpy(synth.skewed_row_factors(1, I, R, seed=0)[0]).cuda()
-    s = Sampler([I], R, 32)
+    s = Sampler([I], R, 32, precision)
     for _ in range(3):
         s.set_factor(0, U)
     assert s.sync_status() == 0, s.last_error()
+
+
+def build_tc():
+    build(precision=1)
 
 
 def prep():
@@ -50,6 +55,6 @@ def prep():
 
 
 if __name__ == "__main__":
-    {"descent": descent, "build": build, "prep": prep}[sys.argv[1]]()
+    {"descent": descent, "build": build, "build_tc": build_tc, "prep": prep}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")
