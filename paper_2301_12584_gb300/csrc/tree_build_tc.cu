@@ -14,8 +14,9 @@
 // discarded.  The operand tile is written once, K-major in 8 x 16-byte core
 // matrices without swizzle, and serves as both A and B.  Warp w reads TMEM
 // lanes 32w..32w+31, i.e. rows of the Gram of the leaf those lanes hold, and
-// writes their upper triangles into the group's leaf array; the pairwise
-// double-float sums up the tree are the ones the FP32 kernel uses.
+// writes their upper triangles into the group's leaf array; the pairwise sums
+// up the tree are the FP32 kernel's, in plain FP32 (the leaves' own ~1e-5
+// error dominates the sums' rounding).
 //
 // Per CTA: 128 threads, 128 TMEM columns; thread 0 issues the MMAs and commits
 // them to an mbarrier that every thread waits on with a bounded number of
@@ -221,7 +222,7 @@ __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ 
             __syncthreads();
         }
         if (!alive) break;
-        reduce_group<LB>(sG, stk, tree, top, L, gleaf0, g, G, Tp, blockIdx.x);
+        reduce_group<LB, false>(sG, stk, tree, top, L, gleaf0, g, G, Tp, blockIdx.x);
         __syncthreads();
     }
 
@@ -470,7 +471,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 2)
             tc_fence_before();
             if (prev.ch == NCH - 1) {
                 __syncthreads();
-                reduce_group<LB>(sG, stk, tree, top, L, (prev.vb * G + prev.g) * LB, prev.g, G, Tp, prev.vb);
+                reduce_group<LB, false>(sG, stk, tree, top, L, (prev.vb * G + prev.g) * LB, prev.g, G, Tp, prev.vb);
             }
             chunk_next<NCH>(prev, G);
         }

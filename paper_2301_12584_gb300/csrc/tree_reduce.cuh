@@ -24,10 +24,12 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
 }
 
 // Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
-// merge across the CTA's groups, all in double-float.  Stores the FP32 value of
-// every left child created; the subtree root of the G groups (the CTA's, or
-// the block `top_slot` of a persistent CTA) goes to top as (hi, lo).
-template <int LB>
+// merge across the CTA's groups, in double-float (DF) or plain FP32 (for leaf
+// Grams that carry ~1e-5 error of their own, where the sums' 2^-24 per level
+// is immaterial).  Stores the FP32 value of every left child created; the
+// subtree root of the G groups (the CTA's, or the block `top_slot` of a
+// persistent CTA) goes to top as (hi, lo).
+template <int LB, bool DF = true>
 __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
                                              float* __restrict__ top, int64_t L, int64_t first_leaf,
                                              int g, int G, int Tp, int64_t top_slot) {
@@ -46,14 +48,20 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
             h >>= 1;
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
-                df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
+                if (DF)
+                    df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
+                else
+                    vh[l] = vh[2 * l] + vh[2 * l + 1];
                 store_node(tree, h + l, Tp, e, vh[l]);
             }
         }
         float hi = vh[0], lo = vl[0];
         int idx = g, lvl = 0;
         while (idx & 1) {
-            df_add(stk[(2 * lvl) * Tp + e], stk[(2 * lvl + 1) * Tp + e], hi, lo, hi, lo);
+            if (DF)
+                df_add(stk[(2 * lvl) * Tp + e], stk[(2 * lvl + 1) * Tp + e], hi, lo, hi, lo);
+            else
+                hi = stk[(2 * lvl) * Tp + e] + hi;
             h >>= 1;
             idx >>= 1;
             ++lvl;
