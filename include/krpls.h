@@ -46,7 +46,7 @@ typedef enum {
     KRP_EZERO = -4,       /* total probability mass is zero (A == 0, or U_k unset)*/
     KRP_ESINGULAR = -5,   /* normal matrix not positive definite                 */
     KRP_ENUMERIC = -6,    /* NaN or Inf probability mass seen on the device      */
-    KRP_ETIMEOUT = -7,    /* reserved: a bounded device wait gave up             */
+    KRP_ETIMEOUT = -7,    /* a bounded device wait gave up (no hang)             */
     KRP_ESTATE = -8       /* call made in the wrong state (e.g. factor not set)  */
 } krp_status;
 
@@ -78,7 +78,7 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
  * sampler's stream first. */
 void krp_destroy(krp_sampler* s);
 
-/* Full-factor update (Thm 1.1 part 1; Alg. 1 lines 2-3).  Copies U (I_j x R,
+/* Full-factor update (Thm 1.1 part 1; Alg. 1).  Copies U (I_j x R,
  * host or device) into the sampler and rebuilds Z_j: leaf partial Grams
  * G^v = U[S(v)]ᵀ U[S(v)] and their sums up the tree (Eq. partial_gram),
  * whose root is G_j = U_jᵀ U_j.  Returns KRP_EINVAL for j out of range. */
@@ -96,7 +96,7 @@ krp_status krp_set_factor_prec(krp_sampler* s, int j, const float* U, int precis
  * eigen-pseudo-inverse with cutoff R*2^-52*lam_max), and for each included k
  * G_{>k} = G⁺ ⊛ ⊛_{m>k} G_m (Eq. G_geq_k_defn), its eigendecomposition
  * (FP64, eigenvalues ascending, negatives clamped to 0) and the eigencomponent
- * sampler E_k (Alg. 2 line 5).  Each sample then descends E_k and Z_k for
+ * sampler E_k (Alg. 2).  Each sample then descends E_k and Z_k for
  * each k (two-stage draw, Eqs. first_dist and second_conditional_dist).
  *
  * Uniforms: Philox4x32-10 with key (seed lo32, seed hi32) and counter
@@ -120,8 +120,8 @@ krp_status krp_sample(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed,
 
 /* krp_sample split in two, for callers that time or overlap the phases:
  * krp_sample_prepare does the per-draw work that does not depend on the
- * samples (Alg. 2 lines 1-5: G, G⁺, G_{>k}, eigendecompositions, E_k) for one
- * exclusion; krp_sample_draw then runs the descent (lines 6-12) and may be
+ * samples (the set-up of Alg. 2: G, G⁺, G_{>k}, eigendecompositions, E_k) for
+ * one exclusion; krp_sample_draw then runs the descent (its sampling loop) and may be
  * called several times (other J, seed or draw_id) while no factor changes.
  * krp_sample_draw returns KRP_ESTATE if the last prepare was for another
  * exclude_j or a factor was set since. */
@@ -185,7 +185,7 @@ krp_status krp_sptensor_create(krp_sptensor** out, int N, const int64_t* I_host,
                                void* stream);
 void krp_sptensor_destroy(krp_sptensor* t);
 
-/* Sketched mode-j solve of Alg. 6 line 6 against the tensor's matricization:
+/* Sketched mode-j least-squares solve of Alg. 6 against the tensor's matricization:
  * Y = SBᵀ SA (I_j x R; each sampled tuple's mode-j fiber is looked up in the
  * index and its nonzeros scattered with weight w_s), M = SAᵀSA, U_out = Y M⁻¹
  * (M⁻¹ from FP64 Cholesky).  idx/weight/SA from krp_sample(exclude_j = j).
@@ -194,7 +194,7 @@ krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* t, int j, int64_
                             const int32_t* idx, const float* weight, const float* SA,
                             float* U_out, int flags);
 
-/* One STS-CP sweep (Alg. 6 lines 5-9) over all modes j = 0..N-1: draw J
+/* One STS-CP sweep (one pass of Alg. 6's loop) over all modes j = 0..N-1: draw J
  * samples excluding j (draw id draw_base + j), solve for U_j, set
  * sigma[i] = ||U_j[:,i]||_2, normalise U_j's columns, and rebuild Z_j.
  * sigma: R floats (device), holds the last mode's norms.  The sampler's
@@ -229,7 +229,7 @@ krp_status krp_debug_wait_timeout(krp_sampler* s, int tries);
 const char* krp_last_error(const krp_sampler* s);
 
 /* krp_sample (without logq/SA) that also records, for samples 0..n_trace-1,
- * every branch the descent evaluated (Alg. 4 lines 12-17): trace (device,
+ * every branch the descent evaluated (Alg. 4): trace (device,
  * float) is laid out [n_trace][n_included][2 stages: eigencomponent, row][66]
  * with [0] = root mass C and, for level l = 0..depth-1, [2+2l] = mass of the
  * left child m(L(c)) and [3+2l] = mass of the current node m(c) (the right

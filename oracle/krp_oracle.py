@@ -220,7 +220,8 @@ def krp_sample(Us, exclude, J, seed, draw_id, d0=0, eig_override=None,
     shaped (n_incl, 2, J) with stage 0 = eigencomponent, 1 = row.
     The weight is 1/sqrt(J_total * q) with q = ℓ_s / rank (Sec. 2.1), where
     J_total is `J` (callers drawing a sub-range pass their own scaling).
-    A SamplerPrep built for the same factors may be passed to skip lines 1-5.
+    A SamplerPrep built for the same factors may be passed to skip the preparation
+    (G, G⁺, the G_{>k} and their eigendecompositions).
     """
     if prep is None:
         prep = SamplerPrep(Us, exclude, eig_override)
@@ -413,7 +414,7 @@ def column_normalize(U):
 
 
 def sketched_mode_solve(Us, coords, vals, dims, j, J, seed, draw_id, table=None):
-    """One sketched solve of Alg. 6 line 6 for mode j:
+    """One sketched least-squares solve of Alg. 6 for mode j:
     U_j = argmin_X ||S U_{≠j} Xᵀ - S mat(T,j)ᵀ||_F with S drawn by Alg. 2
     (excluding j).  Returns (U_j unnormalised, sample dict)."""
     smp = krp_sample(Us, j, J, seed, draw_id)

@@ -1,4 +1,4 @@
-// a4 + a5 (+ a6 fused): batched conditional descent (Alg. 2 lines 6-12 with
+// a4 + a5 (+ a6 fused): batched conditional descent (the sampling loop of Alg. 2, with
 // the loops exchanged as in App. A.6 so all J samples are in flight; Alg. 4
 // RowSample on E_k and Z_k; Eqs. first_dist and second_conditional_dist).
 //
@@ -15,8 +15,8 @@
 // with no real rows (padding) is never entered.  Every thread of the team owns
 // E packed-triangle entries p = tid + 32*TEAM*e; for a fixed history vector it
 // precomputes w_p = h_i h_j (x2 off the diagonal), so each level is E
-// coalesced loads, E FMAs and one team reduction — the quadratic form of Alg. 4
-// line 2 with the symmetric triangle read once.
+// coalesced loads, E FMAs and one team reduction — the node quadratic form of
+// Alg. 4 with the symmetric triangle read once.
 // Epilogue: ℓ_s = hᵀ G⁺ h, q_s = ℓ_s / rank, w_s = 1/sqrt(J q_s) (Sec. 2.1),
 // and optionally SA[s,:] = w_s h (the gather, fused).
 // Precision: the history h and h̃ are carried as double-float (FP32 pairs); the

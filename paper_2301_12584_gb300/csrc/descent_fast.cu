@@ -1,5 +1,5 @@
 // a4 + a5 (+ a6 fused) for R <= 32: the batched conditional descent with one
-// warp per sample (Alg. 2 lines 6-12, loops exchanged as in App. A.6; Alg. 4
+// warp per sample (the sampling loop of Alg. 2, loops exchanged as in App. A.6; Alg. 4
 // on E_k and Z_k; Eqs. first_dist and second_conditional_dist).
 //
 // Per level the mass m(v) = wᵀ g over the packed upper triangle g of the

@@ -1,4 +1,4 @@
-// a2 + a3: per-draw sampler preparation (Alg. 2 lines 1-5; Eq. G_geq_k_defn;
+// a2 + a3: per-draw sampler preparation (the set-up steps of Alg. 2; Eq. G_geq_k_defn;
 // Eq. first_dist; Sec. 3.2).
 //
 // prep_pinv (1 CTA): G = ⊛_{k incl} G_k from the trees' FP32 roots, in FP64;

@@ -12,7 +12,7 @@
 // current group's leaf Grams G^v = U[S(v)]ᵀU[S(v)] are formed (FP32 FMA with
 // 4x4 register tiles on the upper triangle, or tcgen05 BF16x3 in
 // tree_build_tc.cu).  Each thread then owns a fixed set of packed entries and
-// sums them pairwise up the group (parent = left + right, Alg. 3 line 7),
+// sums them pairwise up the group (parent = left + right, Alg. 3),
 // continuing across groups with a per-entry binary-counter stack, storing
 // every left child it creates.  The CTA's subtree root goes to scratch.
 // Kernel 2 (tree_up): the same pairwise sums over LBB nodes per CTA for the

@@ -422,7 +422,7 @@ def test_full_size_index_parity_fp32_band():
 @pytest.mark.parametrize("I,R,excl,rankdef", [(300, 8, -1, False), (500, 32, 1, False), (200, 13, -1, True),
                                               (400, 64, -1, False)])
 def test_prepare_matches_fp64_oracle(I, R, excl, rankdef):
-    """G⁺, rank and the eigendecomposition of every G_{>k} (Alg. 2 lines 1-4)
+    """G⁺, rank and the eigendecomposition of every G_{>k} (the preparation of Alg. 2)
     against numpy FP64 from the exact Grams: eigenvalues, VΛVᵀ = G_{>k},
     VᵀV = I, and individual eigenvectors (up to sign) where the eigenvalue
     gap exceeds 1e-2 of the largest eigenvalue (elsewhere the basis of a
