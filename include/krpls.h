@@ -257,6 +257,76 @@ krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_
 krp_status krp_get_prep(const krp_sampler* s, int k, double* lam_host, double* V_host,
                         double* Gplus_host, int* rank_host);
 
+/* ------------------------------------------------------------------------
+ * Planted right-hand side (a synthetic workload; no counterpart in the paper).
+ *
+ * krp_planted_rows: B_rows[s, c] = a_s · X_true[:, c] + sigma * xi(s, c) for the
+ * sampled tuples s of krp_sample (idx, same exclude_j), where a_s =
+ * ⊛_{k != exclude_j} U_k[idx[k][s], :] is row s of A.  X_true: R x nrhs (device,
+ * row-major); B_rows: J x nrhs (device).  xi is a standard normal by Box–Muller
+ * from Philox4x32-10 with key (seed lo32, seed hi32) and counter (lin lo32,
+ * lin hi32, c, 0x9E3779B9), lin = the C-order linear index of the tuple over
+ * the included factors mod 2^64, so repeated tuples get the same noise.
+ * 1 <= nrhs <= 64.  Asynchronous on the sampler's stream.
+ * ---------------------------------------------------------------------- */
+krp_status krp_planted_rows(krp_sampler* s, int exclude_j, int64_t J, const int32_t* idx, const float* X_true,
+                            int nrhs, float sigma, uint64_t seed, float* B_rows);
+
+/* ------------------------------------------------------------------------
+ * Batches of independent problems: every phase of the path (tree builds,
+ * preparation, descent, planted right-hand side, dense solve) as one launch
+ * over all P problems (Alg. 1-4 and Thm 2.1 applied to each problem), and
+ * the whole sequence capturable as one CUDA graph.
+ *
+ * krp_batch_create: a batch over P existing samplers (not owned; they must
+ * outlive the batch), all with the same N, R <= 32, F <= 32 and every factor
+ * set.  No factor is excluded.  `stream` (a cudaStream_t, not NULL if the
+ * batch is to be captured) carries all batch work; the samplers' own streams
+ * are not used.  Allocates the per-problem parameter tables and scratch.
+ *
+ * Packed layouts (device): idx [P][N][J] int32; weight [P][J]; SA: problem p's
+ * J x R_p rows at SA + J * Roff[p]; B_rows [P][J][nrhs]; X_true and X: problem
+ * p's R_p x nrhs at X + Roff[p] * nrhs, where Roff[p] = R_0 + ... + R_{p-1}.
+ *
+ * krp_batch_set_sources: U_host[p * N + k] = device pointer to problem p's new
+ * factor k (I_k x R_p) or NULL for "rebuild from the sampler's copy"; U_host
+ * NULL = all NULL.  The next krp_batch_build copies each given factor into
+ * its sampler while building.  Updates a device table in place (synchronous),
+ * so a captured graph uses the sources bound when it runs.  Not while capturing.
+ * krp_batch_build: rebuild every tree (FP32 Grams, Alg. 3).
+ * krp_batch_sample: per problem, the preparation of Alg. 2 and J samples (the
+ * per-problem uniforms of krp_sample with the same seed and draw_id); SA may
+ * be NULL.  krp_batch_planted_rows / krp_batch_solve_dense: krp_planted_rows
+ * and krp_solve_dense for every problem (1 <= nrhs <= 16 for the solve).
+ * krp_batch_sync_status: synchronise; the first device status found (batch,
+ * then samplers), cleared.
+ * krp_batch_capture_begin / _end: record the batch calls made in between on
+ * the batch stream into a CUDA graph instead of running them (end reports
+ * the graph's node count); run each call once before capturing, so that no
+ * scratch needs to grow during capture.  krp_batch_replay: launch that graph.
+ * krp_batch_set_tuning: descent CTAs per problem (1..64).  krp_batch_autotune:
+ * time the sampling phase for 1, 2, 4, 8, 16 CTAs per problem at this J and
+ * keep the fastest (allocates and frees temporary outputs; synchronous).
+ * ---------------------------------------------------------------------- */
+typedef struct krp_batch krp_batch;
+krp_status krp_batch_create(krp_batch** out, krp_sampler* const* samplers_host, int P, void* stream);
+void krp_batch_destroy(krp_batch* b);
+krp_status krp_batch_set_sources(krp_batch* b, const float* const* U_host);
+krp_status krp_batch_build(krp_batch* b);
+krp_status krp_batch_sample(krp_batch* b, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx, float* weight,
+                            float* SA);
+krp_status krp_batch_planted_rows(krp_batch* b, int64_t J, const int32_t* idx, const float* X_true, int nrhs,
+                                  float sigma, uint64_t seed, float* B_rows);
+krp_status krp_batch_solve_dense(krp_batch* b, int64_t J, const float* SA, const float* weight, const float* B_rows,
+                                 int nrhs, float* X, int flags);
+krp_status krp_batch_sync_status(krp_batch* b);
+krp_status krp_batch_capture_begin(krp_batch* b);
+krp_status krp_batch_capture_end(krp_batch* b, int64_t* nodes_host);
+krp_status krp_batch_replay(krp_batch* b);
+krp_status krp_batch_set_tuning(krp_batch* b, int descent_ctas_per_problem);
+krp_status krp_batch_autotune(krp_batch* b, int64_t J, int* best_host);
+const char* krp_batch_last_error(const krp_batch* b);
+
 #ifdef __cplusplus
 }
 #endif

@@ -28,7 +28,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .philox import sampler_uniforms
+from .philox import philox4x32_10, sampler_uniforms, u32_to_open_unit
 
 EPS64 = 2.0 ** -52
 
@@ -566,3 +566,34 @@ def krp_sample_tree(Us, exclude, J, seed, draw_id, F, d0=0, prep=None, trees=Non
     q = lev / prep.rank
     out.update(idx=idx, uidx=uidx, q=q, logq=np.log(q), weight=1.0 / np.sqrt(J * q), rank=prep.rank, prep=prep)
     return out
+
+
+def planted_rhs(Us, exclude, idx, X_true, sigma, seed):
+    """Rows of a planted right-hand side B = A X_true + sigma * xi at the sampled
+    tuples idx (n_incl x J): row s is a_s X_true + sigma xi(s, :), a_s the row of
+    A = ⊙ U_k (included factors).  xi(s, c) is a standard normal by Box–Muller
+    from Philox4x32-10 (key = seed halves, counter = (lin lo32, lin hi32, c,
+    0x9E3779B9), lin = the C-order linear index of the tuple mod 2^64), so a
+    repeated tuple gets the same noise.  A workload generator, not part of the
+    method: the sketched solve of Thm 2.1 sees only these rows."""
+    incl = included_factors(len(Us), exclude)
+    idx = np.asarray(idx, dtype=np.int64)
+    J = idx.shape[1]
+    A = sketched_rows(Us, exclude, idx, np.ones(J))
+    lin = np.zeros(J, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        for p, k in enumerate(incl):
+            lin = lin * np.uint64(Us[k].shape[0]) + idx[p].astype(np.uint64)
+    X_true = np.asarray(X_true, dtype=np.float64)
+    nrhs = X_true.shape[1]
+    seed = int(seed)
+    key = np.array([seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF], dtype=np.uint32)
+    ctr = np.zeros((J, nrhs, 4), dtype=np.uint32)
+    ctr[..., 0] = (lin & np.uint64(0xFFFFFFFF)).astype(np.uint32)[:, None]
+    ctr[..., 1] = (lin >> np.uint64(32)).astype(np.uint32)[:, None]
+    ctr[..., 2] = np.arange(nrhs, dtype=np.uint32)[None, :]
+    ctr[..., 3] = np.uint32(0x9E3779B9)
+    w = philox4x32_10(ctr, key)
+    u1, u2 = u32_to_open_unit(w[..., 0]), u32_to_open_unit(w[..., 1])
+    xi = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
+    return A @ X_true + float(sigma) * xi

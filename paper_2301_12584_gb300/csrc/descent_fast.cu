@@ -25,30 +25,6 @@
 
 namespace krp {
 
-struct FastParams {
-    const float* U[16];
-    const float* tree[16];
-    const float* etree[16];
-    const float* Vhi[16];
-    const float* Vlo[16];
-    int64_t I[16];
-    int64_t L[16];
-    int depth[16];
-    int incl[16];
-    int n_incl;
-    int R, F, T, Tp, Rp, dE;
-    const float* Gplus32;
-    const int* rank;
-    int* status;
-    uint32_t key0, key1, draw;
-    int64_t J;
-    int32_t* idx;
-    float* weight;
-    float* logq;
-    float* SA;
-    float* trace;
-    int64_t n_trace;
-};
 
 constexpr int FAST_TRACE_STRIDE = 66;
 
@@ -102,8 +78,10 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     return *reinterpret_cast<float2*>(&d);
 }
 
+// The descent for samples cta*8 + warp, stepping by ncta*8 (ncta CTAs share
+// the J samples of one problem).  P may live in parameter or shared memory.
 template <int RMAX>
-__global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
+__device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t cta, int64_t ncta) {
     using C = FastCfg<RMAX>;
     constexpr int NCH = C::NCH;
     extern __shared__ __align__(128) unsigned char smem[];
@@ -290,8 +268,8 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
     };
 
     const bool leaf_tma = (R & 3) == 0 && P.F * R <= C::STAGE;
-    const int64_t warps_total = (int64_t)gridDim.x * C::WARPS;
-    for (int64_t s = (int64_t)blockIdx.x * C::WARPS + warp; s < P.J && alive; s += warps_total) {
+    const int64_t warps_total = ncta * C::WARPS;
+    for (int64_t s = cta * C::WARPS + warp; s < P.J && alive; s += warps_total) {
         if (lane < RMAX) {
             hh[lane] = lane < R ? 1.f : 0.f;
             hl[lane] = 0.f;
@@ -315,14 +293,14 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
             float cf = 0.f, margin = 0.f;
             int64_t c = 1;
             int u = 0;
-            for (int stage = 0; stage < 2; ++stage) {
-                const float* tr = stage ? P.tree[k] : P.etree[k];
-                const int depth = stage ? P.depth[k] : P.dE;
+            for (int sg = 0; sg < 2; ++sg) {
+                const float* tr = sg ? P.tree[k] : P.etree[k];
+                const int depth = sg ? P.depth[k] : P.dE;
                 // issue the first fetch (root and levels 0-1), then build the
                 // stage's weights while it is in flight
                 const int nfirst = depth >= 1 ? 2 : 1;
                 fetch_issue(tr, (uint32_t)(nfirst * Tp * 4), nullptr, 0);
-                if (stage == 0) {
+                if (sg == 0) {
                     if (lane < RMAX) th[lane] = hh[lane] + hl[lane];
                 } else if (lane < RMAX) {
                     float vh = 0.f, vl = 0.f;
@@ -335,9 +313,9 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
                 }
                 __syncwarp();
                 make_weights(th);
-                if (trc && stage) trc += FAST_TRACE_STRIDE;
+                if (trc && sg) trc += FAST_TRACE_STRIDE;
                 df Cm;
-                c = descend(tr, depth, stage ? Lk : P.Rp, stage ? Ik : R, stage ? F : 1, stage ? u_row : u_eig, Cm,
+                c = descend(tr, depth, sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, Cm,
                             tau, low, trc);
                 if (!alive) break;
                 if (c < 0) {
@@ -348,7 +326,7 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
                 }
                 cf = Cm.hi + Cm.lo;
                 margin = 1e-6f * cf;
-                if (stage == 0) u = (int)(c - P.Rp);
+                if (sg == 0) u = (int)(c - P.Rp);
             }
             if (!alive || !ok) break;
             // ------------------------------------------------ leaf scan
@@ -486,6 +464,11 @@ __global__ void __launch_bounds__(256, 3) krp_descent_fast(FastParams P) {
     }
 }
 
+template <int RMAX>
+__global__ void __launch_bounds__(256, 3) krp_descent_fast(const __grid_constant__ FastParams P) {
+    descent_fast_body<RMAX>(P, blockIdx.x, gridDim.x);
+}
+
 namespace {
 template <int RMAX>
 cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
@@ -521,10 +504,11 @@ cudaError_t launch_wait_timeout_probe(krp_sampler* s, int tries) {
     return cudaGetLastError();
 }
 
-bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
-                         float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err) {
-    if (s->R > 32) return false;
-    FastParams P{};
+// Static part of a problem's parameter block (factors, trees, eigenvectors,
+// G⁺, status); the per-call fields are left zero.
+void fast_params_for(const krp_sampler* s, int exclude_j, FastParams* out) {
+    FastParams& P = *out;
+    P = FastParams{};
     for (int k = 0; k < s->N; ++k) {
         P.U[k] = s->U[k];
         P.tree[k] = s->tree[k];
@@ -545,6 +529,13 @@ bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
     P.Gplus32 = s->Gplus32;
     P.rank = s->rank_dev;
     P.status = s->status;
+}
+
+bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
+                         float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err) {
+    if (s->R > 32) return false;
+    FastParams P;
+    fast_params_for(s, exclude_j, &P);
     P.key0 = (uint32_t)(seed & 0xffffffffu);
     P.key1 = (uint32_t)(seed >> 32);
     P.draw = (uint32_t)(draw_id & 0xffffffffu);
@@ -562,6 +553,48 @@ bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
     else
         *err = launch_fast_t<32>(P, s->num_sms, s->stream);
     return true;
+}
+
+// Batched descent: CTA b serves problem p = b / ctas_per_problem, taking the
+// static block table[p] into shared memory and the per-call fields from `call`
+// (outputs of problem p at idx + p N J, weight + p J, SA + J row_off[p]).
+// RMAX = 32 serves every R <= 32.
+__global__ void __launch_bounds__(256, 3) krp_descent_fast_batch(const FastParams* __restrict__ table,
+                                                                 const __grid_constant__ FastCall call,
+                                                                 int ctas_per_problem) {
+    __shared__ __align__(16) FastParams sP;
+    const int p = blockIdx.x / ctas_per_problem;
+    {
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(table + p);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&sP);
+        for (int w = threadIdx.x; w < (int)(sizeof(FastParams) / 4); w += blockDim.x) dst[w] = src[w];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        sP.key0 = call.key0;
+        sP.key1 = call.key1;
+        sP.draw = call.draw;
+        sP.J = call.J;
+        sP.idx = call.idx + (int64_t)p * call.N * call.J;
+        sP.weight = call.weight + (int64_t)p * call.J;
+        sP.SA = call.SA ? call.SA + call.J * call.row_off[p] : nullptr;
+        sP.logq = nullptr;
+        sP.trace = nullptr;
+        sP.n_trace = 0;
+    }
+    __syncthreads();
+    descent_fast_body<32>(sP, blockIdx.x % ctas_per_problem, ctas_per_problem);
+}
+
+cudaError_t launch_descent_fast_batch(const FastParams* table_dev, const FastCall& call, int P, int ctas_per_problem,
+                                      cudaStream_t st) {
+    using C = FastCfg<32>;
+    cudaFuncSetAttribute(krp_descent_fast_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaFuncSetAttribute(krp_descent_fast_batch, cudaFuncAttributePreferredSharedMemoryCarveout,
+                         cudaSharedmemCarveoutMaxShared);
+    krp_descent_fast_batch<<<(unsigned)(P * ctas_per_problem), 256, C::SMEM, st>>>(table_dev, call, ctas_per_problem);
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace krp

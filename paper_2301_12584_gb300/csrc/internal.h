@@ -70,6 +70,104 @@ struct krp_sptensor {
 
 namespace krp {
 
+// ---------------------------------------------------------------------------
+// Kernel parameter blocks shared between the single-problem launches and the
+// batched ones (batch.cu), which keep one block per problem in device memory.
+// ---------------------------------------------------------------------------
+struct PrepParams {
+    const double* roots[16];  // FP64 root Gram G_k of each factor (packed upper)
+    int incl[16];             // included factors, ascending
+    int n_incl;
+};
+
+struct PrepItem {  // everything prep_pinv / prep_eig read and write for one problem
+    PrepParams P;
+    int N, exclude, R, Rp, dE, Tp;
+    double* G64;
+    double* Gplus64;
+    float* Gplus32;
+    int* rank;
+    int* status;
+    double* gwork;
+    double* lam64;
+    double* V64;
+    float* V32;
+    float* V32lo;
+    float* etree;
+};
+
+struct FastParams {  // the R <= 32 descent of one problem
+    const float* U[16];
+    const float* tree[16];
+    const float* etree[16];
+    const float* Vhi[16];
+    const float* Vlo[16];
+    int64_t I[16];
+    int64_t L[16];
+    int depth[16];
+    int incl[16];
+    int n_incl;
+    int R, F, T, Tp, Rp, dE;
+    const float* Gplus32;
+    const int* rank;
+    int* status;
+    uint32_t key0, key1, draw;
+    int64_t J;
+    int32_t* idx;
+    float* weight;
+    float* logq;
+    float* SA;
+    float* trace;
+    int64_t n_trace;
+};
+
+struct FastCall {  // per-call arguments of the batched descent
+    uint32_t key0, key1, draw;
+    int N;
+    int64_t J;
+    int32_t* idx;            // [P][N][J]
+    float* weight;           // [P][J]
+    float* SA;               // problem p at SA + J * row_off[p], rows of R_p floats
+    const int64_t* row_off;  // device, prefix sums of R_p
+};
+
+struct TreeDesc {  // one factor tree of one problem, for the batched build
+    const float* src;      // rows to build from
+    float* copy_to;        // the sampler's copy of the factor (written if != src), or nullptr
+    float* tree;
+    float* top;            // (hi, lo) pairs of the leaf kernel's block roots
+    double* up[2];         // FP64 levels above the leaf kernel
+    double* root64;
+    int64_t I, L;
+    int R, F, Tp, G;       // G groups of the batch's LB leaves per leaf-kernel block
+};
+
+struct UpDesc {  // one tree in one pass of the batched level sums
+    const float* in_pairs;  // first pass: the leaf kernel's (hi, lo) pairs
+    const double* in64;     // later passes: FP64 nodes
+    double* out;
+    float* tree;
+    int64_t n_in;           // nodes of the input level (heap ids n_in .. 2 n_in - 1)
+    int lbb;                // nodes summed per CTA (1..16)
+    int Tp;
+};
+
+struct SolveItem {  // one problem of the batched dense solve
+    int R;
+    int nparts;
+    int64_t row_off;  // SA rows of this problem start at SA + J * row_off
+    int64_t x_off;    // X of this problem at X + x_off * nrhs
+    float* part;      // nparts x (T + R nrhs) partials
+};
+
+struct PlantItem {  // one problem of the planted right-hand side (included factors only)
+    const float* U[16];
+    int64_t I[16];
+    int krow[16];      // row of idx holding factor m's indices
+    int N, R;
+    int64_t row_off;   // X of this problem at X + row_off * nrhs
+};
+
 krp_status fail(krp_sampler* s, krp_status code, const std::string& msg);
 // Process-wide count of kernel launches made by this library.
 void count_launch();
@@ -96,5 +194,22 @@ krp_status dense_solve(krp_sampler* s, int64_t J, const float* SA, const float* 
                        const float* B_rows, int nrhs, float* X, int flags);
 // a8 (sparse): M⁻¹ into s->solve64 (FP64, R x R), from SA.
 krp_status normal_inverse(krp_sampler* s, int64_t J, const float* SA, int flags);
+
+// Batched launches (one launch per phase for many problems; batch.cu).
+void prep_item_for(const krp_sampler* s, int exclude_j, PrepItem* it);
+cudaError_t launch_prep_batch(const PrepItem* items_dev, int P, int n_incl, int Rmax, cudaStream_t st);
+void fast_params_for(const krp_sampler* s, int exclude_j, FastParams* P);
+cudaError_t launch_descent_fast_batch(const FastParams* table_dev, const FastCall& call, int P, int ctas_per_problem,
+                                      cudaStream_t st);
+cudaError_t launch_leaves_batch(const TreeDesc* trees_dev, const int64_t* block_prefix_dev, int ntrees,
+                                int64_t nblocks, int LB, int Rmax, int Fmax, int Tpmax, int Gmax, bool vec,
+                                cudaStream_t st);
+cudaError_t launch_up_batch(const UpDesc* ups_dev, const int64_t* cta_prefix_dev, int ntrees, int64_t nctas,
+                            int Tpmax, bool from_pairs, cudaStream_t st);
+cudaError_t launch_solve_batch(const SolveItem* items_dev, int P, int max_parts, int Rmax, int64_t J,
+                               const float* SA, const float* weight, const float* B, int nrhs, int flags, float* X,
+                               int* status, cudaStream_t st);
+cudaError_t launch_planted(const PlantItem* items_dev, int P, int64_t J, const int32_t* idx, int N_idx,
+                           const float* X_true, int nrhs, float sigma, uint64_t seed, float* B, cudaStream_t st);
 
 }  // namespace krp

@@ -29,11 +29,6 @@ __device__ void ascending_positions(const double* lam, int n, int* pos) {
     }
 }
 
-struct PrepParams {
-    const double* roots[16];  // FP64 root Gram G_k of each factor (packed upper)
-    int incl[16];             // included factors, ascending
-    int n_incl;
-};
 
 // Block-wide sum of one double per thread (fixed order, every thread gets it).
 __device__ double block_sum(double v, double* red) {
@@ -197,10 +192,10 @@ __host__ size_t carve_smem_bytes(int n, bool fp64_in_smem) {
 // is near the cutoff): G⁺ = G⁻¹ from an FP64 Cholesky factor.  Otherwise the
 // eigen-pseudo-inverse with cutoff R * 2^-52 * lam_max.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) prep_pinv(PrepParams P, int N, int exclude, int R, int Tp,
-                                                 double* __restrict__ G64, double* __restrict__ Gplus64,
-                                                 float* __restrict__ Gplus32, int* __restrict__ rank_out,
-                                                 int* __restrict__ status, double* __restrict__ gwork) {
+__device__ __forceinline__ void prep_pinv_body(const PrepParams& P, int N, int exclude, int R, int Tp,
+                                               double* __restrict__ G64, double* __restrict__ Gplus64,
+                                               float* __restrict__ Gplus32, int* __restrict__ rank_out,
+                                               int* __restrict__ status, double* __restrict__ gwork) {
     extern __shared__ __align__(16) char smp[];
     const int RR = R * R;
     double *X, *A64, *lam;
@@ -324,14 +319,13 @@ __global__ void __launch_bounds__(256) prep_pinv(PrepParams P, int N, int exclud
 // (eig_fp32_refined), eigenvalues ascending with negatives clamped to zero,
 // eigenvectors as FP64 columns, FP32 rows and FP32 residual rows, and E_k.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int Rp, int dE, int Tp,
-                                                const double* __restrict__ G64, const double* __restrict__ Gplus64,
-                                                double* __restrict__ lam64, double* __restrict__ V64,
-                                                float* __restrict__ V32, float* __restrict__ V32lo,
-                                                float* __restrict__ etree, double* __restrict__ gwork) {
+__device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R, int Rp, int dE, int Tp,
+                                              const double* __restrict__ G64, const double* __restrict__ Gplus64,
+                                              double* __restrict__ lam64, double* __restrict__ V64,
+                                              float* __restrict__ V32, float* __restrict__ V32lo,
+                                              float* __restrict__ etree, double* __restrict__ gwork, int p) {
     extern __shared__ __align__(16) char smp[];
     const int RR = R * R;
-    const int p = blockIdx.x;
     const int n_incl = P.n_incl;
     const int k = P.incl[p];
     double *X, *A64, *lam;
@@ -398,6 +392,75 @@ __global__ void __launch_bounds__(256) prep_eig(PrepParams P, int N, int R, int 
 }
 
 size_t carve_smem_bytes(int n, bool fp64_in_smem);
+
+__global__ void __launch_bounds__(256) prep_pinv(const __grid_constant__ PrepParams P, int N, int exclude, int R,
+                                                 int Tp, double* __restrict__ G64, double* __restrict__ Gplus64,
+                                                 float* __restrict__ Gplus32, int* __restrict__ rank_out,
+                                                 int* __restrict__ status, double* __restrict__ gwork) {
+    prep_pinv_body(P, N, exclude, R, Tp, G64, Gplus64, Gplus32, rank_out, status, gwork);
+}
+
+__global__ void __launch_bounds__(256) prep_eig(const __grid_constant__ PrepParams P, int N, int R, int Rp, int dE,
+                                                int Tp, const double* __restrict__ G64,
+                                                const double* __restrict__ Gplus64, double* __restrict__ lam64,
+                                                double* __restrict__ V64, float* __restrict__ V32,
+                                                float* __restrict__ V32lo, float* __restrict__ etree,
+                                                double* __restrict__ gwork) {
+    prep_eig_body(P, N, R, Rp, dE, Tp, G64, Gplus64, lam64, V64, V32, V32lo, etree, gwork, blockIdx.x);
+}
+
+// Batched forms: CTA b of prep_pinv_batch prepares problem b; CTA b of
+// prep_eig_batch the included factor b % n_incl of problem b / n_incl.
+__global__ void __launch_bounds__(256) prep_pinv_batch(const PrepItem* __restrict__ items) {
+    const PrepItem& it = items[blockIdx.x];
+    prep_pinv_body(it.P, it.N, it.exclude, it.R, it.Tp, it.G64, it.Gplus64, it.Gplus32, it.rank, it.status,
+                   it.gwork);
+}
+__global__ void __launch_bounds__(256) prep_eig_batch(const PrepItem* __restrict__ items, int n_incl) {
+    const PrepItem& it = items[blockIdx.x / n_incl];
+    const int p = blockIdx.x % n_incl;
+    prep_eig_body(it.P, it.N, it.R, it.Rp, it.dE, it.Tp, it.G64, it.Gplus64, it.lam64, it.V64, it.V32, it.V32lo,
+                  it.etree, it.gwork ? it.gwork + (size_t)p * 6 * it.R * it.R : nullptr, p);
+}
+
+void prep_item_for(const krp_sampler* s, int exclude_j, PrepItem* it) {
+    PrepItem& x = *it;
+    x = PrepItem{};
+    x.P.n_incl = 0;
+    for (int k = 0; k < s->N; ++k) {
+        x.P.roots[k] = s->root64[k];
+        if (k != exclude_j) x.P.incl[x.P.n_incl++] = k;
+    }
+    x.N = s->N;
+    x.exclude = exclude_j;
+    x.R = s->R;
+    x.Rp = s->Rp;
+    x.dE = s->dE;
+    x.Tp = s->Tp;
+    x.G64 = s->G64;
+    x.Gplus64 = s->Gplus64;
+    x.Gplus32 = s->Gplus32;
+    x.rank = s->rank_dev;
+    x.status = s->status;
+    x.gwork = carve_smem_bytes(s->R, true) <= 200 * 1024 ? nullptr : s->work64;
+    x.lam64 = s->lam64;
+    x.V64 = s->V64;
+    x.V32 = s->V32;
+    x.V32lo = s->V32lo;
+    x.etree = s->etree;
+}
+
+cudaError_t launch_prep_batch(const PrepItem* items_dev, int P, int n_incl, int Rmax, cudaStream_t st) {
+    const bool in_smem = carve_smem_bytes(Rmax, true) <= 200 * 1024;
+    const size_t smem = carve_smem_bytes(Rmax, in_smem);
+    cudaFuncSetAttribute(prep_pinv_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(prep_eig_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    prep_pinv_batch<<<P, 256, smem, st>>>(items_dev); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    prep_eig_batch<<<P * n_incl, 256, smem, st>>>(items_dev, n_incl); count_launch();
+    return cudaGetLastError();
+}
 
 krp_status sampler_prep(krp_sampler* s, int exclude_j) {
     const int R = s->R, N = s->N;

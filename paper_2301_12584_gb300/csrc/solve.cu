@@ -20,21 +20,22 @@ namespace krp {
 constexpr int SOLVE_ROWS = 32;  // rows per shared-memory tile
 
 // Z columns: B_rows (J x nrhs) weighted by w; with B_rows == nullptr Z is not formed.
-__global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ SA, const float* __restrict__ w,
-                                                      const float* __restrict__ B, int64_t J, int R, int nrhs,
-                                                      int64_t rows_per_cta, float* __restrict__ part) {
+// CTA (px, py): rows [px rows_per_cta, (px+1) rows_per_cta), outputs chunk py.
+__device__ __forceinline__ void normal_partial_body(const float* __restrict__ SA, const float* __restrict__ w,
+                                                    const float* __restrict__ B, int64_t J, int R, int nrhs,
+                                                    int64_t rows_per_cta, float* __restrict__ part, int px, int py) {
     extern __shared__ __align__(16) float sm[];
     float* sA = sm;                          // SOLVE_ROWS x R
     float* sB = sA + SOLVE_ROWS * R;         // SOLVE_ROWS x nrhs
     const int T = tri_size(R);
     const int nout = T + R * nrhs;
-    constexpr int MAXO = 8;                  // outputs per thread; blockIdx.y selects the output chunk
+    constexpr int MAXO = 8;                  // outputs per thread; py selects the output chunk
     float acc[MAXO];
     int oi[MAXO], oj[MAXO];
 #pragma unroll
     for (int o = 0; o < MAXO; ++o) {
         acc[o] = 0.f;
-        const int id = (blockIdx.y * MAXO + o) * blockDim.x + threadIdx.x;
+        const int id = (py * MAXO + o) * blockDim.x + threadIdx.x;
         oi[o] = -1;
         oj[o] = 0;
         if (id < T) {
@@ -50,7 +51,7 @@ __global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ 
             oj[o] = -1 - (id - T) % nrhs;  // negative: a column of Z
         }
     }
-    const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
+    const int64_t r0 = (int64_t)px * rows_per_cta;
     const int64_t r1 = min(J, r0 + rows_per_cta);
     for (int64_t base = r0; base < r1; base += SOLVE_ROWS) {
         const int nr = (int)min((int64_t)SOLVE_ROWS, r1 - base);
@@ -79,18 +80,24 @@ __global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ 
     }
 #pragma unroll
     for (int o = 0; o < MAXO; ++o) {
-        const int id = (blockIdx.y * MAXO + o) * blockDim.x + threadIdx.x;
-        if (id < nout) part[(size_t)blockIdx.x * nout + id] = acc[o];
+        const int id = (py * MAXO + o) * blockDim.x + threadIdx.x;
+        if (id < nout) part[(size_t)px * nout + id] = acc[o];
     }
+}
+
+__global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ SA, const float* __restrict__ w,
+                                                      const float* __restrict__ B, int64_t J, int R, int nrhs,
+                                                      int64_t rows_per_cta, float* __restrict__ part) {
+    normal_partial_body(SA, w, B, J, R, nrhs, rows_per_cta, part, blockIdx.x, blockIdx.y);
 }
 
 // One CTA.  mode 0: X = M⁻¹ Z (R x nrhs) written as FP32 to X;
 // mode 1: M⁻¹ (R x R) written as FP64 to Xd (sparse path).
 // Work matrices: shared memory when gbuf == nullptr, else gbuf (global).
-__global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ part, int nparts, int R, int nrhs,
-                                                    int mode, int flags, float* __restrict__ X,
-                                                    double* __restrict__ Xd, int* __restrict__ status,
-                                                    double* __restrict__ gbuf) {
+__device__ __forceinline__ void normal_solve_body(const float* __restrict__ part, int nparts, int R, int nrhs,
+                                                  int mode, int flags, float* __restrict__ X,
+                                                  double* __restrict__ Xd, int* __restrict__ status,
+                                                  double* __restrict__ gbuf) {
     extern __shared__ __align__(16) double smd[];
     const int RR = R * R;
     const int T = tri_size(R);
@@ -202,6 +209,52 @@ __global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ pa
         else
             X[e] = (float)Z[e];
     }
+}
+
+__global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ part, int nparts, int R, int nrhs,
+                                                    int mode, int flags, float* __restrict__ X,
+                                                    double* __restrict__ Xd, int* __restrict__ status,
+                                                    double* __restrict__ gbuf) {
+    normal_solve_body(part, nparts, R, nrhs, mode, flags, X, Xd, status, gbuf);
+}
+
+// Batched forms: blockIdx.z (partials) or blockIdx.x (solve) is the problem.
+__global__ void __launch_bounds__(256) normal_partial_batch(const SolveItem* __restrict__ items, int64_t J,
+                                                            const float* __restrict__ SA,
+                                                            const float* __restrict__ w,
+                                                            const float* __restrict__ B, int nrhs) {
+    const SolveItem& it = items[blockIdx.z];
+    const int nout = tri_size(it.R) + it.R * nrhs;
+    if ((int)blockIdx.x >= it.nparts || (int)blockIdx.y * 8 * (int)blockDim.x >= nout) return;  // CTA-uniform
+    const int64_t rows_per_cta = (J + it.nparts - 1) / it.nparts;
+    normal_partial_body(SA + J * it.row_off, w + (int64_t)blockIdx.z * J,
+                        B ? B + (int64_t)blockIdx.z * J * nrhs : nullptr, J, it.R, nrhs, rows_per_cta, it.part,
+                        blockIdx.x, blockIdx.y);
+}
+
+__global__ void __launch_bounds__(256) normal_solve_batch(const SolveItem* __restrict__ items, int nrhs, int flags,
+                                                          float* __restrict__ X, int* __restrict__ status) {
+    const SolveItem& it = items[blockIdx.x];
+    normal_solve_body(it.part, it.nparts, it.R, nrhs, 0, flags, X + it.x_off * nrhs, nullptr, status, nullptr);
+}
+
+cudaError_t launch_solve_batch(const SolveItem* items_dev, int P, int max_parts, int Rmax, int64_t J,
+                               const float* SA, const float* weight, const float* B, int nrhs, int flags, float* X,
+                               int* status, cudaStream_t st) {
+    const int nout = tri_size(Rmax) + Rmax * nrhs;
+    const dim3 grid1(max_parts, (nout + 256 * 8 - 1) / (256 * 8), P);
+    const size_t smem1 = (size_t)SOLVE_ROWS * (Rmax + nrhs) * 4;
+    normal_partial_batch<<<grid1, 256, smem1, st>>>(items_dev, J, SA, weight, B, nrhs); count_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const size_t small = 64 * 8 + 2 * (Rmax / 2 + 1) * 8 + 2 * (Rmax / 2 + 1) * 4 + 16;
+    const size_t smem2 = small + (size_t)(2 * Rmax * Rmax + Rmax * nrhs) * 8;
+    if (smem2 > 48 * 1024) {
+        e = cudaFuncSetAttribute(normal_solve_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (e != cudaSuccess) return e;
+    }
+    normal_solve_batch<<<P, 256, smem2, st>>>(items_dev, nrhs, flags, X, status); count_launch();
+    return cudaGetLastError();
 }
 
 namespace {

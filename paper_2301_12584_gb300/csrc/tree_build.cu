@@ -124,10 +124,12 @@ __device__ __forceinline__ void copy_rows_out(const float* sU, float* __restrict
     }
 }
 
+// Block blk: leaves [blk G LB, (blk+1) G LB), subtree root to top slot blk.
 template <int LB, bool VEC>
-__global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
-                                                        int64_t L, int G, int Tp, float* __restrict__ tree,
-                                                        float* __restrict__ top, float* __restrict__ copy_to) {
+__device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ U, int64_t I, int R, int F, int64_t L,
+                                                      int G, int Tp, float* __restrict__ tree,
+                                                      float* __restrict__ top, float* __restrict__ copy_to,
+                                                      int64_t blk) {
     extern __shared__ __align__(16) float smem[];
     const int rows = LB * F;
     const int T = tri_size(R);
@@ -137,7 +139,7 @@ __global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restri
     float* stk = sG + (size_t)LB * Tp;
     for (int e = threadIdx.x; e < LB * Tp; e += blockDim.x)
         if (e % Tp >= T) sG[e] = 0.f;  // packed tail stays zero
-    const int64_t leaf0 = (int64_t)blockIdx.x * G * LB;
+    const int64_t leaf0 = blk * G * LB;
     stage_rows<VEC>(sU0, U, I, R, leaf0 * F, rows);
     if (VEC) cp_async_commit();
     for (int g = 0; g < G; ++g) {
@@ -155,11 +157,74 @@ __global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restri
         if (copy_to) copy_rows_out<VEC>(cur, copy_to, I, R, (leaf0 + (int64_t)g * LB) * F, rows);
         leaf_grams_fp32<LB, VEC>(cur, sG, R, F, Tp);
         __syncthreads();
-        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blockIdx.x);
+        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk);
         if (!VEC && g + 1 < G) {
             __syncthreads();
             stage_rows<VEC>(sU0, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);
         }
+    }
+}
+
+template <int LB, bool VEC>
+__global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
+                                                        int64_t L, int G, int Tp, float* __restrict__ tree,
+                                                        float* __restrict__ top, float* __restrict__ copy_to) {
+    tree_leaves_fp32_body<LB, VEC>(U, I, R, F, L, G, Tp, tree, top, copy_to, blockIdx.x);
+}
+
+// Index of the entry of an ascending prefix array whose range holds x.
+__device__ __forceinline__ int prefix_find(const int64_t* __restrict__ pre, int n, int64_t x) {
+    int lo = 0, hi = n - 1;  // pre[0] = 0 <= x < pre[n]
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= x)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+// Batched leaf kernel: CTA b builds block b - prefix[t] of tree t (the tree
+// whose block range holds b), with LB leaves per group and the tree's own G.
+template <int LB, bool VEC>
+__global__ void __launch_bounds__(288, 2) tree_leaves_fp32_batch(const TreeDesc* __restrict__ trees,
+                                                              const int64_t* __restrict__ prefix, int ntrees) {
+    const int t = prefix_find(prefix, ntrees, blockIdx.x);
+    const TreeDesc& d = trees[t];
+    tree_leaves_fp32_body<LB, VEC>(d.src, d.I, d.R, d.F, d.L, d.G, d.Tp, d.tree, d.top,
+                                   d.copy_to, (int64_t)blockIdx.x - prefix[t]);
+}
+
+// Batched level sums: CTA b sums `lbb` nodes of tree t's input level (t found
+// as above) in the same pairwise order as tree_up<lbb>.
+template <bool FROM_PAIRS>
+__global__ void tree_up_batch(const UpDesc* __restrict__ ups, const int64_t* __restrict__ prefix, int ntrees) {
+    const int t = prefix_find(prefix, ntrees, blockIdx.x);
+    const UpDesc& u = ups[t];
+    const int64_t cta = (int64_t)blockIdx.x - prefix[t];
+    const int lbb = u.lbb, Tp = u.Tp;
+    const int64_t first = cta * lbb;
+    for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
+        double v[16];
+#pragma unroll
+        for (int l = 0; l < 16; ++l)
+            v[l] = l >= lbb ? 0.0
+                            : (FROM_PAIRS ? (double)u.in_pairs[((first + l) * 2) * Tp + e] +
+                                                (double)u.in_pairs[((first + l) * 2 + 1) * Tp + e]
+                                          : u.in64[(first + l) * Tp + e]);
+        int64_t h = u.n_in + first;
+#pragma unroll
+        for (int n = 16; n > 1; n >>= 1) {
+            if (n > lbb) continue;
+            h >>= 1;
+#pragma unroll
+            for (int l = 0; l < n / 2; ++l) {
+                v[l] = v[2 * l] + v[2 * l + 1];
+                store_node(u.tree, h + l, Tp, e, (float)v[l]);
+            }
+        }
+        u.out[(size_t)cta * Tp + e] = v[0];
     }
 }
 
@@ -287,6 +352,45 @@ void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* 
     *G_out = G;
     *threads_out = threads;
     *smem_out = smem_of(G);
+}
+
+cudaError_t launch_leaves_batch(const TreeDesc* trees_dev, const int64_t* block_prefix_dev, int ntrees,
+                                int64_t nblocks, int LB, int Rmax, int Fmax, int Tpmax, int Gmax, bool vec,
+                                cudaStream_t st) {
+    int lv = 0;
+    while ((1 << lv) < Gmax) ++lv;
+    const size_t leaf_bytes = (size_t)Fmax * Rmax * 4;
+    const size_t smem = (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)LB * Tpmax * 4 + (size_t)2 * (lv + 1) * Tpmax * 4;
+    cudaError_t e = cudaSuccess;
+#define KRP_LB(LBV)                                                                                              \
+    {                                                                                                            \
+        auto k = vec ? tree_leaves_fp32_batch<LBV, true> : tree_leaves_fp32_batch<LBV, false>;                   \
+        if (smem > 48 * 1024) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+        if (e == cudaSuccess) {                                                                                  \
+            k<<<(unsigned)nblocks, 288, smem, st>>>(trees_dev, block_prefix_dev, ntrees);                         \
+            count_launch();                                                                                      \
+            e = cudaGetLastError();                                                                              \
+        }                                                                                                        \
+    }
+    switch (LB) {
+        case 1: KRP_LB(1) break;
+        case 2: KRP_LB(2) break;
+        case 4: KRP_LB(4) break;
+        default: KRP_LB(8) break;
+    }
+#undef KRP_LB
+    return e;
+}
+
+cudaError_t launch_up_batch(const UpDesc* ups_dev, const int64_t* cta_prefix_dev, int ntrees, int64_t nctas,
+                            int Tpmax, bool from_pairs, cudaStream_t st) {
+    const int threads = std::min(512, std::max(64, ((Tpmax + 31) / 32) * 32));
+    if (from_pairs)
+        tree_up_batch<true><<<(unsigned)nctas, threads, 0, st>>>(ups_dev, cta_prefix_dev, ntrees);
+    else
+        tree_up_batch<false><<<(unsigned)nctas, threads, 0, st>>>(ups_dev, cta_prefix_dev, ntrees);
+    count_launch();
+    return cudaGetLastError();
 }
 
 krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {

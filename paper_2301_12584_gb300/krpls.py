@@ -50,6 +50,21 @@ SIGNATURES = [
     ("krp_tree_info", _INT, [_P, _INT, C.POINTER(_I64), C.POINTER(_INT), C.POINTER(_INT)]),
     ("krp_get_tree", _INT, [_P, _INT, _P, _I64]),
     ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
+    ("krp_planted_rows", _INT, [_P, _INT, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
+    ("krp_batch_create", _INT, [C.POINTER(_P), C.POINTER(_P), _INT, _P]),
+    ("krp_batch_destroy", None, [_P]),
+    ("krp_batch_set_sources", _INT, [_P, C.POINTER(_P)]),
+    ("krp_batch_build", _INT, [_P]),
+    ("krp_batch_sample", _INT, [_P, _I64, _U64, _U64, _P, _P, _P]),
+    ("krp_batch_planted_rows", _INT, [_P, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
+    ("krp_batch_solve_dense", _INT, [_P, _I64, _P, _P, _P, _INT, _P, _INT]),
+    ("krp_batch_sync_status", _INT, [_P]),
+    ("krp_batch_capture_begin", _INT, [_P]),
+    ("krp_batch_capture_end", _INT, [_P, C.POINTER(_I64)]),
+    ("krp_batch_replay", _INT, [_P]),
+    ("krp_batch_set_tuning", _INT, [_P, _INT]),
+    ("krp_batch_autotune", _INT, [_P, _I64, C.POINTER(_INT)]),
+    ("krp_batch_last_error", C.c_char_p, [_P]),
 ]
 
 _lib = None
@@ -153,6 +168,10 @@ class Sampler:
         self._check(self._lib.krp_solve_dense(self.h, int(J), _P(_ptr(SA)), _P(_ptr(weight)), _P(_ptr(B_rows)),
                                               int(nrhs), _P(_ptr(X)), int(flags)))
 
+    def planted_rows(self, exclude_j, J, idx, X_true, nrhs, sigma, seed, B_rows):
+        self._check(self._lib.krp_planted_rows(self.h, int(exclude_j), int(J), _P(_ptr(idx)), _P(_ptr(X_true)),
+                                               int(nrhs), float(sigma), int(seed), _P(_ptr(B_rows))))
+
     def solve_sparse(self, tensor, j, J, idx, weight, SA, U_out, flags=KRP_PINV_FALLBACK):
         self._check(self._lib.krp_solve_sparse(self.h, tensor.h, int(j), int(J), _P(_ptr(idx)), _P(_ptr(weight)),
                                                _P(_ptr(SA)), _P(_ptr(U_out)), int(flags)))
@@ -247,3 +266,86 @@ class SparseTensor:
             self.close()
         except Exception:
             pass
+
+
+class Batch:
+    """Owns a krp_batch over existing Samplers (kept alive here).  Packed
+    layouts as in include/krpls.h: problem p's SA rows and X start at row
+    offset Roff[p] = sum of the earlier problems' R."""
+
+    def __init__(self, samplers, stream):
+        L = lib()
+        self._lib = L
+        self.samplers = list(samplers)
+        self.P = len(self.samplers)
+        self.N = self.samplers[0].N
+        self.R = [s.R for s in self.samplers]
+        self.row_off = [0]
+        for r in self.R:
+            self.row_off.append(self.row_off[-1] + r)
+        arr = (_P * self.P)(*[s.h for s in self.samplers])
+        h = _P()
+        code = L.krp_batch_create(C.byref(h), arr, self.P, _P(_stream_ptr(stream)))
+        if code != KRP_OK:
+            raise KrpError(code, L.krp_last_error(None).decode())
+        self.h = h
+
+    def _check(self, code):
+        if code != KRP_OK:
+            raise KrpError(code, self._lib.krp_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self._lib.krp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_sources(self, U=None):
+        """U: list of P*N device tensors/pointers (None entries: keep), or None."""
+        if U is None:
+            self._check(self._lib.krp_batch_set_sources(self.h, None))
+            return
+        arr = (_P * (self.P * self.N))(*[_ptr(u) for u in U])
+        self._check(self._lib.krp_batch_set_sources(self.h, arr))
+
+    def build(self):
+        self._check(self._lib.krp_batch_build(self.h))
+
+    def sample(self, J, seed, draw_id, idx, weight, SA=None):
+        self._check(self._lib.krp_batch_sample(self.h, int(J), int(seed), int(draw_id), _P(_ptr(idx)),
+                                               _P(_ptr(weight)), _P(_ptr(SA))))
+
+    def planted_rows(self, J, idx, X_true, nrhs, sigma, seed, B_rows):
+        self._check(self._lib.krp_batch_planted_rows(self.h, int(J), _P(_ptr(idx)), _P(_ptr(X_true)), int(nrhs),
+                                                     float(sigma), int(seed), _P(_ptr(B_rows))))
+
+    def solve_dense(self, J, SA, weight, B_rows, nrhs, X, flags=0):
+        self._check(self._lib.krp_batch_solve_dense(self.h, int(J), _P(_ptr(SA)), _P(_ptr(weight)),
+                                                    _P(_ptr(B_rows)), int(nrhs), _P(_ptr(X)), int(flags)))
+
+    def sync_status(self):
+        return int(self._lib.krp_batch_sync_status(self.h))
+
+    def capture_begin(self):
+        self._check(self._lib.krp_batch_capture_begin(self.h))
+
+    def capture_end(self):
+        n = _I64()
+        self._check(self._lib.krp_batch_capture_end(self.h, C.byref(n)))
+        return n.value
+
+    def replay(self):
+        self._check(self._lib.krp_batch_replay(self.h))
+
+    def set_tuning(self, descent_ctas_per_problem):
+        self._check(self._lib.krp_batch_set_tuning(self.h, int(descent_ctas_per_problem)))
+
+    def autotune(self, J):
+        best = _INT()
+        self._check(self._lib.krp_batch_autotune(self.h, int(J), C.byref(best)))
+        return best.value

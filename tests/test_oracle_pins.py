@@ -437,3 +437,25 @@ def test_batched_tree_replay_equals_inverse_cdf_sampler(I, F, excl):
     assert np.array_equal(a["idx"], b["idx"]) and np.array_equal(a["uidx"], b["uidx"])
     np.testing.assert_allclose(b["total"], a["total"], rtol=1e-12)
     np.testing.assert_allclose(b["tau"], a["tau"], rtol=1e-12)
+
+
+def test_planted_rhs_noise_is_standard_normal_and_keyed_by_tuple():
+    """The planted right-hand side's noise (a workload generator): sigma = 0
+    gives A X exactly; repeated tuples get identical rows; over distinct tuples
+    the noise passes a Kolmogorov-Smirnov test against N(0, 1)."""
+    from scipy.stats import kstest
+    rng = np.random.default_rng(3)
+    Us = [rng.standard_normal((40, 5)) for _ in range(3)]
+    idx = np.stack(np.unravel_index(np.arange(40 ** 3), (40, 40, 40)))   # every tuple once
+    X = rng.standard_normal((5, 2))
+    A = O.sketched_rows(Us, -1, idx, np.ones(idx.shape[1]))
+    np.testing.assert_array_equal(O.planted_rhs(Us, -1, idx, X, 0.0, 11), A @ X)
+    xi = O.planted_rhs(Us, -1, idx, X, 1.0, 11) - A @ X
+    assert kstest(xi[:, 0], "norm").pvalue > 1e-3
+    assert kstest(xi[:, 1], "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(xi[:, 0], xi[:, 1])[0, 1]) < 4 / np.sqrt(len(xi))
+    rep = idx[:, [5, 77, 5, 77]]
+    B = O.planted_rhs(Us, -1, rep, X, 1.0, 11)
+    np.testing.assert_array_equal(B[0], B[2])
+    np.testing.assert_array_equal(B[1], B[3])
+    assert not np.allclose(O.planted_rhs(Us, -1, rep, X, 1.0, 12), B)
