@@ -11,9 +11,14 @@ needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|bf16x3] [--no-cpu-baseline]
+                  [--workload sampler|batch512|rank_sweep] [--rank R]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 (independent draws, disjoint draw ids); value = samples of all ranks / max time.
+The default workload is the headline line; batch512 (512 small least-squares
+problems: per-problem launches vs one launch per phase vs graph replay) and
+rank_sweep (N=4, 2^20 x R, U(-1,1), J=2^17, dense solve with 8 planted
+right-hand sides) print their own lines.
 """
 from __future__ import annotations
 
@@ -49,6 +54,11 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--workload", default="sampler", choices=["sampler", "batch512", "rank_sweep"],
+                    help="sampler: the headline line; batch512: 512 small least-squares problems "
+                         "(per-problem launches vs one launch per phase vs graph replay); "
+                         "rank_sweep: N=4, I=2^20, U(-1,1), J=2^17 at --rank R")
+    ap.add_argument("--rank", type=int, default=32)
     return ap.parse_args()
 
 
@@ -164,11 +174,202 @@ def run_reference(args, rank):
     }), flush=True)
 
 
+# ------------------------------------------------------- other workloads ----
+def _events_ms(stream, fn, steps):
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for d in range(steps):
+        fn(d)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_batch512(args):
+    """512 independent dense KRP least-squares problems: N=3, I_j log-uniform in
+    [256, 65536] per factor, R from {8, 16, 32}, N(0,1) factors, 4 right-hand
+    sides planted with 1e-3 noise, J=4096 samples each.  One batch = rebuild
+    every tree from its source + prepare + sample + planted rows + solve."""
+    import torch
+    from paper_2301_12584_gb300 import krpls, synth
+    from paper_2301_12584_gb300.krpls import Batch, Sampler
+    P, N, J, NRHS = 512, 3, 4096, 4
+    rng = np.random.default_rng(4)
+    shapes = []
+    for _ in range(P):
+        R = int(rng.choice([8, 16, 32]))
+        shapes.append(([int(np.exp(rng.uniform(np.log(256), np.log(65536)))) for _ in range(N)], R))
+    dev = torch.device("cuda", 0)
+    krpls.lib()
+    stream = torch.cuda.Stream(device=dev)
+    sams, srcs, xt = [], [], []
+    for p, (I, R) in enumerate(shapes):
+        Us = synth.gaussian_factors(N, I, R, seed=10_000 + p)
+        d = [torch.from_numpy(U).to(dev) for U in Us]
+        s = Sampler(I, R, R, stream=stream)
+        for k in range(N):
+            s.set_factor(k, d[k])
+        sams.append(s)
+        srcs += d
+        xt.append(synth.planted_solution(R, NRHS, seed=20_000 + p).ravel())
+    torch.cuda.synchronize()
+    X_true = torch.from_numpy(np.concatenate(xt).astype(np.float32)).to(dev)
+    batch = Batch(sams, stream)
+    batch.set_sources(srcs)
+    off = batch.row_off
+    idx = torch.zeros((P, N, J), dtype=torch.int32, device=dev)
+    w = torch.zeros((P, J), device=dev)
+    SA = torch.zeros(J * off[-1], device=dev)
+    B = torch.zeros((P, J, NRHS), device=dev)
+    X = torch.zeros(off[-1] * NRHS, device=dev)
+
+    def batched(d):
+        batch.build()
+        batch.sample(J, 1, d, idx, w, SA)
+        batch.planted_rows(J, idx, X_true, NRHS, 1e-3, 2, B)
+        batch.solve_dense(J, SA, w, B, NRHS, X)
+
+    SAp = [SA[J * off[p]: J * off[p + 1]] for p in range(P)]
+    Xp = [X[off[p] * NRHS: off[p + 1] * NRHS] for p in range(P)]
+    Xtp = [X_true[off[p] * NRHS: off[p + 1] * NRHS] for p in range(P)]
+
+    def per_problem(d):
+        for p in range(P):
+            s = sams[p]
+            for k in range(N):
+                s.set_factor(k, srcs[p * N + k])
+            s.sample(-1, J, 1, d, idx[p], w[p], None, SAp[p])
+            s.planted_rows(-1, J, idx[p], Xtp[p], NRHS, 1e-3, 2, B[p])
+            s.solve_dense(J, SAp[p], w[p], B[p], NRHS, Xp[p])
+
+    steps, warm = max(args.steps, 1), max(args.warmup, 3)
+    with torch.cuda.stream(stream):
+        for d in range(warm):
+            per_problem(d)
+        ms_per = _events_ms(stream, per_problem, steps)
+        X_single = X.clone()
+        best = batch.autotune(J)
+        for d in range(warm):
+            batched(d)
+        ms_batched = _events_ms(stream, batched, steps)
+        n0 = krpls.launch_count()
+        batched(0)
+        launches = krpls.launch_count() - n0
+        torch.cuda.synchronize()
+        batch.capture_begin()
+        batched(0)
+        nodes = batch.capture_end()
+        for _ in range(warm):
+            batch.replay()
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.2)
+        ms_graph = _events_ms(stream, lambda d: batch.replay(), steps)
+        clk = clocks.stop()
+    assert batch.sync_status() == 0, "device status"
+    Xb = X.cpu().numpy()
+    Xs = X_single.cpu().numpy()
+    Xt = X_true.cpu().numpy()
+    err_planted, diff_single = [], []
+    for p in range(P):
+        sl = slice(off[p] * NRHS, off[p + 1] * NRHS)
+        err_planted.append(np.linalg.norm(Xb[sl] - Xt[sl]) / np.linalg.norm(Xt[sl]))
+        diff_single.append(np.linalg.norm(Xb[sl] - Xs[sl]) / np.linalg.norm(Xs[sl]))
+    print(json.dumps({
+        "metric": "512 KRP least-squares problems: tree builds + prepare + sample + planted rows + solve",
+        "value": ms_graph, "unit": "ms per batch", "higher_is_better": False, "n_gpus": 1, "steps": steps,
+        "warmup": warm, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": "batch512_N3_I[256,65536]_R{8,16,32}_J4096_nrhs4", "P": P, "J": J,
+                   "rows_total": int(sum(sum(I) for I, _ in shapes)), "l2": "factors 1.3 GB > L2"},
+        "per_problem_ms": ms_per, "batched_ms": ms_batched, "graph_ms": ms_graph,
+        "speedup_graph_vs_per_problem": ms_per / ms_graph,
+        "autotune": {"descent_ctas_per_problem": best},
+        "gpu_launches_per_batch": launches, "graph_nodes": nodes,
+        "x_rel_err_vs_planted_median": float(np.median(err_planted)),
+        "x_rel_diff_batched_vs_per_problem_max": float(np.max(diff_single)),
+        "clocks": clk,
+    }), flush=True)
+
+
+def run_rank_sweep(args):
+    """N=4 factors of 2^20 x R, U(-1,1), F=R; one step = prepare + draw J=2^17
+    (with SA) + planted rows (8 right-hand sides, 1e-3 noise) + dense solve."""
+    import torch
+    from paper_2301_12584_gb300 import krpls, synth
+    from paper_2301_12584_gb300.krpls import Sampler
+    N, I, R, J, NRHS = 4, 1 << 20, int(args.rank), 1 << 17, 8
+    dev = torch.device("cuda", 0)
+    krpls.lib()
+    stream = torch.cuda.Stream(device=dev)
+    Us = synth.uniform_factors(N, I, R, seed=0)
+    s = Sampler([I] * N, R, R, stream=stream)
+    for k in range(N):
+        s.set_factor(k, torch.from_numpy(Us[k]).to(dev))
+    Xt = synth.planted_solution(R, NRHS, seed=1)
+    X_true = torch.from_numpy(Xt).to(dev)
+    idx = torch.zeros((N, J), dtype=torch.int32, device=dev)
+    w = torch.zeros(J, device=dev)
+    SA = torch.zeros((J, R), device=dev)
+    B = torch.zeros((J, NRHS), device=dev)
+    X = torch.zeros((R, NRHS), device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    phase = []
+
+    def step(d, timed=True):
+        e = [ev() for _ in range(4)]
+        e[0].record(stream)
+        s.sample_prepare(-1)
+        s.sample_draw(-1, J, 1, d, idx, w, None, SA)
+        e[1].record(stream)
+        s.planted_rows(-1, J, idx, X_true, NRHS, 1e-3, 2, B)
+        e[2].record(stream)
+        s.solve_dense(J, SA, w, B, NRHS, X)
+        e[3].record(stream)
+        if timed:
+            phase.append(e)
+
+    steps, warm = max(args.steps, 1), max(args.warmup, 3)
+    with torch.cuda.stream(stream):
+        for d in range(warm):
+            step(d, False)
+        clocks = ClockSampler(0)
+        clocks.start()
+        time.sleep(0.2)
+        ms = _events_ms(stream, lambda d: step(warm + d), steps)
+        clk = clocks.stop()
+    assert s.sync_status() == 0, s.last_error()
+    sample_ms = statistics.mean(p[0].elapsed_time(p[1]) for p in phase)
+    solve_ms = statistics.mean(p[2].elapsed_time(p[3]) for p in phase)
+    # errors of the last step against FP64 on the same sketch, and against the planted X
+    from oracle import krp_oracle as O
+    SA64 = SA.cpu().numpy().astype(np.float64)
+    SB64 = w.cpu().numpy().astype(np.float64)[:, None] * B.cpu().numpy().astype(np.float64)
+    Xo = O.lstsq(SA64, SB64)
+    Xg = X.cpu().numpy()
+    print(json.dumps({
+        "metric": "KRP leverage samples/s, rank sweep (prepare + draw + planted rows + dense solve per step)",
+        "value": J / (ms / 1e3), "unit": "samples/s", "higher_is_better": True, "n_gpus": 1, "steps": steps,
+        "warmup": warm, "ms_per_step": ms, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": f"rank_sweep_N4_I2^20_R{R}_J2^17_nrhs8", "R": R, "l2": "inputs larger than L2"},
+        "phases_ms": {"prepare_and_draw": sample_ms, "solve": solve_ms},
+        "x_rel_err_vs_fp64_same_sketch": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),
+        "x_rel_err_vs_planted": float(np.linalg.norm(Xg - Xt) / np.linalg.norm(Xt)),
+        "clocks": clk,
+    }), flush=True)
+
+
 # ------------------------------------------------------------------ ours ----
 def main():
     args = parse()
     from paper_2301_12584_gb300 import replicas
     rank, local, world = replicas.rank_env()
+    if args.workload != "sampler" and args.impl == "ours":
+        if world > 1 and rank != 0:
+            return
+        (run_batch512 if args.workload == "batch512" else run_rank_sweep)(args)
+        return
     if args.impl == "reference":
         if world > 1:
             import torch.distributed as dist
