@@ -11,14 +11,16 @@ needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|bf16x3] [--no-cpu-baseline]
-                  [--workload sampler|batch512|rank_sweep] [--rank R]
+                  [--workload sampler|batch512|rank_sweep|sparse_als] [--rank R]
+                  [--ranks 25,50,100] [--nnz N] [--sweeps S]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 (independent draws, disjoint draw ids); value = samples of all ranks / max time.
 The default workload is the headline line; batch512 (512 small least-squares
 problems: per-problem launches vs one launch per phase vs graph replay) and
 rank_sweep (N=4, 2^20 x R, U(-1,1), J=2^17, dense solve with 8 planted
-right-hand sides) print their own lines.
+right-hand sides) and sparse_als (STS-CP on a 2^22 x 2^22 x 2^14 Zipf tensor:
+FP32, BF16x3 and graph-replayed sweeps) print their own lines.
 """
 from __future__ import annotations
 
@@ -54,11 +56,14 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--workload", default="sampler", choices=["sampler", "batch512", "rank_sweep"],
+    ap.add_argument("--workload", default="sampler", choices=["sampler", "batch512", "rank_sweep", "sparse_als"],
                     help="sampler: the headline line; batch512: 512 small least-squares problems "
                          "(per-problem launches vs one launch per phase vs graph replay); "
                          "rank_sweep: N=4, I=2^20, U(-1,1), J=2^17 at --rank R")
     ap.add_argument("--rank", type=int, default=32)
+    ap.add_argument("--ranks", default="25,50,100", help="sparse_als: decomposition ranks")
+    ap.add_argument("--nnz", type=int, default=200_000_000, help="sparse_als: nonzeros")
+    ap.add_argument("--sweeps", type=int, default=20, help="sparse_als: ALS sweeps per configuration")
     return ap.parse_args()
 
 
@@ -360,6 +365,88 @@ def run_rank_sweep(args):
     }), flush=True)
 
 
+def run_sparse_als(args):
+    """STS-CP (Alg. 6) on a synthetic sparse 2^22 x 2^22 x 2^14 tensor with Zipf(1.1)
+    coordinates and rank-16 U(0,1) values x lognormal(0, 0.5) noise; J = 2^16
+    samples per least-squares solve; per rank: FP32 trees, BF16x3 trees, and
+    the FP32 sweep captured as a CUDA graph.  Reports the median sweep time of
+    sweeps 2..S and the fit after each sweep (fit not timed)."""
+    import torch
+    from paper_2301_12584_gb300 import krpls, synth
+    from paper_2301_12584_gb300.krpls import Sampler, SparseTensor
+    dims, J = (1 << 22, 1 << 22, 1 << 14), 1 << 16
+    dev = torch.device("cuda", 0)
+    krpls.lib()
+    t0 = time.perf_counter()
+    coords, vals = synth.sparse_zipf_tensor(dims, int(args.nnz), seed=0, device=dev)
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.Stream(device=dev)
+    t0 = time.perf_counter()
+    t = SparseTensor(dims, coords, vals, stream=stream)
+    t_index = time.perf_counter() - t0
+    # Row scale of the initial factors: N(0,1) rows times sqrt(nonzeros of that
+    # index + 0.01) / mean.  Plain N(0,1) rows give every index the same
+    # leverage, and at this density (2^44 possible (i_0, i_1) fibers for the
+    # 2^14 mode) the first sketches would see almost no nonzeros.
+    scales = []
+    for k in range(3):
+        cnt = np.bincount(coords[k], minlength=dims[k]).astype(np.float64) + 0.01
+        scales.append(np.sqrt(cnt / cnt.mean()).astype(np.float32))
+    del coords, vals
+    results = []
+    ranks = [int(r) for r in str(args.ranks).split(",") if r]
+    S = max(int(args.sweeps), 3)
+    for R in ranks:
+        Us0 = synth.gaussian_factors(3, list(dims), R, seed=0)
+        Ud = [torch.from_numpy(U * sc[:, None]).to(dev) for U, sc in zip(Us0, scales)]
+        del Us0
+        row = {"R": R}
+        for mode in ("fp32", "bf16x3", "fp32_graph"):
+            prec = krpls.KRP_PREC_BF16X3 if mode == "bf16x3" else krpls.KRP_PREC_FP32
+            s = Sampler(list(dims), R, 0, prec, stream=stream)
+            for k in range(3):
+                s.set_factor(k, Ud[k])
+            sigma = torch.zeros(R, device=dev)
+            times, fits = [], []
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                for sw in range(S):
+                    if mode == "fp32_graph" and sw == 1:
+                        s.capture_begin()
+                        s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
+                        s.capture_end()
+                    torch.cuda.synchronize()
+                    a.record(stream)
+                    if mode == "fp32_graph" and sw >= 1:
+                        s.replay()
+                    else:
+                        s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    times.append(a.elapsed_time(b))
+                    fits.append(s.cp_fit(t, sigma))
+            status = s.sync_status()
+            row[mode] = {"status": status, "sweep_ms_median_2_to_S": statistics.median(times[1:]), "first_sweep_ms": times[0],
+                         "fit_last": fits[-1], "fits": [round(f, 6) for f in fits]}
+            s.close()
+        row["bf16x3_fit_rel_diff"] = abs(row["bf16x3"]["fit_last"] - row["fp32"]["fit_last"]) / max(
+            1e-30, abs(row["fp32"]["fit_last"]))
+        results.append(row)
+        del Ud
+        torch.cuda.empty_cache()
+    print(json.dumps({
+        "metric": "STS-CP sweep time (median of sweeps 2..S), sparse 3-mode tensor",
+        "value": results[0]["fp32"]["sweep_ms_median_2_to_S"], "unit": "ms per sweep",
+        "higher_is_better": False, "n_gpus": 1, "steps": S, "dtype": "f32", "data": "synthetic",
+        "vs_baseline": None,
+        "config": {"workload": f"sparse_als_2^22x2^22x2^14_nnz{int(args.nnz)}_J2^16", "nnz": int(args.nnz),
+                   "ranks": ranks, "sweeps": S,
+                   "init": "N(0,1) rows x sqrt((nnz of the index + 0.01) / mean), seed 0"},
+        "setup_s": {"generate": t_gen, "index": t_index},
+        "results": results,
+    }), flush=True)
+
+
 # ------------------------------------------------------------------ ours ----
 def main():
     args = parse()
@@ -368,7 +455,7 @@ def main():
     if args.workload != "sampler" and args.impl == "ours":
         if world > 1 and rank != 0:
             return
-        (run_batch512 if args.workload == "batch512" else run_rank_sweep)(args)
+        {"batch512": run_batch512, "rank_sweep": run_rank_sweep, "sparse_als": run_sparse_als}[args.workload](args)
         return
     if args.impl == "reference":
         if world > 1:

@@ -257,6 +257,18 @@ krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_
 krp_status krp_get_prep(const krp_sampler* s, int k, double* lam_host, double* V_host,
                         double* Gplus_host, int* rank_host);
 
+/* CUDA-graph capture of a sampler's calls (no counterpart in the paper):
+ * between krp_capture_begin and krp_capture_end the sampler's calls on its
+ * stream are recorded, not run (end reports the node count); krp_replay runs
+ * the recorded sequence again with the arguments given at capture (e.g. one
+ * whole STS-CP sweep, krp_cp_als_sweep).  The sampler must have been created
+ * with its own stream.  Make each call once before capturing, so that no
+ * scratch grows during capture; calls that synchronise (krp_sync_status,
+ * krp_cp_fit, copies to host) must not be captured. */
+krp_status krp_capture_begin(krp_sampler* s);
+krp_status krp_capture_end(krp_sampler* s, int64_t* nodes_host);
+krp_status krp_replay(krp_sampler* s);
+
 /* ------------------------------------------------------------------------
  * Planted right-hand side (a synthetic workload; no counterpart in the paper).
  *

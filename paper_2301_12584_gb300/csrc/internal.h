@@ -47,6 +47,10 @@ struct krp_sampler {
     int64_t als_J = 0;
     std::string last_error;
     int last_exclude = -2;      // exclude_j of the last prep (for inspection)
+    // a captured sequence of this sampler's calls (krp_capture_begin / _end)
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    bool capturing = false;
 };
 
 struct krp_sptensor {

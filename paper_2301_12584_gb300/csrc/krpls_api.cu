@@ -83,7 +83,14 @@ extern "C" {
 
 void krp_destroy(krp_sampler* s) {
     if (!s) return;
+    if (s->capturing) {
+        cudaGraph_t g = nullptr;
+        cudaStreamEndCapture(s->stream, &g);
+        if (g) cudaGraphDestroy(g);
+    }
     cudaStreamSynchronize(s->stream);
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
     for (float* p : s->U) cudaFree(p);
     for (float* p : s->tree) cudaFree(p);
     for (double* p : s->root64) cudaFree(p);
@@ -293,6 +300,39 @@ krp_status krp_sync_status(krp_sampler* s) {
 }
 
 int64_t krp_launch_count(void) { return krp::launch_counter(); }
+
+krp_status krp_capture_begin(krp_sampler* s) {
+    if (!s) return fail(nullptr, KRP_EINVAL, "krp_capture_begin: NULL sampler");
+    if (s->capturing) return fail(s, KRP_ESTATE, "krp_capture_begin: already capturing");
+    if (!s->stream) return fail(s, KRP_ESTATE, "krp_capture_begin: the sampler was created on the legacy stream");
+    const cudaError_t e = cudaStreamBeginCapture(s->stream, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) s->capturing = true;
+    return cuda_check(s, e, "krp_capture_begin");
+}
+
+krp_status krp_capture_end(krp_sampler* s, int64_t* nodes_host) {
+    if (!s) return fail(nullptr, KRP_EINVAL, "krp_capture_end: NULL sampler");
+    if (!s->capturing) return fail(s, KRP_ESTATE, "krp_capture_end: not capturing");
+    s->capturing = false;
+    if (s->graph_exec) cudaGraphExecDestroy(s->graph_exec);
+    if (s->graph) cudaGraphDestroy(s->graph);
+    s->graph_exec = nullptr;
+    s->graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s->stream, &s->graph);
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&s->graph_exec, s->graph, 0);
+    if (e == cudaSuccess && nodes_host) {
+        size_t n = 0;
+        e = cudaGraphGetNodes(s->graph, nullptr, &n);
+        *nodes_host = (int64_t)n;
+    }
+    return cuda_check(s, e, "krp_capture_end");
+}
+
+krp_status krp_replay(krp_sampler* s) {
+    if (!s) return fail(nullptr, KRP_EINVAL, "krp_replay: NULL sampler");
+    if (!s->graph_exec) return fail(s, KRP_ESTATE, "krp_replay: nothing captured");
+    return cuda_check(s, cudaGraphLaunch(s->graph_exec, s->stream), "krp_replay");
+}
 
 krp_status krp_debug_wait_timeout(krp_sampler* s, int tries) {
     if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");

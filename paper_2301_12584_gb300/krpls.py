@@ -51,6 +51,9 @@ SIGNATURES = [
     ("krp_get_tree", _INT, [_P, _INT, _P, _I64]),
     ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
     ("krp_planted_rows", _INT, [_P, _INT, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
+    ("krp_capture_begin", _INT, [_P]),
+    ("krp_capture_end", _INT, [_P, C.POINTER(_I64)]),
+    ("krp_replay", _INT, [_P]),
     ("krp_batch_create", _INT, [C.POINTER(_P), C.POINTER(_P), _INT, _P]),
     ("krp_batch_destroy", None, [_P]),
     ("krp_batch_set_sources", _INT, [_P, C.POINTER(_P)]),
@@ -167,6 +170,17 @@ class Sampler:
     def solve_dense(self, J, SA, weight, B_rows, nrhs, X, flags=0):
         self._check(self._lib.krp_solve_dense(self.h, int(J), _P(_ptr(SA)), _P(_ptr(weight)), _P(_ptr(B_rows)),
                                               int(nrhs), _P(_ptr(X)), int(flags)))
+
+    def capture_begin(self):
+        self._check(self._lib.krp_capture_begin(self.h))
+
+    def capture_end(self):
+        n = _I64()
+        self._check(self._lib.krp_capture_end(self.h, C.byref(n)))
+        return n.value
+
+    def replay(self):
+        self._check(self._lib.krp_replay(self.h))
 
     def planted_rows(self, exclude_j, J, idx, X_true, nrhs, sigma, seed, B_rows):
         self._check(self._lib.krp_planted_rows(self.h, int(exclude_j), int(J), _P(_ptr(idx)), _P(_ptr(X_true)),

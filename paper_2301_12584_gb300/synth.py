@@ -78,25 +78,37 @@ def noise(shape, seed, scale, dtype=np.float32):
     return (scale * rng.standard_normal(shape)).astype(dtype)
 
 
-def zipf_indices(rng, n, dim, s):
-    """n draws from Zipf(s) truncated to [0, dim) by inverse CDF, then mapped
-    through a seeded permutation so that hot indices are not contiguous."""
+def zipf_cdf(dim, s):
+    """CDF of Zipf(s) truncated to ranks 1..dim."""
     ranks = np.arange(1, dim + 1, dtype=np.float64)
-    pmf = ranks ** (-s)
-    cdf = np.cumsum(pmf)
-    cdf /= cdf[-1]
+    cdf = np.cumsum(ranks ** (-s))
+    return cdf / cdf[-1]
+
+
+def zipf_indices(rng, n, dim, s, perm=None, cdf=None):
+    """n draws from Zipf(s) truncated to [0, dim) by inverse CDF, then mapped
+    through a seeded permutation so that hot indices are not contiguous (one
+    permutation per mode: pass the same `perm` for every batch of a mode)."""
+    if cdf is None:
+        cdf = zipf_cdf(dim, s)
+    if perm is None:
+        perm = rng.permutation(dim)
     u = rng.random(n)
     r = np.searchsorted(cdf, u, side="left")
     r = np.minimum(r, dim - 1)
-    perm = rng.permutation(dim)
     return perm[r].astype(np.int32)
 
 
-def sparse_zipf_tensor(dims, nnz, seed, s=1.1, model_rank=16, batch=None):
+def sparse_zipf_tensor(dims, nnz, seed, s=1.1, model_rank=16, batch=None, device=None):
     """Synthetic sparse tensor: coordinates with Zipf(s) per mode, repeats
     dropped in draw order until `nnz` unique coordinates; values are a
     rank-`model_rank` CP model with U(0,1) factors evaluated at each
     coordinate, times lognormal(0, 0.5) noise.
+
+    All random draws come from NumPy's PCG64(seed).  With `device` (a torch
+    device) the inverse-CDF lookups, the removal of repeats and the model
+    values run there instead (same draws and coordinates; values equal up to
+    the order of FP64 summation) — for tensors of 10^8 nonzeros.
 
     Returns (coords int32 [N, nnz], vals float32 [nnz]).
     """
@@ -105,10 +117,52 @@ def sparse_zipf_tensor(dims, nnz, seed, s=1.1, model_rank=16, batch=None):
     bits = [int(np.ceil(np.log2(max(d, 2)))) for d in dims]
     assert sum(bits) <= 63
     batch = batch or max(1024, nnz // 2)
+    perms = [rng.permutation(d) for d in dims]
+    cdfs = [zipf_cdf(d, s) for d in dims]
+    if device is not None:
+        import torch
+        tcdf = [torch.from_numpy(c).to(device) for c in cdfs]
+        tperm = [torch.from_numpy(p).to(device) for p in perms]
+        seen = torch.zeros(0, dtype=torch.int64, device=device)
+        acc = [torch.zeros(0, dtype=torch.int32, device=device) for _ in range(N)]
+        while seen.numel() < nnz:
+            cs = []
+            for k, d in enumerate(dims):
+                u = torch.from_numpy(rng.random(batch)).to(device)
+                r = torch.clamp(torch.searchsorted(tcdf[k], u, right=False), max=d - 1)
+                cs.append(tperm[k][r].to(torch.int32))
+            key = torch.zeros(batch, dtype=torch.int64, device=device)
+            for k in range(N):
+                key = (key << bits[k]) | cs[k].to(torch.int64)
+            uniq, inv = torch.unique(key, sorted=True, return_inverse=True)
+            first = torch.full((uniq.numel(),), batch, dtype=torch.int64, device=device)
+            first.scatter_reduce_(0, inv, torch.arange(batch, device=device), reduce="amin")
+            first = torch.sort(first).values
+            key = key[first]
+            cs = [c[first] for c in cs]
+            fresh = ~torch.isin(key, seen)
+            key = key[fresh]
+            cs = [c[fresh] for c in cs]
+            take = min(key.numel(), nnz - seen.numel())
+            seen = torch.cat([seen, key[:take]])
+            acc = [torch.cat([a, c[:take]]) for a, c in zip(acc, cs)]
+        del seen
+        coords_t = torch.stack(acc)
+        V = [torch.from_numpy(rng.random((d, model_rank))).to(device) for d in dims]
+        noise = rng.lognormal(0.0, 0.5, size=nnz)
+        vals = np.empty(nnz, dtype=np.float32)
+        step = 1 << 24
+        for a in range(0, nnz, step):
+            b = min(nnz, a + step)
+            P = torch.ones((b - a, model_rank), dtype=torch.float64, device=device)
+            for k in range(N):
+                P *= V[k][coords_t[k, a:b].long()]
+            vals[a:b] = (P.sum(dim=1).cpu().numpy() * noise[a:b]).astype(np.float32)
+        return coords_t.cpu().numpy(), vals
     keys_seen = np.zeros(0, dtype=np.int64)
     coords_acc = [np.zeros(0, np.int32) for _ in range(N)]
     while keys_seen.size < nnz:
-        cs = [zipf_indices(rng, batch, d, s) for d in dims]
+        cs = [zipf_indices(rng, batch, d, s, perm=pm, cdf=cf) for d, pm, cf in zip(dims, perms, cdfs)]
         key = np.zeros(batch, dtype=np.int64)
         for k in range(N):
             key = (key << bits[k]) | cs[k].astype(np.int64)
@@ -125,11 +179,16 @@ def sparse_zipf_tensor(dims, nnz, seed, s=1.1, model_rank=16, batch=None):
         coords_acc = [np.concatenate([a, c[:take]]) for a, c in zip(coords_acc, cs)]
     coords = np.stack(coords_acc).astype(np.int32)
     V = [rng.random((d, model_rank)) for d in dims]
-    P = np.ones((nnz, model_rank))
-    for k in range(N):
-        P *= V[k][coords[k]]
-    vals = P.sum(axis=1) * rng.lognormal(0.0, 0.5, size=nnz)
-    return coords, vals.astype(np.float32)
+    noise = rng.lognormal(0.0, 0.5, size=nnz)
+    vals = np.empty(nnz, dtype=np.float32)
+    step = 1 << 22
+    for a in range(0, nnz, step):  # the CP model in chunks (nnz x model_rank would not fit at scale)
+        b = min(nnz, a + step)
+        P = np.ones((b - a, model_rank))
+        for k in range(N):
+            P *= V[k][coords[k, a:b]]
+        vals[a:b] = (P.sum(axis=1) * noise[a:b]).astype(np.float32)
+    return coords, vals
 
 
 def planted_dense_tensor(dims, rank, seed):
