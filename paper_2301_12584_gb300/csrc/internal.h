@@ -70,6 +70,15 @@ struct krp_sptensor {
     double normT2 = 0.0;               // ||T||_F^2 (host, FP64)
     float* Y = nullptr;                // scratch: max I_j x R
     size_t Y_floats = 0;
+    // lookup scratch: per sample its fiber; a hash table of H >= 2J slots (fiber
+    // key, summed w_s SA[s, :]); per slot the fiber's start, length and their scan
+    int64_t* lk_fiber = nullptr;
+    unsigned long long* lk_keys = nullptr;
+    int64_t* lk_begin = nullptr;
+    int64_t* lk_len = nullptr;
+    int64_t* lk_scan = nullptr;
+    float* lk_acc = nullptr;
+    size_t lk_n = 0, lk_acc_n = 0;
 };
 
 namespace krp {

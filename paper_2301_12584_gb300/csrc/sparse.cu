@@ -6,9 +6,15 @@
 // nonzero gets the key packing its coordinates in the modes k != j (ascending
 // k, ceil(log2 I_k) bits each); nonzeros are sorted by key, equal keys form a
 // mode-j fiber (one row of mat(T, j)ᵀ restricted to its nonzeros).
-// Lookup: a warp per sampled tuple binary-searches its key among the fiber
-// keys, then scatters every nonzero (i_j, v) of the fiber into
-// Y[i_j, :] += w_s v SA[s, :]  (Y = SBᵀ SA, I_j x R).
+// Lookup: a thread per sampled tuple binary-searches its key among the fiber
+// keys.  Samples of the same fiber are then merged (their contributions
+// differ only in the sketched row, so Σ_s w_s SA[s, :] per fiber is formed
+// first, in a hash table keyed by the fiber, with H >= 2J slots); an
+// exclusive scan of the merged fibers' lengths numbers the (fiber, nonzero)
+// pairs, and warps take equal runs of those pairs, adding
+// Y[i_j, :] += v · (Σ_s w_s SA[s, :])  (Y = SBᵀ SA, I_j x R) for each
+// nonzero (i_j, v).  Repeated Zipf-hot fibers are so scattered once, and
+// fibers of very different lengths spread over all warps.
 // Then U_j = Y M⁻¹ with M = SAᵀ SA (FP64 Cholesky inverse, applied in FP32).
 #include "common.cuh"
 #include "internal.h"
@@ -38,15 +44,12 @@ struct LookupParams {
     float* Y;            // I_j x R
 };
 
-__global__ void __launch_bounds__(256) fiber_scatter(LookupParams P) {
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.J; s += warps) {
+__global__ void __launch_bounds__(256) fiber_find(LookupParams P, int64_t* __restrict__ fiber) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < P.J; s += (int64_t)gridDim.x * blockDim.x) {
         uint64_t key = 0;
         for (int q = 0; q < P.n_other; ++q)
             key = (key << P.kbits[q]) | (uint64_t)(uint32_t)P.idx[(int64_t)P.other[q] * P.J + s];
-        // lower_bound over the sorted fiber keys (every lane computes the same)
-        int64_t lo = 0, hi = P.nfib;
+        int64_t lo = 0, hi = P.nfib;  // lower_bound over the sorted fiber keys
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
             if (__ldg(P.fkeys + mid) < key)
@@ -54,13 +57,105 @@ __global__ void __launch_bounds__(256) fiber_scatter(LookupParams P) {
             else
                 hi = mid;
         }
-        if (lo >= P.nfib || __ldg(P.fkeys + lo) != key) continue;  // empty fiber: SB row is zero
-        const int64_t b = __ldg(P.fptr + lo), e = __ldg(P.fptr + lo + 1);
-        const float ws = P.weight[s];
-        for (int64_t n = b; n < e; ++n) {
+        fiber[s] = (lo < P.nfib && __ldg(P.fkeys + lo) == key) ? lo : -1;  // -1: the SB row is zero
+    }
+}
+
+constexpr unsigned long long SLOT_EMPTY = ~0ull;
+
+// A warp per sample: find (or claim) the fiber's slot by linear probing, then
+// add w_s SA[s, :] to the slot's R-vector.
+__global__ void __launch_bounds__(256) merge_samples(LookupParams P, const int64_t* __restrict__ fiber,
+                                                     unsigned long long* __restrict__ keys, float* __restrict__ acc,
+                                                     int log2H) {
+    const int lane = threadIdx.x & 31;
+    const int64_t H = (int64_t)1 << log2H;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.J; s += warps) {
+        const int64_t f = fiber[s];
+        if (f < 0) continue;
+        int64_t slot = -1;
+        if (lane == 0) {
+            int64_t h = (int64_t)(((unsigned long long)f * 0x9E3779B97F4A7C15ull) >> (64 - log2H));
+            for (int64_t probe = 0; probe < H; ++probe) {  // H >= 2J: a slot is always found
+                const unsigned long long old = atomicCAS(keys + h, SLOT_EMPTY, (unsigned long long)f);
+                if (old == SLOT_EMPTY || old == (unsigned long long)f) {
+                    slot = h;
+                    break;
+                }
+                h = (h + 1) & (H - 1);
+            }
+        }
+        slot = __shfl_sync(0xffffffffu, slot, 0);
+        if (slot < 0) continue;
+        const float ws = __ldg(P.weight + s);
+        for (int a = lane; a < P.R; a += 32) atomicAdd(acc + slot * P.R + a, ws * __ldg(P.SA + s * P.R + a));
+    }
+}
+
+// Per slot: first nonzero and length of its fiber (0 for an empty slot).
+__global__ void __launch_bounds__(256) slot_lengths(LookupParams P, const unsigned long long* __restrict__ keys,
+                                                    int64_t H, int64_t* __restrict__ begin,
+                                                    int64_t* __restrict__ len) {
+    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long f = keys[h];
+        const bool used = f != SLOT_EMPTY;
+        begin[h] = used ? __ldg(P.fptr + f) : 0;
+        len[h] = used ? __ldg(P.fptr + f + 1) - __ldg(P.fptr + f) : 0;
+    }
+}
+
+// Exclusive scan of len[0..n) into scan[0..n] (scan[n] = total), one CTA.
+__global__ void __launch_bounds__(1024) scan_lengths(const int64_t* __restrict__ len, int64_t* __restrict__ scan,
+                                                     int64_t n) {
+    __shared__ int64_t part[1024];
+    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t a = threadIdx.x * per, b = min(n, a + per);
+    int64_t sum = 0;
+    for (int64_t i = a; i < b; ++i) sum += len[i];
+    part[threadIdx.x] = sum;
+    __syncthreads();
+    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive Hillis-Steele scan
+        const int64_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int64_t run = part[threadIdx.x] - sum;
+    for (int64_t i = a; i < b; ++i) {
+        scan[i] = run;
+        run += len[i];
+    }
+    if (threadIdx.x == blockDim.x - 1) scan[n] = part[threadIdx.x];
+}
+
+// Warps take runs of SCATTER_RUN consecutive (slot, nonzero) pairs.
+constexpr int SCATTER_RUN = 32;
+
+__global__ void __launch_bounds__(256) fiber_scatter(LookupParams P, const int64_t* __restrict__ begin,
+                                                     const int64_t* __restrict__ scan, int64_t H,
+                                                     const float* __restrict__ acc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t total = scan[H];
+    const int64_t nrun = (total + SCATTER_RUN - 1) / SCATTER_RUN;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t run = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nrun; run += warps) {
+        const int64_t w0 = run * SCATTER_RUN, w1 = min(total, w0 + SCATTER_RUN);
+        int64_t lo = 0, hi = H - 1;  // last slot with scan[h] <= w0
+        while (lo < hi) {
+            const int64_t mid = (lo + hi + 1) >> 1;
+            if (__ldg(scan + mid) <= w0)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        int64_t h = lo;
+        for (int64_t w = w0; w < w1; ++w) {
+            while (__ldg(scan + h + 1) <= w) ++h;
+            const int64_t n = __ldg(begin + h) + (w - __ldg(scan + h));
             const int64_t ij = __ldg(P.fidx + n);
-            const float v = ws * __ldg(P.fval + n);
-            for (int a = lane; a < P.R; a += 32) atomicAdd(P.Y + ij * P.R + a, v * P.SA[s * P.R + a]);
+            const float v = __ldg(P.fval + n);
+            for (int a = lane; a < P.R; a += 32) atomicAdd(P.Y + ij * P.R + a, v * __ldg(acc + h * P.R + a));
         }
     }
 }
@@ -108,15 +203,21 @@ __global__ void __launch_bounds__(256) col_sumsq(const float* __restrict__ U, in
     }
 }
 
-__global__ void col_scale(float* __restrict__ U, int64_t I, int R, const double* __restrict__ sumsq,
-                          float* __restrict__ sigma) {
-    const int64_t n = I * R;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
-        const double sg = sqrt(sumsq[e % R]);
-        U[e] = sg > 0.0 ? (float)((double)U[e] / sg) : U[e];
+// U[:, c] /= σ_c (a zero column stays zero), σ_c = sqrt(σ²_c) to sigma;
+// a warp per row, lanes over columns.
+__global__ void __launch_bounds__(256) col_scale(float* __restrict__ U, int64_t I, int R,
+                                                 const double* __restrict__ sumsq, float* __restrict__ sigma) {
+    __shared__ float inv[128];
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        const double sg = sqrt(sumsq[c]);
+        inv[c] = sg > 0.0 ? (float)(1.0 / sg) : 1.f;
+        if (blockIdx.x == 0) sigma[c] = (float)sg;
     }
-    if (blockIdx.x == 0)
-        for (int c = threadIdx.x; c < R; c += blockDim.x) sigma[c] = (float)sqrt(sumsq[c]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t i = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); i < I;
+         i += (int64_t)gridDim.x * (blockDim.x >> 5))
+        for (int c = lane; c < R; c += 32) U[i * R + c] *= inv[c];
 }
 
 // ⟨T, T̃⟩ = Σ_nnz v Σ_r σ_r Π_k U_k[i_k, r]  (FP64 accumulation).
@@ -285,6 +386,12 @@ extern "C" void krp_sptensor_destroy(krp_sptensor* t) {
         cudaFree(t->fval[j]);
     }
     cudaFree(t->Y);
+    cudaFree(t->lk_fiber);
+    cudaFree(t->lk_keys);
+    cudaFree(t->lk_begin);
+    cudaFree(t->lk_len);
+    cudaFree(t->lk_scan);
+    cudaFree(t->lk_acc);
     delete t;
 }
 
@@ -326,10 +433,40 @@ extern "C" krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* tc, i
     P.J = J;
     P.R = R;
     P.Y = t->Y;
-    const int64_t grid = std::min<int64_t>((J + 7) / 8, (int64_t)s->num_sms * 16);
-    fiber_scatter<<<(unsigned)grid, 256, 0, s->stream>>>(P); count_launch();
+    int log2H = 1;
+    while (((int64_t)1 << log2H) < 2 * J) ++log2H;
+    const int64_t H = (int64_t)1 << log2H;
+    if ((size_t)H + 1 > t->lk_n || (size_t)H * R > t->lk_acc_n) {
+        cudaFree(t->lk_fiber);
+        cudaFree(t->lk_keys);
+        cudaFree(t->lk_begin);
+        cudaFree(t->lk_len);
+        cudaFree(t->lk_scan);
+        cudaFree(t->lk_acc);
+        t->lk_fiber = t->lk_begin = t->lk_len = t->lk_scan = nullptr;
+        t->lk_keys = nullptr;
+        t->lk_acc = nullptr;
+        t->lk_n = t->lk_acc_n = 0;
+        if (!dmalloc(&t->lk_fiber, H + 1) || !dmalloc(&t->lk_keys, H + 1) || !dmalloc(&t->lk_begin, H + 1) ||
+            !dmalloc(&t->lk_len, H + 1) || !dmalloc(&t->lk_scan, H + 1) || !dmalloc(&t->lk_acc, (size_t)H * R))
+            return fail(s, KRP_ENOMEM, "sparse lookup scratch allocation failed");
+        t->lk_n = (size_t)H + 1;
+        t->lk_acc_n = (size_t)H * R;
+    }
+    e = cudaMemsetAsync(t->lk_keys, 0xFF, (size_t)H * sizeof(unsigned long long), s->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(t->lk_acc, 0, (size_t)H * R * sizeof(float), s->stream);
+    if (e != cudaSuccess) return cuda_check(s, e, "lookup table memset");
+    const int64_t g0 = std::min<int64_t>((J + 255) / 256, (int64_t)s->num_sms * 8);
+    fiber_find<<<(unsigned)g0, 256, 0, s->stream>>>(P, t->lk_fiber); count_launch();
+    const int64_t g1 = std::min<int64_t>((J + 7) / 8, (int64_t)s->num_sms * 16);
+    merge_samples<<<(unsigned)g1, 256, 0, s->stream>>>(P, t->lk_fiber, t->lk_keys, t->lk_acc, log2H); count_launch();
+    const int64_t gs = std::min<int64_t>((H + 255) / 256, (int64_t)s->num_sms * 8);
+    slot_lengths<<<(unsigned)gs, 256, 0, s->stream>>>(P, t->lk_keys, H, t->lk_begin, t->lk_len); count_launch();
+    scan_lengths<<<1, 1024, 0, s->stream>>>(t->lk_len, t->lk_scan, H); count_launch();
+    fiber_scatter<<<(unsigned)(s->num_sms * 16), 256, 0, s->stream>>>(P, t->lk_begin, t->lk_scan, H, t->lk_acc);
+    count_launch();
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_check(s, e, "fiber_scatter launch");
+    if (e != cudaSuccess) return cuda_check(s, e, "fiber lookup launch");
     krp_status st = normal_inverse(s, J, SA, flags);
     if (st != KRP_OK) return st;
     const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
@@ -365,7 +502,7 @@ extern "C" krp_status krp_cp_als_sweep(krp_sampler* s, const krp_sptensor* t, in
         const int64_t rows_per = 256 / R;
         const int64_t g = std::min<int64_t>((s->I[j] + rows_per - 1) / rows_per, (int64_t)s->num_sms * 4);
         col_sumsq<<<(unsigned)g, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq); count_launch();
-        const int64_t g2 = std::min<int64_t>((s->I[j] * R + 255) / 256, (int64_t)s->num_sms * 8);
+        const int64_t g2 = std::min<int64_t>((s->I[j] + 7) / 8, (int64_t)s->num_sms * 8);
         col_scale<<<(unsigned)g2, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq, sigma); count_launch();
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(s, e, "normalise launch");
