@@ -87,6 +87,18 @@ krp_status krp_set_factor(krp_sampler* s, int j, const float* U);
 /* Same as krp_set_factor with an explicit precision for this rebuild. */
 krp_status krp_set_factor_prec(krp_sampler* s, int j, const float* U, int precision);
 
+/* Single-element updates (App. A, UpdateSampler): for q = 0..n-1 in order,
+ * U_j[rows[q], cols[q]] := values[q] (rows, cols int32 and values FP32, device
+ * arrays of n entries).  Each update changes row and column cols[q] of the
+ * stored Grams on the leaf-to-root path of its row and of the FP64 root:
+ * O(R log(I_j/F)) work instead of a rebuild.  An out-of-range (row, col) is
+ * skipped and sets KRP_EINVAL on the device status.  FP32 tree entries take
+ * the FP32-rounded change, so after many updates a rebuild (krp_set_factor)
+ * restores the build's rounding.  The next krp_sample_draw needs a new
+ * krp_sample_prepare (krp_sample does both). */
+krp_status krp_update_entries(krp_sampler* s, int j, int64_t n, const int32_t* rows, const int32_t* cols,
+                              const float* values);
+
 /* ------------------------------------------------------------------------
  * Sampling (Thm 1.1 part 2; Alg. 2 KRPSample; Alg. 4 RowSample; Thm 3.1).
  *

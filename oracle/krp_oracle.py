@@ -499,6 +499,29 @@ class TreeFP64:
         return np.einsum("sab,sab->s", self.nodes[v], Y_h)
 
 
+def tree_update_entry(tree, r, c, u_new):
+    """UpdateSampler (App. A, efficient single-element updates) on an FP64 tree:
+    U[r, c] := u_new.  With d = u_new - U[r, c] and the old row x = U[r, :],
+    the leaf holding row r gets G[c, :] += d x, G[:, c] += d xᵀ, G[c, c] += d²;
+    every ancestor is then the sum of its two children again, which changes
+    only its row and column c.  Modifies tree.nodes and tree.U in place."""
+    U = tree.U if tree.U.flags.writeable else tree.U.copy()
+    x = U[r].copy()
+    d = float(u_new) - x[c]
+    v = tree.L + r // tree.F
+    G = tree.nodes[v]
+    G[c, :] += d * x
+    G[:, c] += d * x
+    G[c, c] += d * d
+    while v > 1:
+        prev, v = v, v // 2
+        sib = prev ^ 1
+        tree.nodes[v] = tree.nodes[sib] + tree.nodes[prev]
+    U[r, c] = u_new
+    tree.U = U
+    return tree
+
+
 def tree_sample_batch(tree, Y, H, u):
     """Alg. 4 for J history vectors H (J,R) and uniforms u (J,), Y p.s.d.
     Returns (rows, tau, left_edges, right_edges, C) — edges of the chosen bin."""

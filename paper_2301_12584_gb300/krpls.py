@@ -51,6 +51,7 @@ SIGNATURES = [
     ("krp_get_tree", _INT, [_P, _INT, _P, _I64]),
     ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
     ("krp_planted_rows", _INT, [_P, _INT, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
+    ("krp_update_entries", _INT, [_P, _INT, _I64, _P, _P, _P]),
     ("krp_capture_begin", _INT, [_P]),
     ("krp_capture_end", _INT, [_P, C.POINTER(_I64)]),
     ("krp_replay", _INT, [_P]),
@@ -170,6 +171,12 @@ class Sampler:
     def solve_dense(self, J, SA, weight, B_rows, nrhs, X, flags=0):
         self._check(self._lib.krp_solve_dense(self.h, int(J), _P(_ptr(SA)), _P(_ptr(weight)), _P(_ptr(B_rows)),
                                               int(nrhs), _P(_ptr(X)), int(flags)))
+
+    def update_entries(self, j, rows, cols, values):
+        """rows, cols: device int32 tensors; values: device float32 tensor (same length)."""
+        n = int(rows.numel()) if hasattr(rows, "numel") else len(rows)
+        self._check(self._lib.krp_update_entries(self.h, int(j), n, _P(_ptr(rows)), _P(_ptr(cols)),
+                                                 _P(_ptr(values))))
 
     def capture_begin(self):
         self._check(self._lib.krp_capture_begin(self.h))
@@ -344,6 +351,12 @@ class Batch:
 
     def sync_status(self):
         return int(self._lib.krp_batch_sync_status(self.h))
+
+    def update_entries(self, j, rows, cols, values):
+        """rows, cols: device int32 tensors; values: device float32 tensor (same length)."""
+        n = int(rows.numel()) if hasattr(rows, "numel") else len(rows)
+        self._check(self._lib.krp_update_entries(self.h, int(j), n, _P(_ptr(rows)), _P(_ptr(cols)),
+                                                 _P(_ptr(values))))
 
     def capture_begin(self):
         self._check(self._lib.krp_batch_capture_begin(self.h))

@@ -455,3 +455,49 @@ def test_prepare_matches_fp64_oracle(I, R, excl, rankdef):
                 v, vo = V[:, u], prep.V[k][:, u]
                 assert min(np.abs(v - vo).max(), np.abs(v + vo).max()) < 1e-8, (k, u)
     s.close()
+
+
+# ------------------------------------------------- single-element updates ----
+def test_single_entry_updates_match_rebuild_and_oracle():
+    """krp_update_entries (App. A, UpdateSampler) against a tree built from the
+    updated factor, the FP64 oracle tree after the same updates, and the
+    sampler's draws on the updated factors."""
+    rng = np.random.default_rng(31)
+    I, R, F = 1000, 8, 8
+    Us = synth.gaussian_factors(3, I, R, seed=32)
+    s = sampler_for(Us, F)
+    ups = [(int(rng.integers(I)), int(rng.integers(R)), float(rng.standard_normal() * 2)) for _ in range(40)]
+    ups += [(7, 3, 1.5), (7, 5, -0.25), (7, 3, 0.75), (999, 0, 4.0)]      # repeated row, last row
+    rows = torch.tensor([u[0] for u in ups], dtype=torch.int32, device=DEV)
+    cols = torch.tensor([u[1] for u in ups], dtype=torch.int32, device=DEV)
+    vals = torch.tensor([u[2] for u in ups], dtype=torch.float32, device=DEV)
+    s.update_entries(1, rows, cols, vals)
+    assert s.sync_status() == 0
+    U1 = Us[1].astype(np.float64).copy()
+    otree = O.TreeFP64(Us[1].astype(np.float64), F)
+    for r, c, v in ups:
+        U1[r, c] = np.float32(v)
+        O.tree_update_entry(otree, r, c, float(np.float32(v)))
+    L, d, Tp = s.tree_info(1)
+    got = s.get_tree(1)
+    T = R * (R + 1) // 2
+    for slot in range(L):
+        h = 1 if slot == 0 else 2 * slot
+        lo, hi = O.node_rows(h, L, F, I)
+        bound = np.abs(U1[lo:hi]).T @ np.abs(U1[lo:hi])
+        G = unpack(got[slot], R)
+        assert np.all(np.abs(G - otree.nodes[h]) <= 4e-5 * bound + 1e-6), slot
+        assert np.all(np.abs(G - U1[lo:hi].T @ U1[lo:hi]) <= 4e-5 * bound + 1e-6), slot
+        assert np.all(got[slot][T:] == 0)
+    # draws on the updated factors follow the oracle on them
+    Us_new = [Us[0], U1.astype(np.float32), Us[2]]
+    out = draw(s, Us_new, -1, 1 << 14, seed=5, draw_id=1)
+    ref = O.krp_sample([U.astype(np.float64) for U in Us_new], -1, 1 << 14, 5, 1, record=True)
+    mism = check_index_parity(out["idx"], ref, 1 << 14)
+    assert mism < max(1.0, 1e-4 * (1 << 14))
+    # an out-of-range update is skipped and reported
+    s.update_entries(1, torch.tensor([I], dtype=torch.int32, device=DEV),
+                     torch.tensor([0], dtype=torch.int32, device=DEV),
+                     torch.tensor([1.0], device=DEV))
+    assert s.sync_status() == -1
+    s.close()

@@ -459,3 +459,32 @@ def test_planted_rhs_noise_is_standard_normal_and_keyed_by_tuple():
     np.testing.assert_array_equal(B[0], B[2])
     np.testing.assert_array_equal(B[1], B[3])
     assert not np.allclose(O.planted_rhs(Us, -1, rep, X, 1.0, 12), B)
+
+
+def test_single_entry_update_equals_rebuild():
+    """UpdateSampler (App. A): after a sequence of single-entry updates, some
+    to the same row, every node Gram equals the tree rebuilt from the updated
+    matrix (FP64 to 1e-12 relative)."""
+    rng = np.random.default_rng(21)
+    I, R, F = 37, 5, 4
+    U = rng.standard_normal((I, R))
+    tree = O.TreeFP64(U.copy(), F)
+    U2 = U.copy()
+    for r, c in [(0, 0), (36, 4), (17, 2), (17, 3), (17, 2), (5, 1)]:
+        val = float(rng.standard_normal()) * 3.0
+        O.tree_update_entry(tree, r, c, val)
+        U2[r, c] = val
+    ref = O.TreeFP64(U2, F)
+    scale = np.abs(ref.nodes).max()
+    assert np.abs(tree.nodes - ref.nodes).max() <= 1e-12 * scale
+    np.testing.assert_array_equal(tree.U, U2)
+    # a planted mistake (the d^2 term dropped) is caught
+    bad = O.TreeFP64(U.copy(), F)
+    x = bad.U[3].copy()
+    d = 2.0 - x[1]
+    v = bad.L + 3 // F
+    bad.nodes[v][1, :] += d * x
+    bad.nodes[v][:, 1] += d * x
+    U3 = U.copy()
+    U3[3, 1] = 2.0
+    assert np.abs(bad.nodes[v] - O.TreeFP64(U3, F).nodes[v]).max() > 1e-6
