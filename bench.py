@@ -11,8 +11,8 @@ needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--precision fp32|bf16x3] [--no-cpu-baseline]
-                  [--workload sampler|batch512|rank_sweep|sparse_als] [--rank R]
-                  [--ranks 25,50,100] [--nnz N] [--sweeps S]
+                  [--workload sampler|batch512|rank_sweep|sparse_als|accuracy] [--rank R]
+                  [--ranks 25,50,100] [--nnz N] [--sweeps S] [--trials T]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
 (independent draws, disjoint draw ids); value = samples of all ranks / max time.
@@ -20,7 +20,8 @@ The default workload is the headline line; batch512 (512 small least-squares
 problems: per-problem launches vs one launch per phase vs graph replay) and
 rank_sweep (N=4, 2^20 x R, U(-1,1), J=2^17, dense solve with 8 planted
 right-hand sides) and sparse_als (STS-CP on a 2^22 x 2^22 x 2^14 Zipf tensor:
-FP32, BF16x3 and graph-replayed sweeps) print their own lines.
+FP32, BF16x3 and graph-replayed sweeps) and accuracy (Sec. 4.2: distortion
+and residual ratio for N in {3..9}, R in {16, 32, 64}) print their own lines.
 """
 from __future__ import annotations
 
@@ -56,7 +57,8 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=20)
-    ap.add_argument("--workload", default="sampler", choices=["sampler", "batch512", "rank_sweep", "sparse_als"],
+    ap.add_argument("--workload", default="sampler",
+                    choices=["sampler", "batch512", "rank_sweep", "sparse_als", "accuracy"],
                     help="sampler: the headline line; batch512: 512 small least-squares problems "
                          "(per-problem launches vs one launch per phase vs graph replay); "
                          "rank_sweep: N=4, I=2^20, U(-1,1), J=2^17 at --rank R")
@@ -64,6 +66,7 @@ def parse():
     ap.add_argument("--ranks", default="25,50,100", help="sparse_als: decomposition ranks")
     ap.add_argument("--nnz", type=int, default=200_000_000, help="sparse_als: nonzeros")
     ap.add_argument("--sweeps", type=int, default=20, help="sparse_als: ALS sweeps per configuration")
+    ap.add_argument("--trials", type=int, default=5, help="accuracy: problems per (N, R)")
     return ap.parse_args()
 
 
@@ -447,6 +450,69 @@ def run_sparse_als(args):
     }), flush=True)
 
 
+def run_accuracy(args):
+    """Sec. 4.2 least squares: A = U_1 ⊙ ... ⊙ U_N (I = 2^16, N(0,1) with 1% of
+    entries x10), b = c_1 ⊗ ... ⊗ c_N (N(0,1)), J = 5000 leverage samples;
+    distortion D = kappa(SQ) - 1 and eps = residual / optimal residual - 1
+    (both evaluated without forming A or b) for N in {3, 5, 7, 9} and R in
+    {16, 32, 64}.  Timed: build + sample + right-hand side + solve per problem."""
+    import torch
+    from oracle import krp_oracle as O
+    from paper_2301_12584_gb300 import krpls, synth
+    from paper_2301_12584_gb300.krpls import Sampler
+    I, J = 1 << 16, 5000
+    dev = torch.device("cuda", 0)
+    krpls.lib()
+    stream = torch.cuda.Stream(device=dev)
+    rows = []
+    for N in (3, 5, 7, 9):
+        for R in (16, 32, 64):
+            Ds, eps, ms = [], [], []
+            for trial in range(max(1, int(args.trials))):
+                seed = 1000 * N + 10 * R + trial
+                Us = synth.skewed_entry_factors(N, I, R, seed=seed)
+                rng = np.random.default_rng(seed + 7)
+                cs = [rng.standard_normal(I).astype(np.float32) for _ in range(N)]
+                Ud = [torch.from_numpy(U).to(dev) for U in Us]
+                cd = [torch.from_numpy(c).to(dev) for c in cs]
+                idx = torch.zeros((N, J), dtype=torch.int32, device=dev)
+                w = torch.zeros(J, device=dev)
+                SA = torch.zeros((J, R), device=dev)
+                B = torch.zeros((J, 1), device=dev)
+                X = torch.zeros((R, 1), device=dev)
+                s = Sampler([I] * N, R, 0, stream=stream)
+                torch.cuda.synchronize()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                with torch.cuda.stream(stream):
+                    a.record(stream)
+                    for k in range(N):
+                        s.set_factor(k, Ud[k])
+                    s.sample(-1, J, seed, 0, idx, w, None, SA)
+                    s.kron_rows(-1, J, idx, cd, B)
+                    s.solve_dense(J, SA, w, B, 1, X)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                assert s.sync_status() == 0, s.last_error()
+                ms.append(a.elapsed_time(b))
+                D, _ = s.sketch_distortion(-1, J, SA)
+                Ds.append(D)
+                U64 = [U.astype(np.float64) for U in Us]
+                c64 = [c.astype(np.float64) for c in cs]
+                res, G, Atb = O.kron_lstsq_residual(U64, -1, c64, X.cpu().numpy()[:, 0].astype(np.float64))
+                res_opt, _, _ = O.kron_lstsq_residual(U64, -1, c64, np.linalg.solve(G, Atb))
+                eps.append(res / res_opt - 1.0)
+                s.close()
+            rows.append({"N": N, "R": R, "D_mean": float(np.mean(Ds)), "eps_mean": float(np.mean(eps)),
+                         "eps_max": float(np.max(eps)), "ms_per_problem_median": float(np.median(ms[1:] or ms))})
+    print(json.dumps({
+        "metric": "least-squares accuracy: distortion D and residual ratio eps (Sec. 4.2), I=2^16, J=5000",
+        "value": float(np.mean([r["eps_mean"] for r in rows])), "unit": "mean eps", "higher_is_better": False,
+        "n_gpus": 1, "steps": int(args.trials), "dtype": "f32", "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": "accuracy_I2^16_J5000_N{3,5,7,9}_R{16,32,64}", "trials": int(args.trials)},
+        "results": rows,
+    }), flush=True)
+
+
 # ------------------------------------------------------------------ ours ----
 def main():
     args = parse()
@@ -455,7 +521,8 @@ def main():
     if args.workload != "sampler" and args.impl == "ours":
         if world > 1 and rank != 0:
             return
-        {"batch512": run_batch512, "rank_sweep": run_rank_sweep, "sparse_als": run_sparse_als}[args.workload](args)
+        {"batch512": run_batch512, "rank_sweep": run_rank_sweep, "sparse_als": run_sparse_als,
+         "accuracy": run_accuracy}[args.workload](args)
         return
     if args.impl == "reference":
         if world > 1:

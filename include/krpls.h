@@ -269,6 +269,23 @@ krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_
 krp_status krp_get_prep(const krp_sampler* s, int k, double* lam_host, double* V_host,
                         double* Gplus_host, int* rank_host);
 
+/* Least-squares accuracy (Sec. 4.2).
+ * krp_kron_rows: B_rows[s] = Π_{k != exclude_j} c_k[idx[k][s]], the entries of
+ * b = c_1 ⊗ ... ⊗ c_N at the sampled tuples (black-box access: b is never
+ * formed).  c_host[k]: device pointer to c_k (I_k floats; NULL allowed for
+ * k = exclude_j); B_rows: J floats (device).
+ * krp_sketch_distortion: D(S, A) = kappa(SQ) - 1 (Eq. distortion_defn) for the
+ * sketch SA (J x R, device, e.g. krp_sample's SA) of A = ⊙_{k != exclude_j} U_k,
+ * without forming A or a basis of its range: kappa(SQ) = kappa(SA V Σ⁻¹) with
+ * AᵀA = ⊛ U_kᵀU_k = V Σ² Vᵀ (appendix on computing sketch distortion), from
+ * FP32 partial sums of SAᵀSA and FP64 eigendecompositions.  Needs a
+ * preparation (krp_sample / krp_sample_prepare) since the last factor change;
+ * writes D (inf if SQ is rank-deficient) and rank(A) to host; synchronous. */
+krp_status krp_kron_rows(krp_sampler* s, int exclude_j, int64_t J, const int32_t* idx, const float* const* c_host,
+                         float* B_rows);
+krp_status krp_sketch_distortion(krp_sampler* s, int exclude_j, int64_t J, const float* SA, double* D_host,
+                                 int* rank_host);
+
 /* CUDA-graph capture of a sampler's calls (no counterpart in the paper):
  * between krp_capture_begin and krp_capture_end the sampler's calls on its
  * stream are recorded, not run (end reports the node count); krp_replay runs

@@ -620,3 +620,47 @@ def planted_rhs(Us, exclude, idx, X_true, sigma, seed):
     u1, u2 = u32_to_open_unit(w[..., 0]), u32_to_open_unit(w[..., 1])
     xi = np.sqrt(-2.0 * np.log(u1)) * np.cos(2.0 * np.pi * u2)
     return A @ X_true + float(sigma) * xi
+
+
+def sketch_distortion(Us, exclude, idx, weight):
+    """Distortion D(S, A) = kappa(SQ) - 1 (Sec. 4.2, Eq. distortion_defn) by its
+    definition: Q = orthonormal basis of range(A) from the SVD of the
+    materialised A (rank from the SVD), SQ = the sampled, reweighted rows of Q,
+    kappa = largest / smallest nonzero singular value.  Small cases only."""
+    incl = included_factors(len(Us), exclude)
+    A = khatri_rao([np.asarray(Us[k], np.float64) for k in incl])
+    Uq, sv, _ = np.linalg.svd(A, full_matrices=False)
+    r = int((sv > A.shape[1] * np.finfo(float).eps * sv[0]).sum())
+    Q = Uq[:, :r]
+    lin = linear_index(np.asarray(idx, np.int64), tuple(Us[k].shape[0] for k in incl))
+    SQ = np.asarray(weight, np.float64)[:, None] * Q[lin]
+    s = np.linalg.svd(SQ, compute_uv=False)
+    s = s[s > s[0] * 1e-13]
+    return s[0] / s[-1] - 1.0
+
+
+def kron_rows(cs, exclude, idx):
+    """Entries of b = c_1 ⊗ ... ⊗ c_N (Sec. 4.2's right-hand side) at the sampled
+    tuples: b[t] = Π_k c_k[t_k] over the included factors."""
+    incl = included_factors(len(cs), exclude)
+    out = np.ones(np.asarray(idx).shape[1])
+    for p, k in enumerate(incl):
+        out = out * np.asarray(cs[k], np.float64)[np.asarray(idx[p], np.int64)]
+    return out
+
+
+def kron_lstsq_residual(Us, exclude, cs, x):
+    """||A x - b|| for A = ⊙ U_k and b = ⊗ c_k without materialising either:
+    ||Ax - b||² = xᵀ(⊛ U_kᵀU_k)x - 2 xᵀ(⊛ U_kᵀ c_k) + Π ||c_k||², with the
+    column identity Aᵀb = ⊛_k U_kᵀ c_k (each column of A is ⊗_k U_k[:, r])."""
+    incl = included_factors(len(Us), exclude)
+    G = hadamard_gram([Us[k] for k in incl])
+    Atb = np.ones(np.asarray(Us[incl[0]]).shape[1])
+    bb = 1.0
+    for k in incl:
+        U = np.asarray(Us[k], np.float64)
+        c = np.asarray(cs[k], np.float64)
+        Atb = Atb * (U.T @ c)
+        bb *= float(c @ c)
+    x = np.asarray(x, np.float64)
+    return float(np.sqrt(max(x @ G @ x - 2.0 * x @ Atb + bb, 0.0))), G, Atb

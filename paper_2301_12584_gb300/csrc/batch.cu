@@ -316,7 +316,8 @@ krp_status krp_batch_create(krp_batch** out, krp_sampler* const* samplers, int P
     // solve: `parts` partial sums per problem for nrhs <= nrhs_max
     std::vector<SolveItem> sol(P);
     size_t sarena = 0;
-    for (int p = 0; p < P; ++p) sarena += (size_t)b->parts * (tri_size(samplers[p]->R) + samplers[p]->R * b->nrhs_max);
+    for (int p = 0; p < P; ++p)
+        sarena += (size_t)b->parts * (tri_size(samplers[p]->R) + samplers[p]->R * b->nrhs_max + 1);
     if (st == KRP_OK) e = cudaMalloc(&b->solve_arena, sarena * sizeof(float));
     if (st == KRP_OK && e == cudaSuccess) {
         size_t o = 0;
@@ -326,7 +327,7 @@ krp_status krp_batch_create(krp_batch** out, krp_sampler* const* samplers, int P
             sol[p].row_off = b->row_off[p];
             sol[p].x_off = b->row_off[p];
             sol[p].part = b->solve_arena + o;
-            o += (size_t)b->parts * (tri_size(samplers[p]->R) + samplers[p]->R * b->nrhs_max);
+            o += (size_t)b->parts * (tri_size(samplers[p]->R) + samplers[p]->R * b->nrhs_max + 1);
         }
         e = upload(&b->solve_dev, sol);
     }

@@ -414,13 +414,14 @@ __global__ void __launch_bounds__(256) krp_descent(DescentParams P) {
         }
         // ---------------- epilogue: probability, weight, fused gather
         make_weights(h);
+        // q_s = ℓ_s / rank, ℓ_s = hᵀG⁺h = lv 2^gexp (G⁺ stored scaled by 2^-gexp)
         const df levd = team_sum_df(node_part(P.Gplus32));
-        const float lev = levd.hi + levd.lo;
-        const float qs = lev / (float)(*P.rank);
-        const float w = ok ? 1.0f / sqrtf((float)P.J * qs) : 0.f;
+        const float lv = (levd.hi + levd.lo) / (float)P.rank[0];
+        const int gexp = P.rank[1];
+        const float w = ok ? ldexpf(1.0f / sqrtf((float)P.J * lv * ((gexp & 1) ? 2.f : 1.f)), -(gexp >> 1)) : 0.f;
         if (tid == 0) {
             P.weight[s] = w;
-            if (P.logq) P.logq[s] = ok ? logf(qs) : -INFINITY;
+            if (P.logq) P.logq[s] = ok ? logf(lv) + (float)gexp * 0.6931471805599453f : -INFINITY;
         }
         if (P.SA)
             for (int a = tid; a < R; a += NT) P.SA[s * R + a] = w * h[a];

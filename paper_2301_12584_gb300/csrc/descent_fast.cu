@@ -447,12 +447,15 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                 part = fmaf(w4[m].w, v.w, part);
             }
         }
+        // q_s = ℓ_s / rank with ℓ_s = hᵀG⁺h = lv 2^gexp (G⁺ is stored scaled by 2^-gexp);
+        // w_s = 1/sqrt(J q_s) formed without q_s itself, which can underflow FP32
         const df lev = refine(part);
-        const float qs = (lev.hi + lev.lo) / (float)(*P.rank);
-        const float w = ok ? 1.0f / sqrtf((float)P.J * qs) : 0.f;
+        const float lv = (lev.hi + lev.lo) / (float)P.rank[0];
+        const int gexp = P.rank[1];
+        const float w = ok ? ldexpf(1.0f / sqrtf((float)P.J * lv * ((gexp & 1) ? 2.f : 1.f)), -(gexp >> 1)) : 0.f;
         if (lane == 0) {
             P.weight[s] = w;
-            if (P.logq) P.logq[s] = ok ? logf(qs) : -INFINITY;
+            if (P.logq) P.logq[s] = ok ? logf(lv) + (float)gexp * 0.6931471805599453f : -INFINITY;
         }
         if (P.SA && lane < R) P.SA[s * R + lane] = w * th[lane];
         __syncwarp();

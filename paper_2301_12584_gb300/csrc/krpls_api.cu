@@ -166,7 +166,7 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     ok = ok && dalloc(&s->G64, N * RR) && dalloc(&s->Gplus64, RR) && dalloc(&s->lam64, (size_t)N * R) &&
          dalloc(&s->V64, N * RR) && dalloc(&s->work64, (size_t)6 * RR * (N + 1) + 256) &&
          dalloc(&s->Gplus32, (size_t)s->Tp) && dalloc(&s->etree, (size_t)N * s->Rp * s->Tp) &&
-         dalloc(&s->V32, N * RR) && dalloc(&s->V32lo, N * RR) && dalloc(&s->rank_dev, 1) && dalloc(&s->status, 1) &&
+         dalloc(&s->V32, N * RR) && dalloc(&s->V32lo, N * RR) && dalloc(&s->rank_dev, 2) && dalloc(&s->status, 1) &&
          dalloc(&s->solve64, 3 * RR + 128 * (size_t)R);
     if (ok) ok = cudaMemsetAsync(s->status, 0, sizeof(int), s->stream) == cudaSuccess;
     if (ok) ok = cudaMemsetAsync(s->etree, 0, (size_t)N * s->Rp * s->Tp * 4, s->stream) == cudaSuccess;

@@ -21,10 +21,10 @@ namespace krp {
 // kernels defined in solve.cu
 __global__ void normal_partial(const float* __restrict__ SA, const float* __restrict__ w,
                                const float* __restrict__ B, int64_t J, int R, int nrhs, int64_t rows_per_cta,
-                               float* __restrict__ part);
+                               float* __restrict__ part, float* __restrict__ part_exp);
 __global__ void normal_solve(const float* __restrict__ part, int nparts, int R, int nrhs, int mode, int flags,
                             float* __restrict__ X, double* __restrict__ Xd, int* __restrict__ status,
-                            double* __restrict__ gbuf);
+                            double* __restrict__ gbuf, const float* __restrict__ part_exp);
 
 }  // namespace krp
 
@@ -37,9 +37,10 @@ constexpr int NA_MAX_PARTS = 512;
 constexpr int NA_MAX_OUT = NA_MAX_R * (NA_MAX_R + 1) / 2 + NA_MAX_R * NA_MAX_NRHS;  // 1040 floats per partial
 
 // Scratch shared by every call on a device: NA_MAX_PARTS partials of
-// NA_MAX_OUT floats (2.13 MB).  Each call overwrites the partials it uses
-// before reading them, so the array needs no initial value.
-static __device__ __align__(256) float g_krp_noalloc_scratch[NA_MAX_PARTS * NA_MAX_OUT];
+// NA_MAX_OUT floats, then one exponent per partial (2.13 MB).  Each call
+// overwrites the partials it uses before reading them, so the array needs no
+// initial value.
+static __device__ __align__(256) float g_krp_noalloc_scratch[NA_MAX_PARTS * NA_MAX_OUT + NA_MAX_PARTS];
 
 // Device address of the scratch, resolved once per device (the symbol's name
 // is only a host-side stand-in and must not be passed to a kernel).
@@ -97,11 +98,13 @@ extern "C" krp_status krp_solve_dense_noalloc(int64_t J, int R, const float* SA,
     e = cudaMemsetAsync(status, 0, sizeof(int), st);
     if (e != cudaSuccess) return fail(nullptr, KRP_ECUDA, std::string("krp_solve_dense_noalloc: ") + cudaGetErrorString(e));
     const dim3 grid1(nparts, (nout + 256 * 8 - 1) / (256 * 8));
+    float* part_exp = part + (size_t)nparts * nout;
     normal_partial<<<grid1, 256, (size_t)32 * (R + nrhs) * 4, st>>>(SA, weight, B_rows, J, R, nrhs, rows_per_cta,
-                                                                   part); count_launch();
+                                                                   part, part_exp); count_launch();
     const size_t small = 64 * 8 + 2 * (R / 2 + 1) * 8 + 2 * (R / 2 + 1) * 4 + 16;
     const size_t mats = (size_t)(2 * R * R + R * nrhs) * 8;
-    normal_solve<<<1, 256, small + mats, st>>>(part, nparts, R, nrhs, 0, flags, X, nullptr, status, nullptr); count_launch();
+    normal_solve<<<1, 256, small + mats, st>>>(part, nparts, R, nrhs, 0, flags, X, nullptr, status, nullptr,
+                                               part_exp); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return fail(nullptr, KRP_ECUDA, std::string("krp_solve_dense_noalloc: ") + cudaGetErrorString(e));
     return KRP_OK;

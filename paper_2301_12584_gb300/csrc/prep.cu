@@ -296,6 +296,21 @@ __device__ __forceinline__ void prep_pinv_body(const PrepParams& P, int N, int e
         }
     }
     __syncthreads();
+    // FP32 copy of G⁺ scaled by 2^-gexp (gexp from its largest entry, kept in
+    // rank_out[1]): G⁺ ~ 1 / Π_k ||U_k||² leaves the FP32 range for many or
+    // large factors, while the weights need only hᵀ G⁺ h up to that factor
+    double gm = 0.0;
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) gm = fmax(gm, fabs(Gplus64[e]));
+    for (int o = 16; o > 0; o >>= 1) gm = fmax(gm, __shfl_xor_sync(0xffffffffu, gm, o));
+    if ((threadIdx.x & 31) == 0) s_c1[threadIdx.x >> 5] = gm;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmax(m, s_c1[q]);
+        s_c1[0] = m;
+    }
+    __syncthreads();
+    const int gexp = (s_c1[0] > 0.0 && isfinite(s_c1[0])) ? ilogb(s_c1[0]) : 0;
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         float v = 0.f;
         if (e < tri_size(R)) {
@@ -304,12 +319,13 @@ __device__ __forceinline__ void prep_pinv_body(const PrepParams& P, int N, int e
                 rem -= R - i;
                 ++i;
             }
-            v = (float)Gplus64[i * R + i + rem];
+            v = (float)ldexp(Gplus64[i * R + i + rem], -gexp);
         }
         Gplus32[e] = v;
     }
     if (threadIdx.x == 0) {
-        *rank_out = rank;
+        rank_out[0] = rank;
+        rank_out[1] = gexp;
         if (rank == 0) set_status(status, KRP_EZERO);
     }
 }
@@ -361,6 +377,13 @@ __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R,
     const double* Gk = G64 + (size_t)k * RR;
     float* et = etree + (size_t)k * Rp * Tp;
     const int T = tri_size(R);
+    // E_k's masses are compared only with each other, so its nodes carry a
+    // power-of-two scale that keeps them near 1 in FP32 (λ_max(G_{>k}) can
+    // be ~2^-144 for the last of many factors)
+    double gkmax = 0.0;
+    for (int i = 0; i < R; ++i) gkmax = fmax(gkmax, Gk[i * R + i]);
+    const double emag = lk[R - 1] * gkmax;
+    const double esc = (emag > 0.0 && isfinite(emag)) ? ldexp(1.0, -ilogb(emag)) : 1.0;
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         if (e >= T) {
             for (int sl = 0; sl < Rp; ++sl) et[(size_t)sl * Tp + e] = 0.f;
@@ -372,7 +395,7 @@ __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R,
             ++i;
         }
         const int j = i + rem;
-        const double gij = Gk[i * R + j];
+        const double gij = Gk[i * R + j] * esc;
         double stk[8];
         for (int u = 0; u < Rp; ++u) {
             double val = (u < R) ? lk[u] * Vk[i * R + u] * Vk[j * R + u] : 0.0;

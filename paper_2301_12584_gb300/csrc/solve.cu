@@ -5,8 +5,12 @@
 //
 // normal_partial: grid-strided CTAs each reduce a contiguous chunk of rows
 // into FP32 partial sums of the upper triangle of M and of Z (rows staged in
-// shared memory, one output per thread slot).  normal_solve (one CTA): FP64
-// sum of the partials in a fixed order, Cholesky, triangular solves.
+// shared memory, one output per thread slot).  Each chunk is first scaled by
+// a power of two 2^-e (e from its largest entry, stored in part_exp) so that
+// the FP32 sums neither overflow nor underflow when the weights
+// 1/sqrt(J q) are far from 1 (many factors: q ~ 2^-144 at N = 9, I = 2^16).
+// normal_solve (one CTA): FP64 sum of the partials times 2^(2e) in a fixed
+// order, Cholesky, triangular solves.
 #include "common.cuh"
 #include "internal.h"
 #include "jacobi.cuh"
@@ -23,8 +27,10 @@ constexpr int SOLVE_ROWS = 32;  // rows per shared-memory tile
 // CTA (px, py): rows [px rows_per_cta, (px+1) rows_per_cta), outputs chunk py.
 __device__ __forceinline__ void normal_partial_body(const float* __restrict__ SA, const float* __restrict__ w,
                                                     const float* __restrict__ B, int64_t J, int R, int nrhs,
-                                                    int64_t rows_per_cta, float* __restrict__ part, int px, int py) {
+                                                    int64_t rows_per_cta, float* __restrict__ part,
+                                                    float* __restrict__ part_exp, int px, int py) {
     extern __shared__ __align__(16) float sm[];
+    __shared__ float s_max[32];
     float* sA = sm;                          // SOLVE_ROWS x R
     float* sB = sA + SOLVE_ROWS * R;         // SOLVE_ROWS x nrhs
     const int T = tri_size(R);
@@ -53,15 +59,32 @@ __device__ __forceinline__ void normal_partial_body(const float* __restrict__ SA
     }
     const int64_t r0 = (int64_t)px * rows_per_cta;
     const int64_t r1 = min(J, r0 + rows_per_cta);
+    // the chunk's scale 2^-ex from its largest |SA| and |w B| entry
+    float mx = 0.f;
+    for (int64_t e = threadIdx.x; e < (r1 - r0) * R; e += blockDim.x) mx = fmaxf(mx, fabsf(SA[r0 * R + e]));
+    if (B)
+        for (int64_t e = threadIdx.x; e < (r1 - r0) * nrhs; e += blockDim.x)
+            mx = fmaxf(mx, fabsf(w[r0 + e / nrhs] * B[r0 * nrhs + e]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) s_max[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) m = fmaxf(m, s_max[q]);
+        s_max[0] = m;
+    }
+    __syncthreads();
+    const int ex = (s_max[0] > 0.f && isfinite(s_max[0])) ? ilogbf(s_max[0]) : 0;
+    if (part_exp && py == 0 && threadIdx.x == 0) part_exp[px] = (float)ex;
     for (int64_t base = r0; base < r1; base += SOLVE_ROWS) {
         const int nr = (int)min((int64_t)SOLVE_ROWS, r1 - base);
         __syncthreads();
         for (int e = threadIdx.x; e < SOLVE_ROWS * R; e += blockDim.x)
-            sA[e] = (e / R < nr) ? SA[(base + e / R) * R + e % R] : 0.f;
+            sA[e] = (e / R < nr) ? ldexpf(SA[(base + e / R) * R + e % R], -ex) : 0.f;
         if (B)
             for (int e = threadIdx.x; e < SOLVE_ROWS * nrhs; e += blockDim.x) {
                 const int r = e / nrhs;
-                sB[e] = (r < nr) ? w[base + r] * B[(base + r) * nrhs + e % nrhs] : 0.f;
+                sB[e] = (r < nr) ? ldexpf(w[base + r] * B[(base + r) * nrhs + e % nrhs], -ex) : 0.f;
             }
         __syncthreads();
 #pragma unroll
@@ -85,10 +108,13 @@ __device__ __forceinline__ void normal_partial_body(const float* __restrict__ SA
     }
 }
 
+// part_exp: one float per partial (the chunk's exponent), e.g. right after the
+// nparts x nout partials.
 __global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ SA, const float* __restrict__ w,
                                                       const float* __restrict__ B, int64_t J, int R, int nrhs,
-                                                      int64_t rows_per_cta, float* __restrict__ part) {
-    normal_partial_body(SA, w, B, J, R, nrhs, rows_per_cta, part, blockIdx.x, blockIdx.y);
+                                                      int64_t rows_per_cta, float* __restrict__ part,
+                                                      float* __restrict__ part_exp) {
+    normal_partial_body(SA, w, B, J, R, nrhs, rows_per_cta, part, part_exp, blockIdx.x, blockIdx.y);
 }
 
 // One CTA.  mode 0: X = M⁻¹ Z (R x nrhs) written as FP32 to X;
@@ -97,7 +123,7 @@ __global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ 
 __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part, int nparts, int R, int nrhs,
                                                   int mode, int flags, float* __restrict__ X,
                                                   double* __restrict__ Xd, int* __restrict__ status,
-                                                  double* __restrict__ gbuf) {
+                                                  double* __restrict__ gbuf, const float* __restrict__ part_exp) {
     extern __shared__ __align__(16) double smd[];
     const int RR = R * R;
     const int T = tri_size(R);
@@ -114,7 +140,8 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
     // FP64 reduction of the partials, fixed order
     for (int id = threadIdx.x; id < T; id += blockDim.x) {
         double a = 0.0;
-        for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id];
+        for (int p = 0; p < nparts; ++p)
+            a += ldexp((double)part[(size_t)p * nout + id], part_exp ? 2 * (int)part_exp[p] : 0);
         int i = 0, rem = id;
         while (rem >= R - i) {
             rem -= R - i;
@@ -129,7 +156,8 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
             a = (id / ncol == id % ncol) ? 1.0 : 0.0;
         } else {
             a = 0.0;
-            for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + T + id];
+            for (int p = 0; p < nparts; ++p)
+                a += ldexp((double)part[(size_t)p * nout + T + id], part_exp ? 2 * (int)part_exp[p] : 0);
         }
         Z[id] = a;
     }
@@ -214,8 +242,8 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
 __global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ part, int nparts, int R, int nrhs,
                                                     int mode, int flags, float* __restrict__ X,
                                                     double* __restrict__ Xd, int* __restrict__ status,
-                                                    double* __restrict__ gbuf) {
-    normal_solve_body(part, nparts, R, nrhs, mode, flags, X, Xd, status, gbuf);
+                                                    double* __restrict__ gbuf, const float* __restrict__ part_exp) {
+    normal_solve_body(part, nparts, R, nrhs, mode, flags, X, Xd, status, gbuf, part_exp);
 }
 
 // Batched forms: blockIdx.z (partials) or blockIdx.x (solve) is the problem.
@@ -229,13 +257,15 @@ __global__ void __launch_bounds__(256) normal_partial_batch(const SolveItem* __r
     const int64_t rows_per_cta = (J + it.nparts - 1) / it.nparts;
     normal_partial_body(SA + J * it.row_off, w + (int64_t)blockIdx.z * J,
                         B ? B + (int64_t)blockIdx.z * J * nrhs : nullptr, J, it.R, nrhs, rows_per_cta, it.part,
-                        blockIdx.x, blockIdx.y);
+                        it.part + (size_t)it.nparts * nout, blockIdx.x, blockIdx.y);
 }
 
 __global__ void __launch_bounds__(256) normal_solve_batch(const SolveItem* __restrict__ items, int nrhs, int flags,
                                                           float* __restrict__ X, int* __restrict__ status) {
     const SolveItem& it = items[blockIdx.x];
-    normal_solve_body(it.part, it.nparts, it.R, nrhs, 0, flags, X + it.x_off * nrhs, nullptr, status, nullptr);
+    const int nout = tri_size(it.R) + it.R * nrhs;
+    normal_solve_body(it.part, it.nparts, it.R, nrhs, 0, flags, X + it.x_off * nrhs, nullptr, status, nullptr,
+                      it.part + (size_t)it.nparts * nout);
 }
 
 cudaError_t launch_solve_batch(const SolveItem* items_dev, int P, int max_parts, int Rmax, int64_t J,
@@ -267,7 +297,7 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
     nparts = nparts < 1 ? 1 : nparts;
     const int64_t rows_per_cta = (J + nparts - 1) / nparts;
     const int ncol = mode == 1 ? R : nrhs;
-    const size_t need = (size_t)nparts * nout;
+    const size_t need = (size_t)nparts * nout + nparts;  // partials, then their exponents
     const size_t need64 = (size_t)2 * R * R + (size_t)R * ncol + (size_t)R * R;
     if (need > s->solve_scratch_floats) {
         if (s->solve_scratch) cudaFree(s->solve_scratch);
@@ -279,7 +309,9 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
     }
     const size_t smem1 = (size_t)SOLVE_ROWS * (R + nrhs) * 4;
     const dim3 grid1(nparts, (nout + 256 * 8 - 1) / (256 * 8));
-    normal_partial<<<grid1, 256, smem1, s->stream>>>(SA, weight, B, J, R, nrhs, rows_per_cta, s->solve_scratch); count_launch();
+    float* part_exp = s->solve_scratch + (size_t)nparts * nout;
+    normal_partial<<<grid1, 256, smem1, s->stream>>>(SA, weight, B, J, R, nrhs, rows_per_cta, s->solve_scratch,
+                                                     part_exp); count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "normal_partial launch");
     const size_t small = 64 * 8 + 2 * (R / 2 + 1) * 8 + 2 * (R / 2 + 1) * 4 + 16;
@@ -290,7 +322,7 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
         cudaFuncSetAttribute(normal_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     normal_solve<<<1, 256, smem2, s->stream>>>(s->solve_scratch, nparts, R, nrhs, mode, flags, X,
                                               s->solve64 + (size_t)(2 * R * R + R * 128), s->status,
-                                              in_smem ? nullptr : s->solve64); count_launch();
+                                              in_smem ? nullptr : s->solve64, part_exp); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "normal_solve launch");
     (void)need64;

@@ -52,6 +52,8 @@ SIGNATURES = [
     ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
     ("krp_planted_rows", _INT, [_P, _INT, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
     ("krp_update_entries", _INT, [_P, _INT, _I64, _P, _P, _P]),
+    ("krp_kron_rows", _INT, [_P, _INT, _I64, _P, C.POINTER(_P), _P]),
+    ("krp_sketch_distortion", _INT, [_P, _INT, _I64, _P, C.POINTER(C.c_double), C.POINTER(_INT)]),
     ("krp_capture_begin", _INT, [_P]),
     ("krp_capture_end", _INT, [_P, C.POINTER(_I64)]),
     ("krp_replay", _INT, [_P]),
@@ -171,6 +173,19 @@ class Sampler:
     def solve_dense(self, J, SA, weight, B_rows, nrhs, X, flags=0):
         self._check(self._lib.krp_solve_dense(self.h, int(J), _P(_ptr(SA)), _P(_ptr(weight)), _P(_ptr(B_rows)),
                                               int(nrhs), _P(_ptr(X)), int(flags)))
+
+    def kron_rows(self, exclude_j, J, idx, cs, B_rows):
+        """cs: list of N device vectors (None allowed for the excluded factor)."""
+        arr = (_P * self.N)(*[_ptr(c) for c in cs])
+        self._check(self._lib.krp_kron_rows(self.h, int(exclude_j), int(J), _P(_ptr(idx)), arr, _P(_ptr(B_rows))))
+
+    def sketch_distortion(self, exclude_j, J, SA):
+        """Returns (D, rank(A))."""
+        D = C.c_double()
+        r = _INT()
+        self._check(self._lib.krp_sketch_distortion(self.h, int(exclude_j), int(J), _P(_ptr(SA)), C.byref(D),
+                                                    C.byref(r)))
+        return D.value, r.value
 
     def update_entries(self, j, rows, cols, values):
         """rows, cols: device int32 tensors; values: device float32 tensor (same length)."""
@@ -351,6 +366,19 @@ class Batch:
 
     def sync_status(self):
         return int(self._lib.krp_batch_sync_status(self.h))
+
+    def kron_rows(self, exclude_j, J, idx, cs, B_rows):
+        """cs: list of N device vectors (None allowed for the excluded factor)."""
+        arr = (_P * self.N)(*[_ptr(c) for c in cs])
+        self._check(self._lib.krp_kron_rows(self.h, int(exclude_j), int(J), _P(_ptr(idx)), arr, _P(_ptr(B_rows))))
+
+    def sketch_distortion(self, exclude_j, J, SA):
+        """Returns (D, rank(A))."""
+        D = C.c_double()
+        r = _INT()
+        self._check(self._lib.krp_sketch_distortion(self.h, int(exclude_j), int(J), _P(_ptr(SA)), C.byref(D),
+                                                    C.byref(r)))
+        return D.value, r.value
 
     def update_entries(self, j, rows, cols, values):
         """rows, cols: device int32 tensors; values: device float32 tensor (same length)."""

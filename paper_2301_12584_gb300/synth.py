@@ -57,10 +57,11 @@ def skewed_entry_factors(N, I, R, seed, frac=0.01, scale=10.0, dtype=np.float32)
     """N(0,1) factors with a random `frac` of all entries multiplied by
     `scale` (App. A.13.2 / Sec. 4.2 recipe)."""
     rng = np.random.default_rng(seed)
+    Is = list(I) if np.ndim(I) else [I] * N
     out = []
-    for _ in range(N):
-        U = rng.standard_normal((I, R))
-        mask = rng.random((I, R)) < frac
+    for k in range(N):
+        U = rng.standard_normal((Is[k], R))
+        mask = rng.random((Is[k], R)) < frac
         U[mask] *= scale
         out.append(U.astype(dtype))
     return out

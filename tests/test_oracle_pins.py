@@ -488,3 +488,32 @@ def test_single_entry_update_equals_rebuild():
     U3 = U.copy()
     U3[3, 1] = 2.0
     assert np.abs(bad.nodes[v] - O.TreeFP64(U3, F).nodes[v]).max() > 1e-6
+
+
+def test_distortion_and_kronecker_residual():
+    """Sec. 4.2 accuracy workload: the distortion by its definition (QR basis
+    of the materialised A) is 0 for the identity sampler, equals the
+    appendix's route kappa(SA V Σ⁻¹) from the eigendecomposition of ⊛ U_kᵀU_k,
+    and the Kronecker right-hand side and closed-form residual match the
+    materialised b and ||Ax - b||."""
+    rng = np.random.default_rng(41)
+    Us = [rng.standard_normal((n, 4)) for n in (5, 6, 7)]
+    A = O.khatri_rao(Us)
+    allidx = np.stack(np.unravel_index(np.arange(A.shape[0]), (5, 6, 7)))
+    assert abs(O.sketch_distortion(Us, -1, allidx, np.ones(A.shape[0]))) < 1e-10
+    J = 60
+    idx = np.stack([rng.integers(0, n, J) for n in (5, 6, 7)])
+    w = rng.uniform(0.5, 2.0, J)
+    D = O.sketch_distortion(Us, -1, idx, w)
+    SA = O.sketched_rows(Us, -1, idx, w)
+    lam, V = np.linalg.eigh(O.hadamard_gram(Us))
+    sv = np.linalg.svd(SA @ V @ np.diag(lam ** -0.5), compute_uv=False)
+    assert abs(D - (sv[0] / sv[-1] - 1.0)) <= 1e-9 * max(1.0, D)
+    cs = [rng.standard_normal(n) for n in (5, 6, 7)]
+    b = np.kron(np.kron(cs[0], cs[1]), cs[2])
+    lin = O.linear_index(idx, (5, 6, 7))
+    np.testing.assert_allclose(O.kron_rows(cs, -1, idx), b[lin], rtol=1e-14)
+    x = rng.standard_normal(4)
+    res, G, Atb = O.kron_lstsq_residual(Us, -1, cs, x)
+    np.testing.assert_allclose(Atb, A.T @ b, rtol=1e-12)
+    assert abs(res - np.linalg.norm(A @ x - b)) <= 1e-10 * np.linalg.norm(b)
