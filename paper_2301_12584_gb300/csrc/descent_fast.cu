@@ -207,7 +207,6 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         float mnode = cf;
         // level 0 from the first fetch
         float mA = depth >= 1 ? warp_sum(pr[1]) : 0.f, pA = pr[1];
-        float mB = 0.f, pB = 0.f, mD = 0.f, pD = 0.f;
         bool have_next = false;
         while (lvl < depth && alive) {
             if (lvl > 0) {
@@ -217,13 +216,8 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                     break;
                 pA = partial(stage);
                 mA = warp_sum(pA);
-                if (have_next) {
-                    pB = partial(stage + Tp);
-                    pD = partial(stage + 2 * Tp);
-                    mB = warp_sum(pB);
-                    mD = warp_sum(pD);
-                }
             }
+            bool left;
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
                 df cut;
@@ -231,21 +225,21 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                     trc[2 + 2 * lvl] = mA;
                     trc[3 + 2 * lvl] = mnode;
                 }
-                if (rfirst * F >= nreal_rows || go_left(tau, low, mA, pA, margin, cut)) {
+                left = rfirst * F >= nreal_rows || go_left(tau, low, mA, pA, margin, cut);
+                if (left) {
                     c = 2 * c;
                     mnode = mA;
-                    mA = mB;
-                    pA = pB;
                 } else {
                     c = 2 * c + 1;
                     low = cut;
                     mnode = mnode - mA;
-                    mA = mD;
-                    pA = pD;
                 }
                 ++lvl;
             }
             if (!have_next) continue;
+            // only the chosen child's left child is needed at the next level
+            pA = partial(stage + (left ? Tp : 2 * Tp));
+            mA = warp_sum(pA);
             {
                 const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
                 df cut;
