@@ -57,7 +57,8 @@ __global__ void __launch_bounds__(256) distortion_finish(const float* __restrict
     double* Y = W + RR;      // M Z, then the eigenvectors of W
     for (int e = threadIdx.x; e < T; e += blockDim.x) {
         double a = 0.0;
-        for (int p = 0; p < nparts; ++p) a += ldexp((double)part[(size_t)p * T + e], 2 * (int)part[(size_t)nparts * T + p]);
+        for (int p = 0; p < nparts; ++p)
+            a += (double)part[(size_t)p * T + e] * ldexp(1.0, 2 * (int)part[(size_t)nparts * T + p]);
         int i = 0, rem = e;
         while (rem >= R - i) {
             rem -= R - i;

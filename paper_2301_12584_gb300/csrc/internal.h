@@ -198,6 +198,9 @@ krp_status launch_descent(krp_sampler* s, int exclude_j, int64_t J, uint64_t see
 // R <= 32 path of the descent (descent_fast.cu); false if R is out of range.
 bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
                          float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
+// 32 < R <= 128 path (descent_team.cu): TMA-staged teams of warps; false if R is out of range.
+bool launch_descent_team(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
+                         float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
 cudaError_t launch_wait_timeout_probe(krp_sampler* s, int tries);
 // a6: gather
 krp_status launch_gather(krp_sampler* s, int exclude_j, int64_t J, const int32_t* idx,

@@ -75,16 +75,17 @@ __device__ __forceinline__ void normal_partial_body(const float* __restrict__ SA
     }
     __syncthreads();
     const int ex = (s_max[0] > 0.f && isfinite(s_max[0])) ? ilogbf(s_max[0]) : 0;
+    const float sc = ldexpf(1.f, -ex);  // exact power of two (-126 <= ex <= 127)
     if (part_exp && py == 0 && threadIdx.x == 0) part_exp[px] = (float)ex;
     for (int64_t base = r0; base < r1; base += SOLVE_ROWS) {
         const int nr = (int)min((int64_t)SOLVE_ROWS, r1 - base);
         __syncthreads();
         for (int e = threadIdx.x; e < SOLVE_ROWS * R; e += blockDim.x)
-            sA[e] = (e / R < nr) ? ldexpf(SA[(base + e / R) * R + e % R], -ex) : 0.f;
+            sA[e] = (e / R < nr) ? SA[(base + e / R) * R + e % R] * sc : 0.f;
         if (B)
             for (int e = threadIdx.x; e < SOLVE_ROWS * nrhs; e += blockDim.x) {
                 const int r = e / nrhs;
-                sB[e] = (r < nr) ? ldexpf(w[base + r] * B[(base + r) * nrhs + e % nrhs], -ex) : 0.f;
+                sB[e] = (r < nr) ? (w[base + r] * B[(base + r) * nrhs + e % nrhs]) * sc : 0.f;
             }
         __syncthreads();
 #pragma unroll
@@ -136,12 +137,18 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
     double* Lm = M + RR;                                            // R x R
     double* Z = Lm + RR;                                            // R x ncol
     __shared__ int flag;
+    __shared__ double pscale[1024];  // 2^(2 e_p) of the first 1024 partials
     if (threadIdx.x == 0) flag = 0;
+    for (int p = threadIdx.x; p < nparts && p < 1024; p += blockDim.x)
+        pscale[p] = part_exp ? ldexp(1.0, 2 * (int)part_exp[p]) : 1.0;
+    __syncthreads();
+    auto psc = [&](int p) -> double {
+        return p < 1024 ? pscale[p] : (part_exp ? ldexp(1.0, 2 * (int)part_exp[p]) : 1.0);
+    };
     // FP64 reduction of the partials, fixed order
     for (int id = threadIdx.x; id < T; id += blockDim.x) {
         double a = 0.0;
-        for (int p = 0; p < nparts; ++p)
-            a += ldexp((double)part[(size_t)p * nout + id], part_exp ? 2 * (int)part_exp[p] : 0);
+        for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id] * psc(p);
         int i = 0, rem = id;
         while (rem >= R - i) {
             rem -= R - i;
@@ -156,8 +163,7 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
             a = (id / ncol == id % ncol) ? 1.0 : 0.0;
         } else {
             a = 0.0;
-            for (int p = 0; p < nparts; ++p)
-                a += ldexp((double)part[(size_t)p * nout + T + id], part_exp ? 2 * (int)part_exp[p] : 0);
+            for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + T + id] * psc(p);
         }
         Z[id] = a;
     }

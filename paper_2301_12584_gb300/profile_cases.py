@@ -4,6 +4,7 @@
   python -m paper_2301_12584_gb300.profile_cases build     # tree_leaves_fp32, one factor 2^21 x 32
   python -m paper_2301_12584_gb300.profile_cases build_tc  # tree_leaves_tc (BF16x3 on tcgen05), same factor
   python -m paper_2301_12584_gb300.profile_cases prep      # prep_pinv / prep_eig, R=32, N=3
+  python -m paper_2301_12584_gb300.profile_cases descent64 # krp_descent<64,2> (team kernel), N=4, I=2^18, J=2^15
 
 Each case runs its kernel a few times (the first launches warm up), checks the
 device status and exits 0.  Inputs are the seeded generators of synth.py.
@@ -27,6 +28,19 @@ def descent():
     SA = torch.zeros((J, R), device="cuda")
     for d in range(3):
         s.sample(-1, J, 1, d, idx, w, None, SA)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def descent64():
+    I, R, J = 1 << 18, 64, 1 << 15
+    Us = synth.uniform_factors(4, I, R, seed=0)
+    s = Sampler([I] * 4, R, R)
+    for k in range(4):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    idx = torch.zeros((4, J), dtype=torch.int32, device="cuda")
+    w = torch.zeros(J, device="cuda")
+    for d in range(3):
+        s.sample(-1, J, 1, d, idx, w)
     assert s.sync_status() == 0, s.last_error()
 
 
@@ -55,6 +69,7 @@ def prep():
 
 
 if __name__ == "__main__":
-    {"descent": descent, "build": build, "build_tc": build_tc, "prep": prep}[sys.argv[1]]()
+    {"descent": descent, "descent64": descent64, "build": build, "build_tc": build_tc,
+     "prep": prep}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")
