@@ -262,6 +262,12 @@ krp_status krp_tree_info(const krp_sampler* s, int j, int64_t* L_host, int* dept
  * the upper triangle of G^v packed row by row, then zero padding.  Synchronous. */
 krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_floats);
 
+/* Copy the sampler's copy of factor j (I_j x R row-major FP32, n_floats >=
+ * I_j R) to host memory: what krp_set_factor stored, or what the last
+ * krp_cp_als_sweep (or krp_update_entries) left there.  KRP_EINVAL if factor j
+ * was never set.  Synchronous. */
+krp_status krp_get_factor(const krp_sampler* s, int j, float* out_host, int64_t n_floats);
+
 /* After krp_sample: copy the FP64 eigendecomposition of G_{>k} used for
  * included factor k (lam: R values ascending, V: R x R row-major with
  * eigenvector u in column u), the FP64 G⁺ (R x R) and rank(A).  Any pointer

@@ -65,6 +65,14 @@ __device__ __forceinline__ float warp_sum(float v) {
     for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
     return v;
 }
+// Two FP32 fused multiply-adds in one instruction: (a.x b.x + c.x, a.y b.y + c.y).
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b),
+                   uc = *reinterpret_cast<uint64_t*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
+    return *reinterpret_cast<float2*>(&d);
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);

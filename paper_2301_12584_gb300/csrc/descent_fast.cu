@@ -70,13 +70,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int max_
     }
     return false;
 }
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    uint64_t d;
-    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b),
-                   uc = *reinterpret_cast<uint64_t*>(&c);
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
-    return *reinterpret_cast<float2*>(&d);
-}
 
 // The descent for samples cta*8 + warp, stepping by ncta*8 (ncta CTAs share
 // the J samples of one problem).  P may live in parameter or shared memory.
@@ -163,25 +156,30 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
     };
     // lane partial of the mass of the staged node at `node` (smem)
     auto partial = [&](const float* node) -> float {
-        float2 acc = make_float2(0.f, 0.f);
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 0; m < NCH; ++m) {
             const int c = lane + 32 * m;
             if (c < nc4) {
                 const float4 v = reinterpret_cast<const float4*>(node)[c];
-                acc = ffma2(make_float2(w4[m].x, w4[m].y), make_float2(v.x, v.y), acc);
-                acc = ffma2(make_float2(w4[m].z, w4[m].w), make_float2(v.z, v.w), acc);
+                a0 = ffma2(make_float2(w4[m].x, w4[m].y), make_float2(v.x, v.y), a0);
+                a1 = ffma2(make_float2(w4[m].z, w4[m].w), make_float2(v.z, v.w), a1);
             }
         }
-        return acc.x + acc.y;
+        return (a0.x + a1.x) + (a0.y + a1.y);
     };
     auto refine = [&](float part) -> df { return warp_sum_df(df{part, 0.f}); };
-    // Decision "tau <= low + m" (Alg. 4): FP32 mass when tau is more than
-    // `margin` away from the cutoff, else the double-float mass.
+    // Decision "tau <= low + m" (Alg. 4): FP32 when tau is more than `margin`
+    // away from the cutoff, else the double-float mass.  (tau.hi - low.hi) - m
+    // is within a few ulp(C) + |tau.lo| + |low.lo| < 3e-7 C of tau - low - m;
+    // all three are warp-uniform, so the branch into the warp sum is too.
     auto go_left = [&](df tau, df low, float m, float part, float margin, df& cut) -> bool {
-        cut = df_add(low, df{m, 0.f});
-        const df gap = df_add(tau, df_neg(cut));
-        if (fabsf(gap.hi) > margin) return gap.hi < 0.f;
+        const float gapf = (tau.hi - low.hi) - m;
+        if (fabsf(gapf) > margin) {
+            if (gapf < 0.f) return true;
+            cut = df_add(low, df{m, 0.f});
+            return false;
+        }
         cut = df_add(low, refine(part));
         return df_le(tau, cut);
     };

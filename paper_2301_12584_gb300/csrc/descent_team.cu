@@ -11,9 +11,9 @@
 // levels cost one memory round trip; after each decision only the chosen
 // child's next-level mass is formed.  The team's threads own fixed float4
 // chunks of a node (weights w_p = h_i h_j, doubled off the diagonal, in
-// registers with their (i, j) pairs); masses are team sums; decisions use the
-// FP32 mass unless tau is within 1e-6 C of the cutoff, then the double-float
-// team sum, with tau, low and h in double-float.  Every wait is bounded and
+// registers, the (i, j) of each chunk's first entry kept as an 8+8-bit code);
+// masses are team sums; decisions use FP32 unless tau is within 1e-6 C of the
+// cutoff, then the double-float team sum, with tau, low and h in double-float.  Every wait is bounded and
 // its outcome agreed by the whole team (bar.red) before anyone acts on it.
 #include "common.cuh"
 #include "internal.h"
@@ -38,13 +38,6 @@ __device__ __forceinline__ bool tmb_wait(uint64_t* m, uint32_t parity, int max_t
     return false;
 }
 
-__device__ __forceinline__ float2 tffma2(float2 a, float2 b, float2 c) {
-    uint64_t d;
-    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b),
-                   uc = *reinterpret_cast<uint64_t*>(&c);
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
-    return *reinterpret_cast<float2*>(&d);
-}
 
 template <int RMAX, int TEAM>
 struct TeamCfg {
@@ -133,25 +126,24 @@ __global__ void __launch_bounds__(256, 2) krp_descent_team(const __grid_constant
         return t;
     };
 
-    // (i, j) of this thread's packed entries p = 4 (tt + NT m) + q, 8 bits each
-    uint32_t ij[NCH][2];
+    // (i, j) of the first packed entry p = 4 (tt + NT m) of each of this
+    // thread's chunks, 8 bits each, two chunks per word; the chunk's other
+    // entries follow along the row (j + 1, wrapping to (i + 1, i + 1)).
+    constexpr int NIJ = (NCH + 1) / 2;
+    uint32_t ij[NIJ];
+#pragma unroll
+    for (int h = 0; h < NIJ; ++h) ij[h] = 0u;
 #pragma unroll
     for (int m = 0; m < NCH; ++m) {
-        uint32_t pk[2] = {0u, 0u};
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int p = 4 * (tt + NT * m) + q;
-            int i = 0, rem = p;
-            if (p < T)
-                while (rem >= R - i) {
-                    rem -= R - i;
-                    ++i;
-                }
-            const uint32_t code = p < T ? (uint32_t)(i | ((i + rem) << 8)) : 0xFFFFu;
-            pk[q >> 1] |= code << (16 * (q & 1));
-        }
-        ij[m][0] = pk[0];
-        ij[m][1] = pk[1];
+        const int p = 4 * (tt + NT * m);
+        int i = 0, rem = p;
+        if (p < T)
+            while (rem >= R - i) {
+                rem -= R - i;
+                ++i;
+            }
+        const uint32_t code = p < T ? (uint32_t)(i | ((i + rem) << 8)) : 0u;
+        ij[m >> 1] |= code << (16 * (m & 1));
     }
     if (tt == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tsm_u32(mbar)) : "memory");
@@ -198,38 +190,46 @@ __global__ void __launch_bounds__(256, 2) krp_descent_team(const __grid_constant
     auto make_weights = [&](const float* x) {
 #pragma unroll
         for (int m = 0; m < NCH; ++m) {
+            const uint32_t code = (ij[m >> 1] >> (16 * (m & 1))) & 0xFFFFu;
+            int i = code & 0xFF, j = code >> 8;
+            const int p0 = 4 * (tt + NT * m);
             float wv[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const uint32_t code = (ij[m][q >> 1] >> (16 * (q & 1))) & 0xFFFFu;
                 float w = 0.f;
-                if (code != 0xFFFFu) {
-                    const int i = code & 0xFF, j = code >> 8;
+                if (p0 + q < T) {
                     w = x[i] * x[j];
                     if (i != j) w += w;
                 }
                 wv[q] = w;
+                if (++j == R) j = ++i;
             }
             w4[m] = make_float4(wv[0], wv[1], wv[2], wv[3]);
         }
     };
     auto partial = [&](const float* node) -> float {
-        float2 acc = make_float2(0.f, 0.f);
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
 #pragma unroll
         for (int m = 0; m < NCH; ++m) {
             const int c = tt + NT * m;
             if (c < nc4) {
                 const float4 v = reinterpret_cast<const float4*>(node)[c];
-                acc = tffma2(make_float2(w4[m].x, w4[m].y), make_float2(v.x, v.y), acc);
-                acc = tffma2(make_float2(w4[m].z, w4[m].w), make_float2(v.z, v.w), acc);
+                a0 = ffma2(make_float2(w4[m].x, w4[m].y), make_float2(v.x, v.y), a0);
+                a1 = ffma2(make_float2(w4[m].z, w4[m].w), make_float2(v.z, v.w), a1);
             }
         }
-        return acc.x + acc.y;
+        return (a0.x + a1.x) + (a0.y + a1.y);
     };
+    // tau, low and m are the same in every thread of the team, so the branch
+    // into the double-float sum is team-uniform.  (tau.hi - low.hi) - m is
+    // within a few ulp(C) + |tau.lo| + |low.lo| < 3e-7 C of tau - low - m.
     auto go_left = [&](df tau, df low, float m, float part, float margin, df& cut) -> bool {
-        cut = df_add(low, df{m, 0.f});
-        const df gap = df_add(tau, df_neg(cut));
-        if (fabsf(gap.hi) > margin) return gap.hi < 0.f;
+        const float gapf = (tau.hi - low.hi) - m;
+        if (fabsf(gapf) > margin) {
+            if (gapf < 0.f) return true;
+            cut = df_add(low, df{m, 0.f});
+            return false;
+        }
         cut = df_add(low, team_sum_df(part));
         return df_le(tau, cut);
     };
@@ -382,14 +382,15 @@ __global__ void __launch_bounds__(256, 2) krp_descent_team(const __grid_constant
                         const float4* row = reinterpret_cast<const float4*>(stage + t * R);
                         const float4* hv = reinterpret_cast<const float4*>(th);
                         const int nq = R >> 2;
-                        float2 acc = make_float2(0.f, 0.f);
+                        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+                        int j = t % nq;   // rows start on rotated columns (no bank conflicts)
                         for (int a = 0; a < nq; ++a) {
-                            const int j = (a + t) % nq;
                             const float4 x = row[j], y = hv[j];
-                            acc = tffma2(make_float2(x.x, x.y), make_float2(y.x, y.y), acc);
-                            acc = tffma2(make_float2(x.z, x.w), make_float2(y.z, y.w), acc);
+                            a0 = ffma2(make_float2(x.x, x.y), make_float2(y.x, y.y), a0);
+                            a1 = ffma2(make_float2(x.z, x.w), make_float2(y.z, y.w), a1);
+                            j = j + 1 == nq ? 0 : j + 1;
                         }
-                        d = acc.x + acc.y;
+                        d = (a0.x + a1.x) + (a0.y + a1.y);
                     } else {
                         const float* row = Uk + (row0 + t) * R;
                         for (int a = 0; a < R; ++a) d = fmaf(__ldg(row + a), th[a], d);

@@ -18,6 +18,10 @@ __device__ void jacobi_eig(Scalar* A, Scalar* V, int n, Scalar* cs, int* pr, dou
                            int max_sweeps, double tol) {
     const int m = n + (n & 1);  // players, a dummy when n is odd
     const int npair = m / 2;
+    // this thread's first (pair, column) item of the flattened npair x n
+    // rotation loops and the stride between its items, without dividing
+    const int k0 = threadIdx.x / n, c0 = threadIdx.x % n;
+    const int dk = blockDim.x / n, dc = blockDim.x % n;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? Scalar(1) : Scalar(0);
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -71,36 +75,40 @@ __device__ void jacobi_eig(Scalar* A, Scalar* V, int n, Scalar* cs, int* pr, dou
             }
             __syncthreads();
             // rows: A <- Jᵀ A
-            for (int w = threadIdx.x; w < npair * n; w += blockDim.x) {
-                const int k = w / n, col = w % n;
-                const int p = pr[2 * k], q = pr[2 * k + 1];
-                if (p < 0 || cs[2 * k + 1] == Scalar(0)) continue;
-                const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
-                const Scalar ap = A[p * n + col], aq = A[q * n + col];
-                A[p * n + col] = c * ap - sn * aq;
-                A[q * n + col] = sn * ap + c * aq;
-            }
-            __syncthreads();
-            // columns: A <- A J, V <- V J
-            for (int w = threadIdx.x; w < npair * n; w += blockDim.x) {
-                const int k = w / n, row = w % n;
-                const int p = pr[2 * k], q = pr[2 * k + 1];
-                if (p < 0 || cs[2 * k + 1] == Scalar(0)) continue;
-                const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
-                const Scalar ap = A[row * n + p], aq = A[row * n + q];
-                A[row * n + p] = c * ap - sn * aq;
-                A[row * n + q] = sn * ap + c * aq;
-                const Scalar vp = V[row * n + p], vq = V[row * n + q];
-                V[row * n + p] = c * vp - sn * vq;
-                V[row * n + q] = sn * vp + c * vq;
-            }
-            __syncthreads();
-            // the rotated pair is now decoupled
-            for (int k = threadIdx.x; k < npair; k += blockDim.x) {
+            for (int k = k0, col = c0; k < npair;) {
                 const int p = pr[2 * k], q = pr[2 * k + 1];
                 if (p >= 0 && cs[2 * k + 1] != Scalar(0)) {
-                    A[p * n + q] = Scalar(0);
-                    A[q * n + p] = Scalar(0);
+                    const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
+                    const Scalar ap = A[p * n + col], aq = A[q * n + col];
+                    A[p * n + col] = c * ap - sn * aq;
+                    A[q * n + col] = sn * ap + c * aq;
+                }
+                col += dc;
+                k += dk;
+                if (col >= n) {
+                    col -= n;
+                    ++k;
+                }
+            }
+            __syncthreads();
+            // columns: A <- A J, V <- V J; the rotated pair's off-diagonal
+            // entries (rows p and q) are set to their exact value, zero
+            for (int k = k0, row = c0; k < npair;) {
+                const int p = pr[2 * k], q = pr[2 * k + 1];
+                if (p >= 0 && cs[2 * k + 1] != Scalar(0)) {
+                    const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
+                    const Scalar ap = A[row * n + p], aq = A[row * n + q];
+                    A[row * n + p] = row == q ? Scalar(0) : c * ap - sn * aq;
+                    A[row * n + q] = row == p ? Scalar(0) : sn * ap + c * aq;
+                    const Scalar vp = V[row * n + p], vq = V[row * n + q];
+                    V[row * n + p] = c * vp - sn * vq;
+                    V[row * n + q] = sn * vp + c * vq;
+                }
+                row += dc;
+                k += dk;
+                if (row >= n) {
+                    row -= n;
+                    ++k;
                 }
             }
             __syncthreads();

@@ -358,6 +358,14 @@ krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_
     return cudaMemcpy(out_host, s->tree[j], n * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? KRP_OK : KRP_ECUDA;
 }
 
+krp_status krp_get_factor(const krp_sampler* s, int j, float* out_host, int64_t n_floats) {
+    if (!s || j < 0 || j >= s->N || !out_host || !s->has_factor[j]) return KRP_EINVAL;
+    const int64_t n = s->I[j] * s->R;
+    if (n_floats < n) return KRP_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return KRP_ECUDA;
+    return cudaMemcpy(out_host, s->U[j], n * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? KRP_OK : KRP_ECUDA;
+}
+
 krp_status krp_get_prep(const krp_sampler* s, int k, double* lam_host, double* V_host, double* Gplus_host,
                         int* rank_host) {
     if (!s || k < 0 || k >= s->N) return KRP_EINVAL;

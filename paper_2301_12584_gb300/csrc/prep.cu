@@ -333,7 +333,8 @@ __device__ __forceinline__ void prep_pinv_body(const PrepParams& P, int N, int e
 // ---------------------------------------------------------------------------
 // prep_eig: one CTA per included factor k: G_{>k}, its eigendecomposition
 // (eig_fp32_refined), eigenvalues ascending with negatives clamped to zero,
-// eigenvectors as FP64 columns, FP32 rows and FP32 residual rows, and E_k.
+// eigenvectors as FP64 columns, FP32 rows and FP32 residual rows (E_k is
+// built from them by prep_etree).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R, int Rp, int dE, int Tp,
                                               const double* __restrict__ G64, const double* __restrict__ Gplus64,
@@ -368,10 +369,18 @@ __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R,
         V32lo[(size_t)k * RR + o * R + row] = (float)(v - (double)vh);
     }
     for (int u = threadIdx.x; u < R; u += blockDim.x) lam64[(size_t)k * R + pos[u]] = lam[u];
-    __syncthreads();
-    // E_k: per packed entry e=(i,j), leaves u = 0..Rp-1 hold λ_u V[i,u] V[j,u]
-    // (zero for u >= R); binary-counter pairwise sums up the tree; stored
-    // nodes multiplied by G_k[i,j].  Reads the sorted eigenpairs from global.
+}
+
+// ---------------------------------------------------------------------------
+// E_k (a3) from the sorted eigenpairs that prep_eig wrote: per packed entry
+// e = (i, j) (one thread each, CTAs spread over the entries), leaves
+// u = 0..Rp-1 hold λ_u V[i,u] V[j,u] (zero for u >= R); binary-counter
+// pairwise sums up the tree; stored nodes multiplied by G_k[i,j].
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void etree_body(int k, int R, int Rp, int Tp, const double* __restrict__ G64,
+                                           const double* __restrict__ lam64, const double* __restrict__ V64,
+                                           float* __restrict__ etree, int e) {
+    const int RR = R * R;
     const double* lk = lam64 + (size_t)k * R;
     const double* Vk = V64 + (size_t)k * RR;
     const double* Gk = G64 + (size_t)k * RR;
@@ -380,56 +389,70 @@ __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R,
     // E_k's masses are compared only with each other, so its nodes carry a
     // power-of-two scale that keeps them near 1 in FP32 (λ_max(G_{>k}) can
     // be ~2^-144 for the last of many factors)
-    double gkmax = 0.0;
-    for (int i = 0; i < R; ++i) gkmax = fmax(gkmax, Gk[i * R + i]);
-    const double emag = lk[R - 1] * gkmax;
-    const double esc = (emag > 0.0 && isfinite(emag)) ? ldexp(1.0, -ilogb(emag)) : 1.0;
-    for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
-        if (e >= T) {
-            for (int sl = 0; sl < Rp; ++sl) et[(size_t)sl * Tp + e] = 0.f;
-            continue;
-        }
-        int i = 0, rem = e;
-        while (rem >= R - i) {
-            rem -= R - i;
-            ++i;
-        }
-        const int j = i + rem;
-        const double gij = Gk[i * R + j] * esc;
-        double stk[8];
-        for (int u = 0; u < Rp; ++u) {
-            double val = (u < R) ? lk[u] * Vk[i * R + u] * Vk[j * R + u] : 0.0;
-            int64_t h = Rp + u;
+    __shared__ double s_esc;
+    if (threadIdx.x == 0) {
+        double gkmax = 0.0;
+        for (int i = 0; i < R; ++i) gkmax = fmax(gkmax, Gk[i * R + i]);
+        const double emag = lk[R - 1] * gkmax;
+        s_esc = (emag > 0.0 && isfinite(emag)) ? ldexp(1.0, -ilogb(emag)) : 1.0;
+    }
+    __syncthreads();
+    const double esc = s_esc;
+    if (e >= Tp) return;
+    if (e >= T) {
+        for (int sl = 0; sl < Rp; ++sl) et[(size_t)sl * Tp + e] = 0.f;
+        return;
+    }
+    int i = 0, rem = e;
+    while (rem >= R - i) {
+        rem -= R - i;
+        ++i;
+    }
+    const int j = i + rem;
+    const double gij = Gk[i * R + j] * esc;
+    double stk[8];
+    for (int u = 0; u < Rp; ++u) {
+        double val = (u < R) ? lk[u] * Vk[i * R + u] * Vk[j * R + u] : 0.0;
+        int64_t h = Rp + u;
+        if (tree_stored(h)) et[tree_slot(h) * Tp + e] = (float)(val * gij);
+        int idx = u, lvl = 0;
+        while (idx & 1) {
+            val = stk[lvl] + val;
+            h >>= 1;
+            idx >>= 1;
+            ++lvl;
             if (tree_stored(h)) et[tree_slot(h) * Tp + e] = (float)(val * gij);
-            int idx = u, lvl = 0;
-            while (idx & 1) {
-                val = stk[lvl] + val;
-                h >>= 1;
-                idx >>= 1;
-                ++lvl;
-                if (tree_stored(h)) et[tree_slot(h) * Tp + e] = (float)(val * gij);
-            }
-            stk[lvl] = val;
         }
+        stk[lvl] = val;
     }
 }
 
+constexpr int ETREE_THREADS = 128;
+
 size_t carve_smem_bytes(int n, bool fp64_in_smem);
 
-__global__ void __launch_bounds__(256) prep_pinv(const __grid_constant__ PrepParams P, int N, int exclude, int R,
+__global__ void __launch_bounds__(1024) prep_pinv(const __grid_constant__ PrepParams P, int N, int exclude, int R,
                                                  int Tp, double* __restrict__ G64, double* __restrict__ Gplus64,
                                                  float* __restrict__ Gplus32, int* __restrict__ rank_out,
                                                  int* __restrict__ status, double* __restrict__ gwork) {
     prep_pinv_body(P, N, exclude, R, Tp, G64, Gplus64, Gplus32, rank_out, status, gwork);
 }
 
-__global__ void __launch_bounds__(256) prep_eig(const __grid_constant__ PrepParams P, int N, int R, int Rp, int dE,
+__global__ void __launch_bounds__(1024) prep_eig(const __grid_constant__ PrepParams P, int N, int R, int Rp, int dE,
                                                 int Tp, const double* __restrict__ G64,
                                                 const double* __restrict__ Gplus64, double* __restrict__ lam64,
                                                 double* __restrict__ V64, float* __restrict__ V32,
                                                 float* __restrict__ V32lo, float* __restrict__ etree,
                                                 double* __restrict__ gwork) {
     prep_eig_body(P, N, R, Rp, dE, Tp, G64, Gplus64, lam64, V64, V32, V32lo, etree, gwork, blockIdx.x);
+}
+
+// grid (entry blocks, included factors)
+__global__ void __launch_bounds__(ETREE_THREADS) prep_etree(const __grid_constant__ PrepParams P, int R, int Rp, int Tp,
+                                                            const double* __restrict__ G64,
+                                                            const double* __restrict__ lam64,
+                                                            const double* __restrict__ V64, float* __restrict__ etree) {
+    etree_body(P.incl[blockIdx.y], R, Rp, Tp, G64, lam64, V64, etree, blockIdx.x * ETREE_THREADS + threadIdx.x);
 }
 
 // Batched forms: CTA b of prep_pinv_batch prepares problem b; CTA b of
@@ -444,6 +467,13 @@ __global__ void __launch_bounds__(256) prep_eig_batch(const PrepItem* __restrict
     const int p = blockIdx.x % n_incl;
     prep_eig_body(it.P, it.N, it.R, it.Rp, it.dE, it.Tp, it.G64, it.Gplus64, it.lam64, it.V64, it.V32, it.V32lo,
                   it.etree, it.gwork ? it.gwork + (size_t)p * 6 * it.R * it.R : nullptr, p);
+}
+// grid (entry blocks of the largest Tp, problems x included factors)
+__global__ void __launch_bounds__(ETREE_THREADS) prep_etree_batch(const PrepItem* __restrict__ items, int n_incl) {
+    const PrepItem& it = items[blockIdx.y / n_incl];
+    if ((int)(blockIdx.x * ETREE_THREADS) >= it.Tp) return;   // uniform across the CTA
+    etree_body(it.P.incl[blockIdx.y % n_incl], it.R, it.Rp, it.Tp, it.G64, it.lam64, it.V64, it.etree,
+               blockIdx.x * ETREE_THREADS + threadIdx.x);
 }
 
 void prep_item_for(const krp_sampler* s, int exclude_j, PrepItem* it) {
@@ -482,6 +512,12 @@ cudaError_t launch_prep_batch(const PrepItem* items_dev, int P, int n_incl, int 
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     prep_eig_batch<<<P * n_incl, 256, smem, st>>>(items_dev, n_incl); count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int tpmax = (tri_size(Rmax) + 7) & ~7;
+    prep_etree_batch<<<dim3((tpmax + ETREE_THREADS - 1) / ETREE_THREADS, P * n_incl), ETREE_THREADS, 0, st>>>(
+        items_dev, n_incl);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -499,15 +535,23 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j) {
         cudaFuncSetAttribute(prep_pinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         cudaFuncSetAttribute(prep_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     }
-    prep_pinv<<<1, 256, smem, s->stream>>>(P, N, exclude_j, R, s->Tp, s->G64, s->Gplus64, s->Gplus32, s->rank_dev,
-                                          s->status, in_smem ? nullptr : s->work64); count_launch();
+    // one CTA per R x R problem: more threads hide the rotation steps'
+    // shared-memory latency once R is past a warp's width
+    const int nt = R > 32 ? 1024 : 256;
+    prep_pinv<<<1, nt, smem, s->stream>>>(P, N, exclude_j, R, s->Tp, s->G64, s->Gplus64, s->Gplus32, s->rank_dev,
+                                         s->status, in_smem ? nullptr : s->work64); count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_pinv launch");
-    prep_eig<<<P.n_incl, 256, smem, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64, s->lam64, s->V64,
-                                                s->V32, s->V32lo, s->etree,
-                                                in_smem ? nullptr : s->work64); count_launch();
+    prep_eig<<<P.n_incl, nt, smem, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64, s->lam64, s->V64,
+                                               s->V32, s->V32lo, s->etree,
+                                               in_smem ? nullptr : s->work64); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_eig launch");
+    prep_etree<<<dim3((s->Tp + ETREE_THREADS - 1) / ETREE_THREADS, P.n_incl), ETREE_THREADS, 0, s->stream>>>(
+        P, R, s->Rp, s->Tp, s->G64, s->lam64, s->V64, s->etree);
+    count_launch();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_check(s, e, "prep_etree launch");
     s->last_exclude = exclude_j;
     return KRP_OK;
 }

@@ -10,7 +10,9 @@
 // the FP32 sums neither overflow nor underflow when the weights
 // 1/sqrt(J q) are far from 1 (many factors: q ~ 2^-144 at N = 9, I = 2^16).
 // normal_solve (one CTA): FP64 sum of the partials times 2^(2e) in a fixed
-// order, Cholesky, triangular solves.
+// order, Cholesky, triangular solves.  A single problem's sum runs first, in
+// the same order, over many CTAs (normal_reduce; GB300's FP64 rate is ~1/64 of
+// FP32 per SM), and normal_solve_sums starts from it.
 #include "common.cuh"
 #include "internal.h"
 #include "jacobi.cuh"
@@ -124,7 +126,8 @@ __global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ 
 __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part, int nparts, int R, int nrhs,
                                                   int mode, int flags, float* __restrict__ X,
                                                   double* __restrict__ Xd, int* __restrict__ status,
-                                                  double* __restrict__ gbuf, const float* __restrict__ part_exp) {
+                                                  double* __restrict__ gbuf, const float* __restrict__ part_exp,
+                                                  const double* __restrict__ sums = nullptr) {
     extern __shared__ __align__(16) double smd[];
     const int RR = R * R;
     const int T = tri_size(R);
@@ -145,10 +148,13 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
     auto psc = [&](int p) -> double {
         return p < 1024 ? pscale[p] : (part_exp ? ldexp(1.0, 2 * (int)part_exp[p]) : 1.0);
     };
-    // FP64 reduction of the partials, fixed order
+    // FP64 reduction of the partials, fixed order (or their sums from normal_reduce)
     for (int id = threadIdx.x; id < T; id += blockDim.x) {
         double a = 0.0;
-        for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id] * psc(p);
+        if (sums)
+            a = sums[id];
+        else
+            for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id] * psc(p);
         int i = 0, rem = id;
         while (rem >= R - i) {
             rem -= R - i;
@@ -161,6 +167,8 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
         double a;
         if (mode == 1) {
             a = (id / ncol == id % ncol) ? 1.0 : 0.0;
+        } else if (sums) {
+            a = sums[T + id];
         } else {
             a = 0.0;
             for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + T + id] * psc(p);
@@ -252,6 +260,25 @@ __global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ pa
     normal_solve_body(part, nparts, R, nrhs, mode, flags, X, Xd, status, gbuf, part_exp);
 }
 
+// The FP64 reduction of normal_solve spread over CTAs (one thread per output
+// entry, partials in the same fixed order): at R = 100 and 304 partials it is
+// 1.5 M FP64 adds, too many for the one SM the solve runs on.
+__global__ void __launch_bounds__(256) normal_reduce(const float* __restrict__ part,
+                                                     const float* __restrict__ part_exp, int nparts, int nout,
+                                                     double* __restrict__ sums) {
+    const int id = blockIdx.x * blockDim.x + threadIdx.x;
+    if (id >= nout) return;
+    double a = 0.0;
+    for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id] * ldexp(1.0, 2 * (int)part_exp[p]);
+    sums[id] = a;
+}
+
+__global__ void __launch_bounds__(256) normal_solve_sums(const double* __restrict__ sums, int R, int nrhs, int mode,
+                                                         int flags, float* __restrict__ X, double* __restrict__ Xd,
+                                                         int* __restrict__ status, double* __restrict__ gbuf) {
+    normal_solve_body(nullptr, 0, R, nrhs, mode, flags, X, Xd, status, gbuf, nullptr, sums);
+}
+
 // Batched forms: blockIdx.z (partials) or blockIdx.x (solve) is the problem.
 __global__ void __launch_bounds__(256) normal_partial_batch(const SolveItem* __restrict__ items, int64_t J,
                                                             const float* __restrict__ SA,
@@ -303,7 +330,9 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
     nparts = nparts < 1 ? 1 : nparts;
     const int64_t rows_per_cta = (J + nparts - 1) / nparts;
     const int ncol = mode == 1 ? R : nrhs;
-    const size_t need = (size_t)nparts * nout + nparts;  // partials, then their exponents
+    // partials, their exponents, then (8-byte aligned) the FP64 sums
+    const size_t sums_off = ((size_t)nparts * nout + nparts + 1) & ~(size_t)1;
+    const size_t need = sums_off + (size_t)2 * nout;
     const size_t need64 = (size_t)2 * R * R + (size_t)R * ncol + (size_t)R * R;
     if (need > s->solve_scratch_floats) {
         if (s->solve_scratch) cudaFree(s->solve_scratch);
@@ -325,10 +354,13 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
     const bool in_smem = small + mats <= 160 * 1024;
     const size_t smem2 = small + (in_smem ? mats : 0);
     if (smem2 > 48 * 1024)
-        cudaFuncSetAttribute(normal_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
-    normal_solve<<<1, 256, smem2, s->stream>>>(s->solve_scratch, nparts, R, nrhs, mode, flags, X,
-                                              s->solve64 + (size_t)(2 * R * R + R * 128), s->status,
-                                              in_smem ? nullptr : s->solve64, part_exp); count_launch();
+        cudaFuncSetAttribute(normal_solve_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+    double* sums = reinterpret_cast<double*>(s->solve_scratch + sums_off);
+    normal_reduce<<<(nout + 255) / 256, 256, 0, s->stream>>>(s->solve_scratch, part_exp, nparts, nout, sums);
+    count_launch();
+    normal_solve_sums<<<1, 256, smem2, s->stream>>>(sums, R, nrhs, mode, flags, X,
+                                                    s->solve64 + (size_t)(2 * R * R + R * 128), s->status,
+                                                    in_smem ? nullptr : s->solve64); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "normal_solve launch");
     (void)need64;

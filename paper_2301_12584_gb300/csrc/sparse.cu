@@ -160,47 +160,128 @@ __global__ void __launch_bounds__(256) fiber_scatter(LookupParams P, const int64
     }
 }
 
-// U[i, :] = Y[i, :] M⁻¹  (M⁻¹ FP64 -> FP32 in shared memory).
-__global__ void __launch_bounds__(256) apply_minv(const float* __restrict__ Y, const double* __restrict__ Minv,
-                                                  int64_t I, int R, float* __restrict__ U) {
+// U[i, :] = Y[i, :] M⁻¹ (M⁻¹ FP64 -> FP32 in shared memory) and, when sumsq
+// is non-null, σ²[c] += Σ_i U[i, c]² (double-float partials per thread, one
+// FP64 atomic per column and CTA).  Persistent CTAs walk tiles of TM rows of
+// Y, staged in shared memory with row stride R | 1 (the rows a warp reads
+// fall in distinct banks); thread (ty, tx) accumulates RT rows x 8 columns,
+// {4tx .. 4tx+3} and {RP/2 + 4tx ..}, against float4 rows of M⁻¹ (columns
+// >= R zero).  RP = R padded to 32, 64 or 128.
+constexpr int MINV_THREADS = 256;
+template <int RP>
+struct MinvCfg {
+    static constexpr int TX = RP / 8, TY = MINV_THREADS / TX, RT = 4, TM = TY * RT;
+    // M⁻¹, then the Y tile, which the final column reduction reuses for
+    // 8 x MINV_THREADS doubles
+    static size_t smem(int R) {
+        return (size_t)RP * RP * 4 + std::max<size_t>((size_t)TM * (R | 1) * 4, (size_t)8 * MINV_THREADS * 8);
+    }
+};
+
+template <int RP>
+__global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __restrict__ Y,
+                                                              const double* __restrict__ Minv, int64_t I, int R,
+                                                              float* __restrict__ U, double* __restrict__ sumsq) {
+    using C = MinvCfg<RP>;
+    constexpr int TX = C::TX, RT = C::RT, TM = C::TM;
     extern __shared__ __align__(16) float sm[];
-    float* sM = sm;            // R x R
-    float* sY = sM + R * R;    // 32 x R
-    for (int e = threadIdx.x; e < R * R; e += blockDim.x) sM[e] = (float)Minv[e];
-    for (int64_t r0 = (int64_t)blockIdx.x * 32; r0 < I; r0 += (int64_t)gridDim.x * 32) {
-        const int nr = (int)min((int64_t)32, I - r0);
+    float* sM = sm;              // [R][RP]
+    float* sY = sM + RP * RP;    // [TM][RS]
+    const int RS = R | 1;
+    const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int k = warp; k < R; k += MINV_THREADS / 32)
+        for (int c = lane; c < RP; c += 32) sM[k * RP + c] = c < R ? (float)Minv[k * R + c] : 0.f;
+    df ss[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) ss[q] = df{0.f, 0.f};
+    const int64_t ntiles = (I + TM - 1) / TM;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t r0 = tile * TM;
+        const int nr = (int)min((int64_t)TM, I - r0);
+        __syncthreads();   // the previous tile's reads of sY (and the writes of sM) are done
+        const float* src = Y + r0 * R;
+        for (int r = warp; r < nr; r += MINV_THREADS / 32)
+            for (int k = lane; k < R; k += 32) sY[r * RS + k] = src[(int64_t)r * R + k];
         __syncthreads();
-        for (int e = threadIdx.x; e < 32 * R; e += blockDim.x) sY[e] = (e / R < nr) ? Y[r0 * R + e] : 0.f;
-        __syncthreads();
-        for (int e = threadIdx.x; e < nr * R; e += blockDim.x) {
-            const int r = e / R, c = e % R;
-            float a = 0.f;
-            for (int k = 0; k < R; ++k) a = fmaf(sY[r * R + k], sM[k * R + c], a);
-            U[(r0 + r) * R + c] = a;
+        float2 acc[RT][4];
+#pragma unroll
+        for (int r = 0; r < RT; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = make_float2(0.f, 0.f);
+        const float* yrow = sY + ty * RT * RS;
+        for (int k = 0; k < R; ++k) {
+            const float4 m0 = *reinterpret_cast<const float4*>(sM + k * RP + 4 * tx);
+            const float4 m1 = *reinterpret_cast<const float4*>(sM + k * RP + RP / 2 + 4 * tx);
+#pragma unroll
+            for (int r = 0; r < RT; ++r) {
+                const float y = yrow[r * RS + k];
+                const float2 yy = make_float2(y, y);
+                acc[r][0] = ffma2(yy, make_float2(m0.x, m0.y), acc[r][0]);
+                acc[r][1] = ffma2(yy, make_float2(m0.z, m0.w), acc[r][1]);
+                acc[r][2] = ffma2(yy, make_float2(m1.x, m1.y), acc[r][2]);
+                acc[r][3] = ffma2(yy, make_float2(m1.z, m1.w), acc[r][3]);
+            }
         }
+        // rows >= nr hold stale shared memory: neither written nor summed
+#pragma unroll
+        for (int r = 0; r < RT; ++r) {
+            const int row = ty * RT + r;
+            if (row >= nr) continue;
+            float* dst = U + (r0 + row) * R;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int c0 = h * (RP / 2) + 4 * tx;
+                const float v[4] = {acc[r][2 * h].x, acc[r][2 * h].y, acc[r][2 * h + 1].x, acc[r][2 * h + 1].y};
+                if ((R & 3) == 0 && c0 + 3 < R) {
+                    *reinterpret_cast<float4*>(dst + c0) = make_float4(v[0], v[1], v[2], v[3]);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (c0 + q < R) dst[c0 + q] = v[q];
+                }
+                if (sumsq) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) ss[4 * h + q] = df_add(ss[4 * h + q], df{v[q] * v[q], 0.f});
+                }
+            }
+        }
+    }
+    if (!sumsq) return;
+    // column totals: the TY threads of a column group in fixed order, then one
+    // FP64 atomic per column
+    __syncthreads();
+    double* red = reinterpret_cast<double*>(sY);   // [TY][8 x TX] doubles <= TM * RS floats
+#pragma unroll
+    for (int q = 0; q < 8; ++q) red[ty * 8 * TX + q * TX + tx] = (double)ss[q].hi + (double)ss[q].lo;
+    __syncthreads();
+    for (int col = threadIdx.x; col < R; col += MINV_THREADS) {
+        const int h = col / (RP / 2), rem = col % (RP / 2), t = rem / 4, q = 4 * h + rem % 4;
+        double a = 0.0;
+        for (int y = 0; y < C::TY; ++y) a += red[y * 8 * TX + q * TX + t];
+        atomicAdd(sumsq + col, a);
     }
 }
 
-// σ²[c] += Σ_i U[i, c]² (FP64 atomics, one partial per CTA and column).
-__global__ void __launch_bounds__(256) col_sumsq(const float* __restrict__ U, int64_t I, int R,
-                                                 double* __restrict__ out) {
-    __shared__ double part[256];
-    const int c = threadIdx.x % R;
-    const int lanes = (blockDim.x / R) * R;
-    double a = 0.0;
-    if ((int)threadIdx.x < lanes)
-        for (int64_t i = (int64_t)blockIdx.x * (blockDim.x / R) + threadIdx.x / R; i < I;
-             i += (int64_t)gridDim.x * (blockDim.x / R)) {
-            const double v = U[i * R + c];
-            a += v * v;
-        }
-    part[threadIdx.x] = (int)threadIdx.x < lanes ? a : 0.0;
-    __syncthreads();
-    if ((int)threadIdx.x < R) {
-        double t = 0.0;
-        for (int q = threadIdx.x; q < lanes; q += R) t += part[q];
-        atomicAdd(out + threadIdx.x, t);
-    }
+template <int RP>
+cudaError_t launch_minv_t(const float* Y, const double* Minv, int64_t I, int R, float* U, double* sumsq,
+                          int num_sms, cudaStream_t st) {
+    using C = MinvCfg<RP>;
+    const size_t sm = C::smem(R);
+    cudaError_t e = cudaFuncSetAttribute(apply_minv<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    const int64_t ntiles = (I + C::TM - 1) / C::TM;
+    const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms * 2);
+    apply_minv<RP><<<(unsigned)grid, MINV_THREADS, sm, st>>>(Y, Minv, I, R, U, sumsq);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_minv(const float* Y, const double* Minv, int64_t I, int R, float* U, double* sumsq,
+                              int num_sms, cudaStream_t st) {
+    if (R <= 32) return launch_minv_t<32>(Y, Minv, I, R, U, sumsq, num_sms, st);
+    if (R <= 64) return launch_minv_t<64>(Y, Minv, I, R, U, sumsq, num_sms, st);
+    return launch_minv_t<128>(Y, Minv, I, R, U, sumsq, num_sms, st);
 }
 
 // U[:, c] /= σ_c (a zero column stays zero), σ_c = sqrt(σ²_c) to sigma;
@@ -395,9 +476,10 @@ extern "C" void krp_sptensor_destroy(krp_sptensor* t) {
     delete t;
 }
 
-extern "C" krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* tc, int j, int64_t J,
-                                       const int32_t* idx, const float* weight, const float* SA, float* U_out,
-                                       int flags) {
+namespace krp {
+// krp_solve_sparse, plus σ²[c] += Σ_i U_out[i, c]² when sumsq is non-null
+krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int64_t J, const int32_t* idx,
+                             const float* weight, const float* SA, float* U_out, int flags, double* sumsq) {
     if (!s || !tc || !idx || !weight || !SA || !U_out) return s ? fail(s, KRP_EINVAL, "null argument") : KRP_EINVAL;
     krp_sptensor* t = const_cast<krp_sptensor*>(tc);
     if (t->N != s->N || j < 0 || j >= s->N || J < 1 || J >= ((int64_t)1 << 31))
@@ -470,13 +552,16 @@ extern "C" krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* tc, i
     krp_status st = normal_inverse(s, J, SA, flags);
     if (st != KRP_OK) return st;
     const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
-    const size_t sm = (size_t)(R * R + 32 * R) * 4;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(apply_minv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    const int64_t g2 = std::min<int64_t>((s->I[j] + 31) / 32, (int64_t)s->num_sms * 4);
-    apply_minv<<<(unsigned)g2, 256, sm, s->stream>>>(t->Y, Minv, s->I[j], R, U_out); count_launch();
-    e = cudaGetLastError();
+    e = launch_apply_minv(t->Y, Minv, s->I[j], R, U_out, sumsq, s->num_sms, s->stream);
     if (e != cudaSuccess) return cuda_check(s, e, "apply_minv launch");
     return KRP_OK;
+}
+}  // namespace krp
+
+extern "C" krp_status krp_solve_sparse(krp_sampler* s, const krp_sptensor* tc, int j, int64_t J,
+                                       const int32_t* idx, const float* weight, const float* SA, float* U_out,
+                                       int flags) {
+    return solve_sparse_impl(s, tc, j, J, idx, weight, SA, U_out, flags, nullptr);
 }
 
 namespace krp {
@@ -495,13 +580,11 @@ extern "C" krp_status krp_cp_als_sweep(krp_sampler* s, const krp_sptensor* t, in
     for (int j = 0; j < s->N; ++j) {
         st = krp_sample(s, j, J, seed, draw_base + (uint64_t)j, idx, w, nullptr, SA);
         if (st != KRP_OK) return st;
-        st = krp_solve_sparse(s, t, j, J, idx, w, SA, s->U[j], KRP_PINV_FALLBACK);
-        if (st != KRP_OK) return st;
         cudaError_t e = cudaMemsetAsync(sumsq, 0, R * sizeof(double), s->stream);
         if (e != cudaSuccess) return cuda_check(s, e, "sumsq memset");
-        const int64_t rows_per = 256 / R;
-        const int64_t g = std::min<int64_t>((s->I[j] + rows_per - 1) / rows_per, (int64_t)s->num_sms * 4);
-        col_sumsq<<<(unsigned)g, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq); count_launch();
+        // U_j = Y M⁻¹ with its column sums of squares from the same pass
+        st = solve_sparse_impl(s, t, j, J, idx, w, SA, s->U[j], KRP_PINV_FALLBACK, sumsq);
+        if (st != KRP_OK) return st;
         const int64_t g2 = std::min<int64_t>((s->I[j] + 7) / 8, (int64_t)s->num_sms * 8);
         col_scale<<<(unsigned)g2, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq, sigma); count_launch();
         e = cudaGetLastError();

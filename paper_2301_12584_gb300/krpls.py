@@ -49,6 +49,7 @@ SIGNATURES = [
     ("krp_last_error", C.c_char_p, [_P]),
     ("krp_tree_info", _INT, [_P, _INT, C.POINTER(_I64), C.POINTER(_INT), C.POINTER(_INT)]),
     ("krp_get_tree", _INT, [_P, _INT, _P, _I64]),
+    ("krp_get_factor", _INT, [_P, _INT, _P, _I64]),
     ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
     ("krp_planted_rows", _INT, [_P, _INT, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
     ("krp_update_entries", _INT, [_P, _INT, _I64, _P, _P, _P]),
@@ -235,6 +236,13 @@ class Sampler:
         L, d, st = _I64(), _INT(), _INT()
         self._check(self._lib.krp_tree_info(self.h, int(j), C.byref(L), C.byref(d), C.byref(st)))
         return L.value, d.value, st.value
+
+    def get_factor(self, j):
+        """Host copy (numpy, I_j x R FP32) of the sampler's factor j."""
+        import numpy as np
+        out = np.zeros((self.I[j], self.R), dtype=np.float32)
+        self._check(self._lib.krp_get_factor(self.h, int(j), out.ctypes.data_as(_P), out.size))
+        return out
 
     def get_tree(self, j):
         import numpy as np

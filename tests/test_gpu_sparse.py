@@ -30,10 +30,12 @@ def make(dims, R, coords, vals, Us):
     return s, t
 
 
-def test_sparse_solve_matches_oracle_on_gpu_samples():
-    dims = (60, 50, 20)
-    coords, vals = synth.sparse_zipf_tensor(dims, 4000, seed=3)
-    R, J = 6, 3000
+# I_j spans several row tiles of Y M⁻¹ (64, 128 or 256 rows) with a ragged
+# tail; R covers each padded width (32, 64, 128) and R % 4 != 0
+@pytest.mark.parametrize("dims,R,J,nnz", [((60, 50, 20), 6, 3000, 4000), ((700, 40, 30), 40, 3000, 20000),
+                                          ((300, 33, 29), 50, 3000, 15000), ((520, 30, 24), 100, 4000, 20000)])
+def test_sparse_solve_matches_oracle_on_gpu_samples(dims, R, J, nnz):
+    coords, vals = synth.sparse_zipf_tensor(dims, nnz, seed=3)
     Us = synth.gaussian_factors(3, list(dims), R, seed=4)
     s, t = make(dims, R, coords, vals, Us)
     U64 = [U.astype(np.float64) for U in Us]
@@ -73,6 +75,40 @@ def test_fit_kernel_matches_oracle():
     assert abs(fit - ref) <= 1e-6 * max(1.0, abs(ref)), (fit, ref)
     s.close()
     t.close()
+
+
+@pytest.mark.parametrize("dims,R", [((300, 200, 40), 37), ((520, 300, 90), 100)])
+def test_sweep_normalises_columns(dims, R):
+    """After a sweep every factor has unit columns and sigma holds the norms
+    the last solve produced (column sums of squares fused into Y M⁻¹)."""
+    from paper_2301_12584_gb300.krpls import Sampler, SparseTensor
+    coords, vals = synth.sparse_zipf_tensor(dims, 30000, seed=12)
+    Us = synth.gaussian_factors(3, list(dims), R, seed=13)
+    s, t = make(dims, R, coords, vals, Us)
+    J = 2048
+    idx = torch.zeros((3, J), dtype=torch.int32, device=DEV)
+    w = torch.zeros(J, device=DEV)
+    SA = torch.zeros((J, R), device=DEV)
+    sigma = torch.zeros(R, device=DEV)
+    s.cp_als_sweep(t, J, 5, 0, sigma)
+    assert s.sync_status() == 0, s.last_error()
+    for k in range(3):
+        U = s.get_factor(k).astype(np.float64)
+        np.testing.assert_allclose(np.linalg.norm(U, axis=0), 1.0, rtol=2e-6)
+    # sigma: norms of the last mode's U_j = Y M⁻¹ before scaling, replayed on a
+    # second sampler holding the swept factors 0 and 1 (same seed and draw id)
+    s2, t2 = make(dims, R, coords, vals, Us)
+    for k in range(2):
+        s2.set_factor(k, torch.from_numpy(np.ascontiguousarray(s.get_factor(k), np.float32)).to(DEV))
+    s2.set_factor(2, torch.from_numpy(np.ascontiguousarray(Us[2], np.float32)).to(DEV))
+    s2.sample(2, J, 5, 2, idx, w, None, SA)
+    Uo = torch.zeros((dims[2], R), device=DEV)
+    s2.solve_sparse(t2, 2, J, idx, w, SA, Uo)
+    assert s2.sync_status() == 0, s2.last_error()
+    norms = np.linalg.norm(Uo.cpu().numpy().astype(np.float64), axis=0)
+    np.testing.assert_allclose(sigma.cpu().numpy(), norms, rtol=1e-4)
+    for x in (s, t, s2, t2):
+        x.close()
 
 
 @pytest.mark.parametrize("dims,rank,sweeps,converges", [((12, 10, 8), 3, 6, False), ((6, 7, 5), 2, 8, True)])
