@@ -240,18 +240,24 @@ __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ 
     }
 }
 
-// Persistent, pipelined form for R <= 32 with R % 4 == 0 and F <= 32 (the
-// sampler-at-scale shape).  A CTA walks blocks of G groups of LB leaves
-// (block v covers leaves [v G LB, (v+1) G LB) and leaves its subtree root in
-// top slot v), in chunks of 128/RP leaves: one chunk's rows are one
-// contiguous run of U (<= 16 KB), brought in by a bulk copy S chunks ahead.
+// Persistent, pipelined form (F R % 4 == 0, shared memory permitting).  A CTA
+// walks blocks of G groups of LB leaves (block v covers leaves
+// [v G LB, (v+1) G LB) and leaves its subtree root in top slot v), in chunks
+// of 128/RP leaves: one chunk's rows are one contiguous run of U (NL F R
+// floats, a stage), brought in by a bulk copy S chunks ahead (S = 3 for
+// RP <= 32, 2 for RP = 64, 1 for RP = 128, where one chunk is a whole leaf
+// of up to 64 KB); the sub-16-byte tail of a ragged last chunk comes by plain
+// loads.
 // Iteration i: wait for chunk i's rows, split them into the operand buffer
 // (i mod 2) and write the factor copy; thread 0 then refills the stage with
 // chunk i+S and issues chunk i's MMAs into TMEM buffer (i mod 2); meanwhile
 // the warps wait for chunk i-1's products, read its leaf Grams, and sum a
 // completed group up the tree.
-constexpr int PIPE_S = 3;
-constexpr int PIPE_STAGE_FLOATS = 4096;  // 128/RP leaves x F <= 32 rows x R <= RP columns
+template <int RP>
+struct PipeCfg {
+    static constexpr int S = RP <= 32 ? 3 : RP == 64 ? 2 : 1;   // stages
+    static constexpr int MINB = RP <= 32 ? 2 : 1;                // CTAs per SM
+};
 
 __device__ __forceinline__ void tc_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc_saddr(bar)), "r"(bytes) : "memory");
@@ -298,13 +304,13 @@ __device__ __forceinline__ void chunk_next(ChunkPos& c, int G) {
 constexpr int PIPE_THREADS = 256;
 
 template <int RP, int LB>
-__global__ void __launch_bounds__(PIPE_THREADS, 2)
+__global__ void __launch_bounds__(PIPE_THREADS, PipeCfg<RP>::MINB)
     tree_leaves_tc_pipe(const float* __restrict__ U, int64_t I, int R, int F, int Fp, int64_t L, int G, int Tp,
-                        int64_t nvb, float* __restrict__ tree, float* __restrict__ top, float* __restrict__ copy_to,
-                        int* __restrict__ status) {
+                        int64_t nvb, int stage_floats, float* __restrict__ tree, float* __restrict__ top,
+                        float* __restrict__ copy_to, int* __restrict__ status) {
     constexpr int NL = 128 / RP;
     constexpr int NCH = (LB + NL - 1) / NL;
-    constexpr int S = PIPE_S;
+    constexpr int S = PipeCfg<RP>::S;
     constexpr int NT = PIPE_THREADS;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t full[S];
@@ -315,8 +321,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 2)
     const int nk8 = Fp >> 3;
     const uint32_t sbo = (uint32_t)nk8 * 128u;
     const uint32_t xbytes = 16u * sbo;  // 128 rows x Fp bf16
-    float* stages = reinterpret_cast<float*>(smem);
-    unsigned char* X = smem + (size_t)S * PIPE_STAGE_FLOATS * 4;  // [buffer][hi, lo]
+    float* stages = reinterpret_cast<float*>(smem);                  // stage_floats: a multiple of 32
+    unsigned char* X = smem + (size_t)S * stage_floats * 4;         // [buffer][hi, lo]
     float* sG = reinterpret_cast<float*>(X + 4 * xbytes);
     float* stk = sG + (size_t)LB * Tp;
     const bool dense_shape = (F == Fp) && (R == RP);  // no padding inside a full chunk
@@ -355,10 +361,11 @@ __global__ void __launch_bounds__(PIPE_THREADS, 2)
         int nl, nvalid;
         rows_of(ahead, row0, nl, nvalid);
         uint64_t* b = &full[i % S];
-        const uint32_t bytes = (uint32_t)nvalid * (uint32_t)R * 4u;  // R % 4 == 0: a multiple of 16
+        // row0 R is a multiple of 4 (F R % 4 == 0): the source is 16-byte aligned
+        const uint32_t bytes = ((uint32_t)nvalid * (uint32_t)R * 4u) & ~15u;
         if (bytes) {
             tc_expect_tx(b, bytes);
-            tc_bulk_load(stages + (i % S) * PIPE_STAGE_FLOATS, U + row0 * R, bytes, b);
+            tc_bulk_load(stages + (size_t)(i % S) * stage_floats, U + row0 * R, bytes, b);
         } else {
             tc_arrive(b);
         }
@@ -381,7 +388,12 @@ __global__ void __launch_bounds__(PIPE_THREADS, 2)
             int64_t row0;
             int nl, nvalid;
             rows_of(cur, row0, nl, nvalid);
-            const float* sU = stages + (size_t)st * PIPE_STAGE_FLOATS;
+            float* sU = stages + (size_t)st * stage_floats;
+            const int nval = nvalid * R, ntail = nval & 3;   // floats past the bulk copy
+            if (ntail) {                                     // CTA-uniform
+                if (tid < ntail) sU[nval - ntail + tid] = U[row0 * R + nval - ntail + tid];
+                __syncthreads();
+            }
             unsigned char* Xh = X + (size_t)(i & 1) * 2 * xbytes;
             unsigned char* Xl = Xh + xbytes;
             const bool full_chunk = dense_shape && nl == NL && nvalid == NL * F;
@@ -413,7 +425,8 @@ __global__ void __launch_bounds__(PIPE_THREADS, 2)
             if (copy_to) {
                 float4* dst = reinterpret_cast<float4*>(copy_to + row0 * R);
                 const float4* srcv = reinterpret_cast<const float4*>(sU);
-                for (int q = tid; q < nvalid * R / 4; q += NT) dst[q] = srcv[q];
+                for (int q = tid; q < nval / 4; q += NT) dst[q] = srcv[q];
+                if (tid < ntail) copy_to[row0 * R + nval - ntail + tid] = sU[nval - ntail + tid];
             }
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
@@ -443,29 +456,36 @@ __global__ void __launch_bounds__(PIPE_THREADS, 2)
             int64_t row0;
             int nl, nvalid;
             rows_of(prev, row0, nl, nvalid);
-            // warp w reads lanes 32 (w mod 4).. of TMEM, columns half (w / 4) of its 32-column block
+            // warp w reads TMEM lanes 32 (w mod 4) .. +31 and half (w / 4) of the
+            // RP columns of the leaf those lanes hold
             const int qd = warp & 3, hf = warp >> 2;
-            const uint32_t taddr = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(j & 1) * TC_COLS +
-                                   (uint32_t)(32 * qd + 16 * hf);
-            float v[16];
-            tc_ld16(taddr, v);
-            int b, r, c0;
-            if (RP == 32) {
-                b = qd;
-                r = lane;
-                c0 = 16 * hf;
-            } else {  // RP == 16: lanes 0-15 hold leaf 2qd, lanes 16-31 leaf 2qd+1; half hf holds leaf 2qd+hf
-                b = 2 * qd + hf;
-                r = lane & 15;
-                c0 = 0;
-            }
-            const bool mine = (RP == 32) || ((lane >> 4) == hf);
-            if (mine && b < nl && r < R) {
-                float* gr = sG + (size_t)(prev.ch * NL + b) * Tp + tri_index(r, r, R) - r;
+            const uint32_t tbase = tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(j & 1) * TC_COLS;
+            if (RP >= 32) {
+                const int b = (32 * qd) / RP, r = (32 * qd + lane) % RP;
+                float* gr = (b < nl && r < R) ? sG + (size_t)(prev.ch * NL + b) * Tp + tri_index(r, r, R) - r
+                                              : nullptr;
 #pragma unroll
-                for (int q = 0; q < 16; ++q) {
-                    const int c = c0 + q;
-                    if (c >= r && c < R) gr[c] = v[q];
+                for (int t = 0; t < RP / 32; ++t) {
+                    const int c0 = hf * (RP / 2) + 16 * t;
+                    float v[16];
+                    tc_ld16(tbase + (uint32_t)(b * RP + c0), v);
+                    if (gr) {
+#pragma unroll
+                        for (int q = 0; q < 16; ++q) {
+                            const int c = c0 + q;
+                            if (c >= r && c < R) gr[c] = v[q];
+                        }
+                    }
+                }
+            } else {  // RP == 16: lanes 0-15 hold leaf 2qd, lanes 16-31 leaf 2qd+1; half hf holds leaf 2qd+hf
+                float v[16];
+                tc_ld16(tbase + (uint32_t)(32 * qd + 16 * hf), v);   // leaf 2qd+hf's 16 columns
+                const int b = 2 * qd + hf, r = lane & 15;
+                if ((lane >> 4) == hf && b < nl && r < R) {
+                    float* gr = sG + (size_t)(prev.ch * NL + b) * Tp + tri_index(r, r, R) - r;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        if (q >= r && q < R) gr[q] = v[q];
                 }
             }
             tc_fence_before();
@@ -529,15 +549,37 @@ cudaError_t launch_tc_lb(int LB, const float* U, int64_t I, int R, int F, int64_
     }
 }
 
+int pipe_stages(int RP) { return RP <= 32 ? PipeCfg<32>::S : RP == 64 ? PipeCfg<64>::S : PipeCfg<128>::S; }
+// one chunk: 128/RP leaves x F rows x R columns, padded to 128 bytes
+int pipe_stage_floats(int R, int F) { return ((128 / padded_rank(R)) * F * R + 31) / 32 * 32; }
+size_t pipe_smem(int R, int F, int LB, int G, int Tp) {
+    const int Fp = (F + 15) / 16 * 16;
+    int lv = 0;
+    while ((1 << lv) < G) ++lv;
+    return (size_t)pipe_stages(padded_rank(R)) * pipe_stage_floats(R, F) * 4 + (size_t)1024 * Fp +
+           (size_t)LB * Tp * 4 + (G > 1 ? (size_t)2 * (lv + 1) * Tp * 4 : 0);
+}
+constexpr size_t PIPE_SMEM_MAX = 220 * 1024;
+
 template <int RP, int LB>
 cudaError_t launch_pipe(const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree, float* top,
                         float* copy_to, int* status, int64_t nvb, size_t smem, int num_sms, cudaStream_t st) {
     auto k = tree_leaves_tc_pipe<RP, LB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    // the whole carveout as shared memory, so that the occupancy below (and the
+    // launch) see two 105 KB CTAs per SM at RP <= 32
+    e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PIPE_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, PipeCfg<RP>::MINB));
     const int Fp = (F + 15) / 16 * 16;
-    const int64_t grid = std::min<int64_t>(nvb, (int64_t)2 * num_sms);
-    k<<<(unsigned)grid, PIPE_THREADS, smem, st>>>(U, I, R, F, Fp, L, G, Tp, nvb, tree, top, copy_to, status); count_launch();
+    const int64_t grid = std::min<int64_t>(nvb, (int64_t)per_sm * num_sms);
+    k<<<(unsigned)grid, PIPE_THREADS, smem, st>>>(U, I, R, F, Fp, L, G, Tp, nvb, pipe_stage_floats(R, F), tree, top,
+                                                  copy_to, status);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -557,15 +599,19 @@ cudaError_t launch_pipe_lb(int LB, const float* U, int64_t I, int R, int F, int6
 
 bool tree_tc_supported(int R, int F) { return R >= 1 && R <= 128 && F >= 1 && F <= 128; }
 
-// The pipelined form needs R <= 32, R % 4 == 0 (bulk copies of whole rows in
-// 16-byte units), F <= 32 (one chunk <= 16 KB) and a 16-byte aligned source.
+// The pipelined form needs F R % 4 == 0 and a 16-byte aligned source (every
+// chunk starts on a 16-byte boundary) and its stages, operand buffers and one
+// leaf Gram within the shared memory of an SM.
 bool tree_tc_pipelined(int R, int F, const float* U) {
-    return R <= 32 && R % 4 == 0 && F <= 32 && ((uintptr_t)U & 15u) == 0;
+    if (R < 1 || R > 128 || F < 1 || F > 128 || (F * R) % 4 != 0 || ((uintptr_t)U & 15u) != 0) return false;
+    const int Tp = (tri_size(R) + 7) & ~7;
+    return pipe_smem(R, F, 1, 1, Tp) <= PIPE_SMEM_MAX;
 }
 
-// Geometry of the tensor-core leaf kernels.  Pipelined: LB = min(8, L) leaves
-// per group, G = 2 groups per block when L allows; shared memory padded to
-// 80 KB so that at most two CTAs (2 x 256 TMEM columns) share an SM.  Else:
+// Geometry of the tensor-core leaf kernels.  Pipelined: the largest LB <=
+// min(8, L) leaves per group, then G = 2 groups per block when L allows, that
+// fit the shared memory; padded to 80 KB so that at most two CTAs
+// (2 x 256 TMEM columns) share an SM.  Else:
 // LB leaves per group (power of two, <= 16, <= L, one group's leaf Grams
 // <= 64 KB), G groups per CTA (power of two, <= 8, shared memory <= 200 KB).
 void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out) {
@@ -573,11 +619,18 @@ void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_o
     int LB = 1, G = 1;
     size_t smem;
     if (pipelined) {
-        while (LB < 8 && (int64_t)LB * 2 <= L) LB *= 2;
-        if (L / LB >= 2) G = 2;
-        const int Fp = (F + 15) / 16 * 16;
-        const size_t need = (size_t)PIPE_S * PIPE_STAGE_FLOATS * 4 + (size_t)4 * 256 * Fp + (size_t)LB * Tp * 4 +
-                            (size_t)2 * (G == 2 ? 2 : 1) * Tp * 4;
+        int lb = 1;
+        while (lb < 8 && (int64_t)lb * 2 <= L) lb *= 2;
+        size_t need = 0;
+        for (bool done = false; lb >= 1 && !done; lb /= 2)
+            for (int g = L / lb >= 2 ? 2 : 1; g >= 1 && !done; --g) {
+                need = pipe_smem(R, F, lb, g, Tp);
+                if (need <= PIPE_SMEM_MAX || (lb == 1 && g == 1)) {
+                    LB = lb;
+                    G = g;
+                    done = true;
+                }
+            }
         smem = std::max<size_t>(need, 80 * 1024);
     } else {
         while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * Tp * 4 <= 64 * 1024) LB *= 2;
@@ -593,10 +646,12 @@ void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_o
 cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
                                   float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
                                   bool pipelined, int num_sms, cudaStream_t st) {
-    if (pipelined)
-        return padded_rank(R) == 16
-                   ? launch_pipe_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st)
-                   : launch_pipe_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
+    if (pipelined) switch (padded_rank(R)) {
+            case 16: return launch_pipe_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
+            case 32: return launch_pipe_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
+            case 64: return launch_pipe_lb<64>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
+            default: return launch_pipe_lb<128>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
+        }
     switch (padded_rank(R)) {
         case 16: return launch_tc_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
         case 32: return launch_tc_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);

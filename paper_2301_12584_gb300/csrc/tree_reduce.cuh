@@ -67,8 +67,10 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
             ++lvl;
             store_node(tree, h, Tp, e, hi);
         }
-        stk[(2 * lvl) * Tp + e] = hi;
-        stk[(2 * lvl + 1) * Tp + e] = lo;
+        if (G > 1) {   // with one group the stack is never read (and may have no space)
+            stk[(2 * lvl) * Tp + e] = hi;
+            stk[(2 * lvl + 1) * Tp + e] = lo;
+        }
         if (g == G - 1) {
             top[((size_t)top_slot * 2) * Tp + e] = hi;
             top[((size_t)top_slot * 2 + 1) * Tp + e] = lo;

@@ -5,6 +5,11 @@
   python -m paper_2301_12584_gb300.profile_cases build_tc  # tree_leaves_tc (BF16x3 on tcgen05), same factor
   python -m paper_2301_12584_gb300.profile_cases prep      # prep_pinv / prep_eig, R=32, N=3
   python -m paper_2301_12584_gb300.profile_cases descent64 # krp_descent<64,2> (team kernel), N=4, I=2^18, J=2^15
+  python -m paper_2301_12584_gb300.profile_cases descent100 # krp_descent_team<128,8>, N=3, I=2^20, R=100, J=2^14
+  python -m paper_2301_12584_gb300.profile_cases build100   # tree_leaves_fp32, one factor 2^20 x 100
+  python -m paper_2301_12584_gb300.profile_cases build100_tc # tree_leaves_tc_pipe<128,.> (BF16x3), same factor
+  python -m paper_2301_12584_gb300.profile_cases prep100    # prep_pinv / prep_eig / prep_etree, R=100, N=3
+  python -m paper_2301_12584_gb300.profile_cases minv100    # apply_minv<128>: U_0 = Y M⁻¹, 2^21 x 100
 
 Each case runs its kernel a few times (the first launches warm up), checks the
 device status and exits 0.  Inputs are the seeded generators of synth.py.
@@ -44,10 +49,23 @@ def descent64():
     assert s.sync_status() == 0, s.last_error()
 
 
-def build(precision=0):
-    I, R = 1 << 21, 32
+def descent100():
+    I, R, J = 1 << 20, 100, 1 << 14
+    Us = synth.gaussian_factors(3, I, R, seed=0)
+    s = Sampler([I] * 3, R, R)
+    for k in range(3):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    idx = torch.zeros((3, J), dtype=torch.int32, device="cuda")
+    w = torch.zeros(J, device="cuda")
+    SA = torch.zeros((J, R), device="cuda")
+    for d in range(3):
+        s.sample(0, J, 1, d, idx, w, None, SA)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def build(precision=0, I=1 << 21, R=32):
     U = torch.from_numpy(synth.skewed_row_factors(1, I, R, seed=0)[0]).cuda()
-    s = Sampler([I], R, 32, precision)
+    s = Sampler([I], R, R, precision)
     for _ in range(3):
         s.set_factor(0, U)
     assert s.sync_status() == 0, s.last_error()
@@ -55,6 +73,36 @@ def build(precision=0):
 
 def build_tc():
     build(precision=1)
+
+
+def prep100():
+    I, R = 1 << 14, 100
+    Us = synth.gaussian_factors(3, I, R, seed=0)
+    s = Sampler([I] * 3, R, R)
+    for k in range(3):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    for _ in range(4):
+        s.sample_prepare(0)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def minv100():
+    from .krpls import SparseTensor
+    dims, R, J = (1 << 21, 64, 64), 100, 1 << 14
+    coords, vals = synth.sparse_zipf_tensor(dims, 200000, seed=0)
+    Us = synth.gaussian_factors(3, list(dims), R, seed=1)
+    s = Sampler(list(dims), R, R)
+    for k in range(3):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    t = SparseTensor(dims, coords, vals)
+    idx = torch.zeros((3, J), dtype=torch.int32, device="cuda")
+    w = torch.zeros(J, device="cuda")
+    SA = torch.zeros((J, R), device="cuda")
+    Uo = torch.zeros((dims[0], R), device="cuda")
+    for d in range(3):
+        s.sample(0, J, 1, d, idx, w, None, SA)
+        s.solve_sparse(t, 0, J, idx, w, SA, Uo)
+    assert s.sync_status() == 0, s.last_error()
 
 
 def prep():
@@ -69,7 +117,8 @@ def prep():
 
 
 if __name__ == "__main__":
-    {"descent": descent, "descent64": descent64, "build": build, "build_tc": build_tc,
-     "prep": prep}[sys.argv[1]]()
+    {"descent": descent, "descent64": descent64, "descent100": descent100, "build": build, "build_tc": build_tc,
+     "build100": lambda: build(0, 1 << 20, 100), "build100_tc": lambda: build(1, 1 << 20, 100),
+     "prep": prep, "prep100": prep100, "minv100": minv100}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")

@@ -50,13 +50,16 @@ def unpack(slot, R):
 
 @pytest.mark.parametrize("I,R,F", [(64, 8, 8), (1000, 8, 8), (37, 5, 3), (5, 8, 8), (20000, 32, 32),
                                    (3001, 25, 25), (700, 64, 64), (300, 128, 128), (100, 3, 1), (4096, 16, 16),
-                                   (5000, 32, 20), (999, 50, 50), (3000, 100, 100)])
+                                   (5000, 32, 20), (999, 50, 50), (3000, 100, 100), (1001, 70, 70),
+                                   (777, 90, 60)])
 def test_bf16x3_tree_matches_partial_grams(I, R, F):
     rng = np.random.default_rng(I * 7 + R)
     U = rng.standard_normal((I, R)).astype(np.float32)
     U[rng.choice(I, max(1, I // 100), replace=False)] *= 100.0
     s = sampler_for([U], F, BF16X3)
     assert s.sync_status() == 0, s.last_error()
+    # the leaf kernel also wrote the sampler's copy of the rows (ragged tails included)
+    assert np.array_equal(s.get_factor(0), U)
     L, d, Tp = s.tree_info(0)
     tree = s.get_tree(0)
     U64 = U.astype(np.float64)
