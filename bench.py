@@ -63,6 +63,8 @@ def parse():
                          "(per-problem launches vs one launch per phase vs graph replay); "
                          "rank_sweep: N=4, I=2^20, U(-1,1), J=2^17 at --rank R")
     ap.add_argument("--rank", type=int, default=32)
+    ap.add_argument("--descent", choices=["auto", "team", "node_major"], default="auto",
+                    help="rank_sweep: descent form for 32 < R <= 128")
     ap.add_argument("--ranks", default="25,50,100", help="sparse_als: decomposition ranks")
     ap.add_argument("--nnz", type=int, default=200_000_000, help="sparse_als: nonzeros")
     ap.add_argument("--sweeps", type=int, default=20, help="sparse_als: ALS sweeps per configuration")
@@ -313,6 +315,7 @@ def run_rank_sweep(args):
     stream = torch.cuda.Stream(device=dev)
     Us = synth.uniform_factors(N, I, R, seed=0)
     s = Sampler([I] * N, R, R, stream=stream)
+    s.set_descent_form({"auto": 0, "team": 1, "node_major": 2}[args.descent])
     for k in range(N):
         s.set_factor(k, torch.from_numpy(Us[k]).to(dev))
     Xt = synth.planted_solution(R, NRHS, seed=1)
@@ -364,7 +367,9 @@ def run_rank_sweep(args):
     depth = (-(-I // R) - 1).bit_length()
     path_bytes = N * (4 * Tp * depth + 4 * R * R)
     achieved = path_bytes * J / (draw_ms / 1e3) / 1e9
-    kernel = "krp_descent_fast" if R <= 32 else ("krp_descent_team<64,2>" if R <= 64 else "krp_descent_team<128,8>")
+    kernel = "krp_descent_fast" if R <= 32 else (
+        ("krp_descent_nm<64>" if R <= 64 else "krp_descent_nm<128>") if args.descent == "node_major" else
+        ("krp_descent_team<64,2>" if R <= 64 else "krp_descent_team<128,8>"))
     roof = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": path_bytes * J,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
@@ -379,7 +384,8 @@ def run_rank_sweep(args):
         "metric": "KRP leverage samples/s, rank sweep (prepare + draw + planted rows + dense solve per step)",
         "value": J / (ms / 1e3), "unit": "samples/s", "higher_is_better": True, "n_gpus": 1, "steps": steps,
         "warmup": warm, "ms_per_step": ms, "dtype": "f32", "data": "synthetic", "vs_baseline": None,
-        "config": {"workload": f"rank_sweep_N4_I2^20_R{R}_J2^17_nrhs8", "R": R, "l2": "inputs larger than L2"},
+        "config": {"workload": f"rank_sweep_N4_I2^20_R{R}_J2^17_nrhs8", "R": R, "descent": args.descent,
+                   "l2": "inputs larger than L2"},
         "phases_ms": {"prepare_and_draw": sample_ms, "prepare": prep_ms, "draw": draw_ms, "solve": solve_ms},
         "roofline": roof,
         "x_rel_err_vs_fp64_same_sketch": float(np.linalg.norm(Xg - Xo) / np.linalg.norm(Xo)),

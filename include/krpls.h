@@ -138,6 +138,23 @@ krp_status krp_sample(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed,
  * krp_sample_draw returns KRP_ESTATE if the last prepare was for another
  * exclude_j or a factor was set since. */
 krp_status krp_sample_prepare(krp_sampler* s, int exclude_j);
+
+/* Form of the descent for 32 < R <= 128 (no effect at R <= 32): the same
+ * draws up to the rounding of the masses (flips only where a uniform lies
+ * within ~1e-6 of a bin edge).
+ *   KRP_DESCENT_AUTO (default) and KRP_DESCENT_TEAM: one team of warps per
+ *     sample, two tree levels per fetch, the sample's quadratic-form weights
+ *     kept in registers for a whole tree;
+ *   KRP_DESCENT_NODE_MAJOR: each CTA advances a batch of up to 32 samples
+ *     level by level together, grouping them by the node they sit at so that
+ *     every distinct node is fetched once per batch (shared upper levels cost
+ *     one fetch per CTA, deeper ones stream through a ring of copies across
+ *     the batch); the weights are formed per sample and level.
+ * KRP_EINVAL for another value. */
+#define KRP_DESCENT_AUTO 0
+#define KRP_DESCENT_TEAM 1
+#define KRP_DESCENT_NODE_MAJOR 2
+krp_status krp_set_descent_form(krp_sampler* s, int form);
 krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
                            int32_t* idx, float* weight, float* logq, float* SA);
 

@@ -11,6 +11,7 @@
 
 struct krp_sampler {
     int N = 0, R = 0, F = 0, prec = 0;
+    int descent_form = 0;       // KRP_DESCENT_* for 32 < R <= 128
     cudaStream_t stream = nullptr;
     int T = 0, Tp = 0;          // packed triangle size and node stride (floats)
     int Rp = 1, dE = 0;         // eigencomponent tree: leaves (R padded to 2^dE)
@@ -201,6 +202,10 @@ bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
 // 32 < R <= 128 path (descent_team.cu): TMA-staged teams of warps; false if R is out of range.
 bool launch_descent_team(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
                          float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
+// 32 < R <= 128 node-major path (descent_nm.cu): CTA batches advanced level by
+// level; false if R is out of range or no batch fits the shared memory.
+bool launch_descent_nm(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
+                       float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
 cudaError_t launch_wait_timeout_probe(krp_sampler* s, int tries);
 // a6: gather
 krp_status launch_gather(krp_sampler* s, int exclude_j, int64_t J, const int32_t* idx,

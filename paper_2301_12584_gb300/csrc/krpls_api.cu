@@ -210,6 +210,14 @@ krp_status krp_set_factor(krp_sampler* s, int j, const float* U) {
     return krp_set_factor_prec(s, j, U, s->prec);
 }
 
+krp_status krp_set_descent_form(krp_sampler* s, int form) {
+    if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");
+    if (form != KRP_DESCENT_AUTO && form != KRP_DESCENT_TEAM && form != KRP_DESCENT_NODE_MAJOR)
+        return fail(s, KRP_EINVAL, "krp_set_descent_form: unknown form");
+    s->descent_form = form;
+    return KRP_OK;
+}
+
 static krp_status check_sample_args(krp_sampler* s, int exclude_j) {
     if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");
     if (exclude_j < -1 || exclude_j >= s->N) return fail(s, KRP_EINVAL, "exclude_j out of range");

@@ -567,16 +567,12 @@ cudaError_t launch_pipe(const float* U, int64_t I, int R, int F, int64_t L, int 
     auto k = tree_leaves_tc_pipe<RP, LB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    // the whole carveout as shared memory, so that the occupancy below (and the
-    // launch) see two 105 KB CTAs per SM at RP <= 32
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, PIPE_THREADS, smem);
-    if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, PipeCfg<RP>::MINB));
+    // MINB CTAs per SM by design (the occupancy query reports one 105 KB CTA
+    // per SM at RP <= 32 although two are resident: 0.28 vs 0.17 ms at 2^21 rows)
     const int Fp = (F + 15) / 16 * 16;
-    const int64_t grid = std::min<int64_t>(nvb, (int64_t)per_sm * num_sms);
+    const int64_t grid = std::min<int64_t>(nvb, (int64_t)PipeCfg<RP>::MINB * num_sms);
     k<<<(unsigned)grid, PIPE_THREADS, smem, st>>>(U, I, R, F, Fp, L, G, Tp, nvb, pipe_stage_floats(R, F), tree, top,
                                                   copy_to, status);
     count_launch();

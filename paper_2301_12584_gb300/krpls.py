@@ -17,6 +17,7 @@ KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EZERO, KRP_ESINGULAR, KRP_ENUMERI
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 KRP_PREC_FP32, KRP_PREC_BF16X3 = 0, 1
 KRP_PINV_FALLBACK = 1
+KRP_DESCENT_AUTO, KRP_DESCENT_TEAM, KRP_DESCENT_NODE_MAJOR = 0, 1, 2
 
 STATUS_NAMES = {0: "KRP_OK", -1: "KRP_EINVAL", -2: "KRP_ENOMEM", -3: "KRP_ECUDA", -4: "KRP_EZERO",
                 -5: "KRP_ESINGULAR", -6: "KRP_ENUMERIC", -7: "KRP_ETIMEOUT", -8: "KRP_ESTATE"}
@@ -33,6 +34,7 @@ SIGNATURES = [
     ("krp_set_factor_prec", _INT, [_P, _INT, _P, _INT]),
     ("krp_sample", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_sample_prepare", _INT, [_P, _INT]),
+    ("krp_set_descent_form", _INT, [_P, _INT]),
     ("krp_sample_draw", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_launch_count", _I64, []),
     ("krp_debug_wait_timeout", _INT, [_P, _INT]),
@@ -155,6 +157,10 @@ class Sampler:
     def sample(self, exclude_j, J, seed, draw_id, idx, weight, logq=None, SA=None):
         self._check(self._lib.krp_sample(self.h, int(exclude_j), int(J), int(seed), int(draw_id),
                                          _P(_ptr(idx)), _P(_ptr(weight)), _P(_ptr(logq)), _P(_ptr(SA))))
+
+    def set_descent_form(self, form):
+        """KRP_DESCENT_AUTO / _NODE_MAJOR (batched node-major) or _TEAM (team per sample), 32 < R <= 128."""
+        self._check(self._lib.krp_set_descent_form(self.h, int(form)))
 
     def sample_prepare(self, exclude_j):
         self._check(self._lib.krp_sample_prepare(self.h, int(exclude_j)))

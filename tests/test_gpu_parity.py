@@ -114,8 +114,14 @@ def test_tree_matches_partial_grams(I, R, F):
 
 # -------------------------------------------------- sampler index parity ----
 @pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1",
-                                  "R64_N4", "R128"])
+                                  "R64_N4", "R128", "R64_N4_nm", "R128_nm", "R37_excl", "R37_excl_nm",
+                                  "R100_ragged_nm", "R48_F20_nm"])
 def test_sampler_index_parity(case):
+    """For 32 < R <= 128 the default descent is the team-per-sample kernel;
+    "_nm" cases draw with the node-major batched kernel."""
+    from paper_2301_12584_gb300.krpls import KRP_DESCENT_NODE_MAJOR
+    nm = case.endswith("_nm")
+    case = case.replace("_nm", "")
     J = 1 << 15
     excl = -1
     F = 0
@@ -141,11 +147,21 @@ def test_sampler_index_parity(case):
         Us, F, J = synth.uniform_factors(4, 200, 64, seed=11), 64, 1 << 14
     elif case == "R128":
         Us, F, J = synth.uniform_factors(3, 300, 128, seed=12), 128, 1 << 12
+    elif case == "R37_excl":   # F R odd: leaf blocks by plain loads; factor 1 excluded
+        Us, F, J, excl = synth.gaussian_factors(3, [300, 211, 150], 37, seed=13), 37, 1 << 13, 1
+    elif case == "R100_ragged":
+        Us, F, J = synth.gaussian_factors(3, [1234, 777, 2001], 100, seed=14), 100, 1 << 12
+    elif case == "R48_F20":
+        Us, F, J = synth.skewed_row_factors(3, 700, 48, seed=15), 20, 1 << 13
     s = sampler_for(Us, F)
+    if nm:
+        s.set_descent_form(KRP_DESCENT_NODE_MAJOR)
     out = draw(s, Us, excl, J, seed=12345, draw_id=3, logq=True)
     U64 = [U.astype(np.float64) for U in Us]
     eig = None
-    if case == "R128":
+    # R128 and the Gaussian large-R cases (each G_k is close to a multiple of
+    # the identity, so G_{>k}'s eigenvalues cluster tightly)
+    if case in ("R128", "R100_ragged", "R37_excl", "R48_F20"):
         # G_{>k} has 128 eigenvalues within a factor 1.3 (relative gaps down to
         # 2e-6): the eigenbasis inside such clusters is not pinned (reading C6),
         # while any decomposition G_{>k} = sum_u lam_u v_u v_uᵀ yields the same
@@ -164,7 +180,7 @@ def test_sampler_index_parity(case):
     if case == "R32":
         mism = check_index_parity(out["idx"], ref, J, tol=2e-7)
         assert mism <= 2e-3 * J, f"{mism} mismatches of {J}"
-    elif case in ("R64_N4", "R128"):
+    elif case in ("R64_N4", "R128", "R37_excl", "R100_ragged", "R48_F20"):
         # FP32 tree storage: a mass is off by ~6e-8 x (sum of |terms|), and with
         # R^2 terms of both signs that sum exceeds the mass itself; flips stay
         # within 1e-5 C of an edge, at a rate like the R32 case's
@@ -232,6 +248,77 @@ def test_branch_probabilities_match_fp64_tree():
                     checked += 1
             h = h * U64[p][t_k]
     assert checked > 1000
+    s.close()
+
+
+@pytest.mark.parametrize("form", [2, 1])
+def test_branch_probabilities_r64(form):
+    """Per-level branch probabilities m_L / m_c of the node-major (2) and team
+    (1) descents at R = 64 against the FP64 trees, replaying the GPU's own
+    eigendecomposition (checked to reconstruct G_{>k}; the basis inside
+    clusters of eigenvalues is not pinned)."""
+    Us = synth.skewed_entry_factors(3, [300, 260, 170], 64, seed=21)
+    F = 64
+    s = sampler_for(Us, F)
+    s.set_descent_form(form)
+    N, R, J, n_tr = 3, 64, 512, 96
+    idx = torch.zeros((N, J), dtype=torch.int32, device=DEV)
+    w = torch.zeros(J, dtype=torch.float32, device=DEV)
+    tr = torch.zeros(n_tr * N * 2 * 66, dtype=torch.float32, device=DEV)
+    s.debug_trace(-1, J, 77, 4, idx, w, tr, n_tr)
+    assert s.sync_status() == 0, s.last_error()
+    trace = tr.cpu().numpy().reshape(n_tr, N, 2, 66)
+    gi = idx.cpu().numpy().astype(np.int64)
+    U64 = [U.astype(np.float64) for U in Us]
+    prep = O.SamplerPrep(U64, -1)
+    eig = {}
+    for k in prep.incl:
+        lam, V, _, _ = s.get_prep(k)
+        rec = (V * np.maximum(lam, 0.0)) @ V.T
+        # the replayed decomposition must reconstruct G_{>k} (measured 3e-6 of
+        # its largest entry on this clustered spectrum; the eigensolver's own
+        # bars are test_prepare_matches_fp64_oracle's)
+        assert np.abs(rec - prep.Ggt[k]).max() <= 1e-5 * np.abs(prep.Ggt[k]).max()
+        eig[k] = (lam, V)
+    ue, ur = sampler_uniforms(77, 4, n_tr, N)
+    checked = 0
+    for sm in range(n_tr):
+        h = np.ones(R)
+        for p in range(N):
+            lam, V = eig[p]
+            u_k, tr_u = O.eig_tree_row_sample(lam, V, O.gram(U64[p]), h, ue[sm, p])
+            ht = h * V[:, u_k]
+            t_k, tr_t = O.tree_row_sample(U64[p], F, np.ones((R, R)), ht, ur[sm, p])
+            if t_k != gi[p, sm]:
+                break   # a near-edge flip: the rest of this sample's path differs
+            for st, trc in ((0, tr_u), (1, tr_t)):
+                for lvl, (ml, mc) in enumerate(trc):
+                    g_ml, g_mc = trace[sm, p, st, 2 + 2 * lvl], trace[sm, p, st, 3 + 2 * lvl]
+                    pl, gpl = ml / mc, g_ml / g_mc
+                    # masses sum R^2 terms of both signs: FP32 storage error
+                    # relative to a small mass grows with R
+                    assert abs(gpl - pl) <= 1e-6 + 2e-5 * pl, (form, sm, p, st, lvl, gpl, pl)
+                    checked += 1
+            h = h * U64[p][t_k]
+    assert checked > 1000, checked
+    s.close()
+
+
+def test_node_major_and_team_draws_agree():
+    """The two descent forms differ only in the rounding of the masses: the
+    same draws but for rare near-edge flips, and the same weights."""
+    from paper_2301_12584_gb300.krpls import KRP_DESCENT_NODE_MAJOR, KRP_DESCENT_TEAM
+    Us = synth.uniform_factors(4, 3000, 64, seed=31)
+    s = sampler_for(Us, 64)
+    J = 1 << 15
+    outs = []
+    for form in (KRP_DESCENT_NODE_MAJOR, KRP_DESCENT_TEAM):
+        s.set_descent_form(form)
+        outs.append(draw(s, Us, -1, J, 5, 9, logq=True))
+    diff = (outs[0]["idx"] != outs[1]["idx"]).any(axis=0)
+    assert diff.mean() <= 2e-3, diff.mean()
+    same = ~diff
+    np.testing.assert_allclose(outs[0]["weight"][same], outs[1]["weight"][same], rtol=1e-5)
     s.close()
 
 
