@@ -20,6 +20,8 @@
 
 #include <math.h>
 
+#include <algorithm>
+
 namespace krp {
 namespace {
 
@@ -39,10 +41,12 @@ __device__ __forceinline__ bool tmb_wait(uint64_t* m, uint32_t parity, int max_t
 }
 
 
-template <int RMAX, int TEAM>
+template <int RMAX, int TEAM, int CTA_THREADS = 256, int MINB = 2>
 struct TeamCfg {
     static constexpr int NT = 32 * TEAM;                        // threads per sample
-    static constexpr int TEAMS = 256 / NT;                      // samples per CTA
+    static constexpr int THREADS = CTA_THREADS;
+    static constexpr int BLOCKS = MINB;                         // CTAs per SM the registers are sized for
+    static constexpr int TEAMS = CTA_THREADS / NT;              // samples per CTA
     static constexpr int TPMAX = ((RMAX * (RMAX + 1) / 2) + 7) & ~7;
     static constexpr int NC4 = TPMAX / 4;
     static constexpr int NCH = (NC4 + NT - 1) / NT;             // float4 chunks per thread
@@ -51,24 +55,31 @@ struct TeamCfg {
     // stage, hh, hl, th, 4 x TEAM floats of reductions, pick/flag ints, mbarrier
     static constexpr int TEAM_BYTES = ((STAGE + 3 * RMAX + 4 * TEAM) * 4 + 4 * 4 + 16 + 127) & ~127;
     static constexpr int SMEM = TEAMS * TEAM_BYTES;
+    // one team's bytes for the actual node stride: a three-node stage of 3 Tp floats
+    static int team_bytes(int Tp) { return ((3 * Tp + 3 * RMAX + 4 * TEAM) * 4 + 4 * 4 + 16 + 127) & ~127; }
 };
 
-template <int RMAX, int TEAM>
-__global__ void __launch_bounds__(256, 2) krp_descent_team(const __grid_constant__ FastParams P) {
-    using C = TeamCfg<RMAX, TEAM>;
+template <int RMAX, int TEAM, int CTA_THREADS, int MINB>
+__global__ void __launch_bounds__(CTA_THREADS, MINB)
+    krp_descent_team(const __grid_constant__ FastParams P) {
+    using C = TeamCfg<RMAX, TEAM, CTA_THREADS, MINB>;
     constexpr int NT = C::NT, NCH = C::NCH;
     extern __shared__ __align__(128) unsigned char smem[];
     const int team = threadIdx.x / NT, tt = threadIdx.x % NT, lane = tt & 31, wib = tt >> 5;
-    unsigned char* base = smem + team * C::TEAM_BYTES;
+    // a CTA of one team lays its stage out for the actual node stride (3 Tp
+    // floats); CTAs of several teams use the fixed stride of RMAX
+    constexpr bool ONE = C::TEAMS == 1;
+    const int stage_f = ONE ? 3 * P.Tp : C::STAGE;
+    unsigned char* base = smem + (ONE ? 0 : (size_t)team * C::TEAM_BYTES);
     float* stage = reinterpret_cast<float*>(base);
-    float* hh = stage + C::STAGE;
+    float* hh = stage + stage_f;
     float* hl = hh + RMAX;
     float* th = hl + RMAX;
     float* red = th + RMAX;                    // TEAM floats (sums), then 2 TEAM (double-float sums)
     float* red2 = red + TEAM;
     float* scn = red2 + 2 * TEAM;              // TEAM floats (scan totals)
     int* pick = reinterpret_cast<int*>(scn + TEAM);   // [0] first, [1] last
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + ((C::STAGE + 3 * RMAX + 4 * TEAM) * 4 + 16 + 7) / 8 * 8);
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(base + ((stage_f + 3 * RMAX + 4 * TEAM) * 4 + 16 + 7) / 8 * 8);
 
     const int R = P.R, T = P.T, Tp = P.Tp;
     const int nc4 = Tp >> 2;
@@ -306,7 +317,7 @@ __global__ void __launch_bounds__(256, 2) krp_descent_team(const __grid_constant
         return c;
     };
 
-    const bool leaf_tma = (R & 3) == 0 && P.F * R <= C::STAGE;
+    const bool leaf_tma = (R & 3) == 0 && P.F * R <= stage_f;
     const int64_t teams_total = (int64_t)gridDim.x * C::TEAMS;
     for (int64_t s = (int64_t)blockIdx.x * C::TEAMS + team; s < P.J && alive; s += teams_total) {
         for (int a = tt; a < RMAX; a += NT) {
@@ -538,19 +549,19 @@ __global__ void __launch_bounds__(256, 2) krp_descent_team(const __grid_constant
     }
 }
 
-template <int RMAX, int TEAM>
+template <int RMAX, int TEAM, int CTA_THREADS = 256, int MINB = 2>
 cudaError_t launch_team_t(const FastParams& P, int num_sms, cudaStream_t st) {
-    using C = TeamCfg<RMAX, TEAM>;
-    auto k = krp_descent_team<RMAX, TEAM>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    using C = TeamCfg<RMAX, TEAM, CTA_THREADS, MINB>;
+    auto k = krp_descent_team<RMAX, TEAM, CTA_THREADS, MINB>;
+    const int smem = C::TEAMS == 1 ? C::team_bytes(P.Tp) : C::SMEM;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, C::SMEM);
-    per_sm = per_sm > 0 ? per_sm : 1;
+    // CTAs per SM: what the shared memory holds, up to the register design (MINB)
+    const int per_sm = std::max(1, std::min(MINB, (228 * 1024) / (smem + 1024)));
     const int64_t need = (P.J + C::TEAMS - 1) / C::TEAMS;
     const int64_t grid = need < (int64_t)num_sms * per_sm ? need : (int64_t)num_sms * per_sm;
-    k<<<(unsigned)grid, 256, C::SMEM, st>>>(P); count_launch();
+    k<<<(unsigned)grid, CTA_THREADS, smem, st>>>(P); count_launch();
     return cudaGetLastError();
 }
 
@@ -572,7 +583,14 @@ bool launch_descent_team(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
     P.SA = SA;
     P.trace = trace;
     P.n_trace = trace ? n_trace : 0;
-    *err = s->R <= 64 ? launch_team_t<64, 2>(P, s->num_sms, s->stream) : launch_team_t<128, 8>(P, s->num_sms, s->stream);
+    // 64 < R <= 104: one team of 4 warps per 128-thread CTA, three CTAs per SM
+    // (a stage of 3 Tp floats <= 65 KB); larger R: teams of 8 warps, two per SM
+    if (s->R <= 64)
+        *err = launch_team_t<64, 2>(P, s->num_sms, s->stream);
+    else if (s->R <= 104)
+        *err = launch_team_t<104, 4, 128, 3>(P, s->num_sms, s->stream);
+    else
+        *err = launch_team_t<128, 8>(P, s->num_sms, s->stream);
     return true;
 }
 

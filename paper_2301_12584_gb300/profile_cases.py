@@ -5,7 +5,8 @@
   python -m paper_2301_12584_gb300.profile_cases build_tc  # tree_leaves_tc (BF16x3 on tcgen05), same factor
   python -m paper_2301_12584_gb300.profile_cases prep      # prep_pinv / prep_eig, R=32, N=3
   python -m paper_2301_12584_gb300.profile_cases descent64 # krp_descent<64,2> (team kernel), N=4, I=2^18, J=2^15
-  python -m paper_2301_12584_gb300.profile_cases descent100 # krp_descent_team<128,8>, N=3, I=2^20, R=100, J=2^14
+  python -m paper_2301_12584_gb300.profile_cases descent100 # team descent (default form), N=3, I=2^20, R=100, J=2^14
+  python -m paper_2301_12584_gb300.profile_cases descent100_nm # krp_descent_nm<128> (node-major form), same case
   python -m paper_2301_12584_gb300.profile_cases build100   # tree_leaves_fp32, one factor 2^20 x 100
   python -m paper_2301_12584_gb300.profile_cases build100_tc # tree_leaves_tc_pipe<128,.> (BF16x3), same factor
   python -m paper_2301_12584_gb300.profile_cases prep100    # prep_pinv / prep_eig / prep_etree, R=100, N=3
@@ -49,10 +50,11 @@ def descent64():
     assert s.sync_status() == 0, s.last_error()
 
 
-def descent100():
+def descent100(form=0):
     I, R, J = 1 << 20, 100, 1 << 14
     Us = synth.gaussian_factors(3, I, R, seed=0)
     s = Sampler([I] * 3, R, R)
+    s.set_descent_form(form)
     for k in range(3):
         s.set_factor(k, torch.from_numpy(Us[k]).cuda())
     idx = torch.zeros((3, J), dtype=torch.int32, device="cuda")
@@ -117,7 +119,8 @@ def prep():
 
 
 if __name__ == "__main__":
-    {"descent": descent, "descent64": descent64, "descent100": descent100, "build": build, "build_tc": build_tc,
+    {"descent": descent, "descent64": descent64, "descent100": descent100,
+     "descent100_nm": lambda: descent100(2), "build": build, "build_tc": build_tc,
      "build100": lambda: build(0, 1 << 20, 100), "build100_tc": lambda: build(1, 1 << 20, 100),
      "prep": prep, "prep100": prep100, "minv100": minv100}[sys.argv[1]]()
     torch.cuda.synchronize()

@@ -115,7 +115,7 @@ def test_tree_matches_partial_grams(I, R, F):
 # -------------------------------------------------- sampler index parity ----
 @pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1",
                                   "R64_N4", "R128", "R64_N4_nm", "R128_nm", "R37_excl", "R37_excl_nm",
-                                  "R100_ragged_nm", "R48_F20_nm"])
+                                  "R100_ragged", "R100_ragged_nm", "R48_F20_nm"])
 def test_sampler_index_parity(case):
     """For 32 < R <= 128 the default descent is the team-per-sample kernel;
     "_nm" cases draw with the node-major batched kernel."""
