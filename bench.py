@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 N_FACT, I_ROWS, RANK, LEAF, J_DRAW = 3, 1 << 22, 32, 32, 1 << 16
 # dram__bytes_read.sum + dram__bytes_write.sum of one krp_descent_fast<32> launch of this
 # workload (one-pass ncu capture of the first timed draw); to be re-taken whenever that kernel changes.
-DESCENT_DRAM_BYTES = 3_838_974_976 + 12_240_128
+DESCENT_DRAM_BYTES = 3_818_774_016 + 12_289_536
 METRIC = "KRP leverage samples/s (one-factor update + prepare + draw + gather per step)"
 UNIT = "samples/s"
 WORKLOAD = "krp_sampler_N3_I2^22_R32_F32_J2^16_update_per_draw"

@@ -65,8 +65,9 @@ struct EigWork {
     double* red;
 };
 
-__device__ void eig_fp32_refined(const double* __restrict__ A, int n, double* __restrict__ X, double* __restrict__ lam,
-                                 EigWork w) {
+// Scale A by max |A| into w.As (FP64) and w.Af (FP32), FP32 Jacobi, X = the
+// FP32 eigenvectors in FP64.  Returns the scale.
+__device__ double eig_fp32_start(const double* __restrict__ A, int n, double* __restrict__ X, EigWork w) {
     const int nn = n * n;
     double mx = 0.0;
     for (int e = threadIdx.x; e < nn; e += blockDim.x) mx = fmax(mx, fabs(A[e]));
@@ -86,6 +87,13 @@ __device__ void eig_fp32_refined(const double* __restrict__ A, int n, double* __
     jacobi_eig<float>(w.Af, w.Vf, n, w.csf, w.pr, w.red, 30, 4e-7);
     for (int e = threadIdx.x; e < nn; e += blockDim.x) X[e] = (double)w.Vf[e];
     __syncthreads();
+    return scale;
+}
+
+__device__ void eig_fp32_refined(const double* __restrict__ A, int n, double* __restrict__ X, double* __restrict__ lam,
+                                 EigWork w) {
+    const int nn = n * n;
+    const double scale = eig_fp32_start(A, n, X, w);
     // Rm = I - XᵀX ; T = As X
     for (int e = threadIdx.x; e < nn; e += blockDim.x) {
         const int i = e / n, j = e % n;
@@ -336,25 +344,12 @@ __device__ __forceinline__ void prep_pinv_body(const PrepParams& P, int N, int e
 // eigenvectors as FP64 columns, FP32 rows and FP32 residual rows (E_k is
 // built from them by prep_etree).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R, int Rp, int dE, int Tp,
-                                              const double* __restrict__ G64, const double* __restrict__ Gplus64,
-                                              double* __restrict__ lam64, double* __restrict__ V64,
-                                              float* __restrict__ V32, float* __restrict__ V32lo,
-                                              float* __restrict__ etree, double* __restrict__ gwork, int p) {
-    extern __shared__ __align__(16) char smp[];
+// Eigenvalues clamped to >= 0 and put in ascending order; eigenvectors as
+// FP64 columns, FP32 rows and FP32 residual rows (the outputs of prep_eig).
+__device__ __forceinline__ void eig_output(int k, int R, const double* __restrict__ X, double* lam, int* pos,
+                                           double* __restrict__ lam64, double* __restrict__ V64,
+                                           float* __restrict__ V32, float* __restrict__ V32lo) {
     const int RR = R * R;
-    const int n_incl = P.n_incl;
-    const int k = P.incl[p];
-    double *X, *A64, *lam;
-    int* pos;
-    EigWork w = carve(smp, R, gwork ? gwork + (size_t)p * 6 * RR : nullptr, &X, &A64, &lam, &pos);
-    for (int e = threadIdx.x; e < RR; e += blockDim.x) {     // G_{>k} = G⁺ ⊛ ⊛_{m>k} G_m
-        double v = Gplus64[e];
-        for (int q = p + 1; q < n_incl; ++q) v *= G64[(size_t)P.incl[q] * RR + e];
-        A64[e] = v;
-    }
-    __syncthreads();
-    eig_fp32_refined(A64, R, X, lam, w);
     for (int i = threadIdx.x; i < R; i += blockDim.x) lam[i] = fmax(lam[i], 0.0);
     __syncthreads();
     ascending_positions(lam, R, pos);
@@ -369,6 +364,130 @@ __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R,
         V32lo[(size_t)k * RR + o * R + row] = (float)(v - (double)vh);
     }
     for (int u = threadIdx.x; u < R; u += blockDim.x) lam64[(size_t)k * R + pos[u]] = lam[u];
+}
+
+// split: stop after the FP32 Jacobi, leaving As and X in gwork and the scale
+// in scales[p]; the refinement then runs over many CTAs (refine_* below).
+__device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R, int Rp, int dE, int Tp,
+                                              const double* __restrict__ G64, const double* __restrict__ Gplus64,
+                                              double* __restrict__ lam64, double* __restrict__ V64,
+                                              float* __restrict__ V32, float* __restrict__ V32lo,
+                                              float* __restrict__ etree, double* __restrict__ gwork, int p,
+                                              bool split = false, double* __restrict__ scales = nullptr) {
+    extern __shared__ __align__(16) char smp[];
+    const int RR = R * R;
+    const int n_incl = P.n_incl;
+    const int k = P.incl[p];
+    double *X, *A64, *lam;
+    int* pos;
+    EigWork w = carve(smp, R, gwork ? gwork + (size_t)p * 6 * RR : nullptr, &X, &A64, &lam, &pos);
+    for (int e = threadIdx.x; e < RR; e += blockDim.x) {     // G_{>k} = G⁺ ⊛ ⊛_{m>k} G_m
+        double v = Gplus64[e];
+        for (int q = p + 1; q < n_incl; ++q) v *= G64[(size_t)P.incl[q] * RR + e];
+        A64[e] = v;
+    }
+    __syncthreads();
+    if (split) {
+        const double scale = eig_fp32_start(A64, R, X, w);
+        if (threadIdx.x == 0) scales[p] = scale;
+        return;
+    }
+    eig_fp32_refined(A64, R, X, lam, w);
+    eig_output(k, R, X, lam, pos, lam64, V64, V32, V32lo);
+}
+
+// ---------------------------------------------------------------------------
+// The Ogita–Aishima refinement step of eig_fp32_refined for R > 32, spread
+// over CTAs: GB300 runs FP64 at ~1/64 of FP32, so the four R x R products on
+// one SM dominate the preparation there.  Per included factor p the work area
+// holds six R x R FP64 matrices: [0] As (scaled G_{>k}), [1] S, [2] T,
+// [3] Rm, [4] X, [5] the input (then λ).  Steps: T = As X and Rm = I - XᵀX;
+// S = Xᵀ T; λ, δ and E (into [2]) in one CTA per factor; X + X E (into [1]);
+// then the outputs of eig_output.
+// ---------------------------------------------------------------------------
+constexpr int RG_TILE = 16;
+
+// C = eye I + sign op(A) B + Add, on 16 x 16 output tiles; matrices are
+// indices into the factor's six (Add: -1 for none); op(A) = Aᵀ if transA.
+__global__ void __launch_bounds__(RG_TILE * RG_TILE) refine_gemm(double* __restrict__ work, int n, int iA, int iB,
+                                                                 int iC, int iAdd, int transA, int eye,
+                                                                 double sign) {
+    const size_t RR = (size_t)n * n;
+    double* base = work + (size_t)blockIdx.z * 6 * RR;
+    const double* A = base + iA * RR;
+    const double* B = base + iB * RR;
+    double* C = base + iC * RR;
+    const double* Add = iAdd >= 0 ? base + iAdd * RR : nullptr;
+    __shared__ double sA[RG_TILE][RG_TILE + 1], sB[RG_TILE][RG_TILE + 1];
+    const int ty = threadIdx.x / RG_TILE, tx = threadIdx.x % RG_TILE;
+    const int i = blockIdx.y * RG_TILE + ty, j = blockIdx.x * RG_TILE + tx;
+    double acc = 0.0;
+    for (int k0 = 0; k0 < n; k0 += RG_TILE) {
+        const int ia = blockIdx.y * RG_TILE + ty, ka = k0 + tx;   // op(A)[ia][ka]
+        sA[ty][tx] = (ia < n && ka < n) ? (transA ? A[(size_t)ka * n + ia] : A[(size_t)ia * n + ka]) : 0.0;
+        const int kb = k0 + ty;
+        sB[ty][tx] = (kb < n && j < n) ? B[(size_t)kb * n + j] : 0.0;
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < RG_TILE; ++kk) acc = fma(sA[ty][kk], sB[kk][tx], acc);
+        __syncthreads();
+    }
+    if (i < n && j < n)
+        C[(size_t)i * n + j] = (eye && i == j ? 1.0 : 0.0) + sign * acc + (Add ? Add[(size_t)i * n + j] : 0.0);
+}
+
+// λ_i = S_ii / (1 - Rm_ii), δ, and E into slot [2] (one CTA per factor).
+__global__ void __launch_bounds__(1024) refine_mid(double* __restrict__ work, int n) {
+    __shared__ double red[64];
+    __shared__ double lam[128];
+    const size_t RR = (size_t)n * n;
+    double* base = work + (size_t)blockIdx.x * 6 * RR;
+    const double *As = base, *S = base + RR, *Rm = base + 3 * RR;
+    double* E = base + 2 * RR;
+    double* lam_out = base + 5 * RR;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        lam[i] = S[(size_t)i * n + i] / (1.0 - Rm[(size_t)i * n + i]);
+        lam_out[i] = lam[i];
+    }
+    __syncthreads();
+    double off = 0.0, an = 0.0, rn = 0.0;
+    for (size_t e = threadIdx.x; e < RR; e += blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        const double sd = S[e] - (i == j ? lam[i] : 0.0);
+        off += sd * sd;
+        an += As[e] * As[e];
+        rn += Rm[e] * Rm[e];
+    }
+    off = block_sum(off, red);
+    an = block_sum(an, red);
+    rn = block_sum(rn, red);
+    const double delta = 2.0 * (sqrt(off) + sqrt(an) * sqrt(rn));
+    for (size_t e = threadIdx.x; e < RR; e += blockDim.x) {
+        const int i = (int)(e / n), j = (int)(e % n);
+        double v;
+        if (i == j)
+            v = 0.5 * Rm[e];
+        else if (fabs(lam[i] - lam[j]) > delta)
+            v = (S[e] + lam[j] * Rm[e]) / (lam[j] - lam[i]);
+        else
+            v = 0.5 * Rm[e];
+        E[e] = v;
+    }
+}
+
+// The refined X (slot [1]) and λ (slot [5]) times the scale, to the outputs.
+__global__ void __launch_bounds__(1024) refine_finish(const __grid_constant__ PrepParams P, double* __restrict__ work,
+                                                      int n, const double* __restrict__ scales,
+                                                      double* __restrict__ lam64, double* __restrict__ V64,
+                                                      float* __restrict__ V32, float* __restrict__ V32lo) {
+    __shared__ double lam[128];
+    __shared__ int pos[128];
+    const size_t RR = (size_t)n * n;
+    const int p = blockIdx.x;
+    const double* base = work + (size_t)p * 6 * RR;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = base[5 * RR + i] * scales[p];
+    __syncthreads();
+    eig_output(P.incl[p], n, base + RR, lam, pos, lam64, V64, V32, V32lo);
 }
 
 // ---------------------------------------------------------------------------
@@ -443,8 +562,9 @@ __global__ void __launch_bounds__(1024) prep_eig(const __grid_constant__ PrepPar
                                                 const double* __restrict__ Gplus64, double* __restrict__ lam64,
                                                 double* __restrict__ V64, float* __restrict__ V32,
                                                 float* __restrict__ V32lo, float* __restrict__ etree,
-                                                double* __restrict__ gwork) {
-    prep_eig_body(P, N, R, Rp, dE, Tp, G64, Gplus64, lam64, V64, V32, V32lo, etree, gwork, blockIdx.x);
+                                                double* __restrict__ gwork, int split, double* __restrict__ scales) {
+    prep_eig_body(P, N, R, Rp, dE, Tp, G64, Gplus64, lam64, V64, V32, V32lo, etree, gwork, blockIdx.x, split != 0,
+                  scales);
 }
 
 // grid (entry blocks, included factors)
@@ -542,11 +662,28 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j) {
                                          s->status, in_smem ? nullptr : s->work64); count_launch();
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_pinv launch");
+    // R > 32 with the FP64 work in global memory: the refinement step over many CTAs
+    const bool split = R > 32 && !in_smem;
+    double* scales = s->work64 + (size_t)6 * R * R * (N + 1);   // the area's 256-double tail
     prep_eig<<<P.n_incl, nt, smem, s->stream>>>(P, N, R, s->Rp, s->dE, s->Tp, s->G64, s->Gplus64, s->lam64, s->V64,
-                                               s->V32, s->V32lo, s->etree,
-                                               in_smem ? nullptr : s->work64); count_launch();
+                                               s->V32, s->V32lo, s->etree, in_smem ? nullptr : s->work64,
+                                               split ? 1 : 0, scales); count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "prep_eig launch");
+    if (split) {
+        const int nt16 = (R + RG_TILE - 1) / RG_TILE;
+        const dim3 g(nt16, nt16, P.n_incl);
+        double* w = s->work64;
+        refine_gemm<<<g, RG_TILE * RG_TILE, 0, s->stream>>>(w, R, 0, 4, 2, -1, 0, 0, 1.0);    // T = As X
+        refine_gemm<<<g, RG_TILE * RG_TILE, 0, s->stream>>>(w, R, 4, 4, 3, -1, 1, 1, -1.0);   // Rm = I - XᵀX
+        refine_gemm<<<g, RG_TILE * RG_TILE, 0, s->stream>>>(w, R, 4, 2, 1, -1, 1, 0, 1.0);    // S = Xᵀ T
+        refine_mid<<<P.n_incl, 1024, 0, s->stream>>>(w, R);                                    // λ, δ, E
+        refine_gemm<<<g, RG_TILE * RG_TILE, 0, s->stream>>>(w, R, 4, 2, 1, 4, 0, 0, 1.0);     // X + X E
+        refine_finish<<<P.n_incl, 1024, 0, s->stream>>>(P, w, R, scales, s->lam64, s->V64, s->V32, s->V32lo);
+        for (int q = 0; q < 6; ++q) count_launch();
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_check(s, e, "prep refinement launch");
+    }
     prep_etree<<<dim3((s->Tp + ETREE_THREADS - 1) / ETREE_THREADS, P.n_incl), ETREE_THREADS, 0, s->stream>>>(
         P, R, s->Rp, s->Tp, s->G64, s->lam64, s->V64, s->etree);
     count_launch();
