@@ -459,8 +459,11 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
     }
 }
 
+// Four CTAs (32 samples) per SM where the registers allow it without spills
+// (RMAX <= 16: 63 registers); at RMAX = 32 a 64-register cap spills and the
+// draw slows from 1.24 to 1.34 ms, so three.
 template <int RMAX>
-__global__ void __launch_bounds__(256, 3) krp_descent_fast(const __grid_constant__ FastParams P) {
+__global__ void __launch_bounds__(256, RMAX <= 16 ? 4 : 3) krp_descent_fast(const __grid_constant__ FastParams P) {
     descent_fast_body<RMAX>(P, blockIdx.x, gridDim.x);
 }
 
