@@ -27,7 +27,8 @@ struct krp_sampler {
     double* Gplus64 = nullptr;  // R x R
     double* lam64 = nullptr;    // N x R      eigenvalues of G_{>k} (ascending)
     double* V64 = nullptr;      // N x R x R  eigenvectors (column u)
-    double* work64 = nullptr;   // prep scratch: N x (2 R x R) FP64
+    double* work64 = nullptr;   // prep scratch: (N + 1) x 6 R x R FP64 (per included factor six
+                                // R x R matrices of the eigen-refinement), then 256 doubles (scales)
     float* Gplus32 = nullptr;   // Tp packed upper triangle of G⁺
     float* etree = nullptr;     // N x Rp x Tp : eigencomponent trees E_k
     float* V32 = nullptr;       // N x R x R : row u = eigenvector u of G_{>k}

@@ -41,7 +41,8 @@ struct LookupParams {
     const float* SA;     // J x R
     int64_t J;
     int R;
-    float* Y;            // I_j x R
+    float* Y;            // I_j x RS, RS = R rounded up to 4 (columns >= R unused)
+    int RS;
 };
 
 __global__ void __launch_bounds__(256) fiber_find(LookupParams P, int64_t* __restrict__ fiber) {
@@ -129,7 +130,10 @@ __global__ void __launch_bounds__(1024) scan_lengths(const int64_t* __restrict__
     if (threadIdx.x == blockDim.x - 1) scan[n] = part[threadIdx.x];
 }
 
-// Warps take runs of SCATTER_RUN consecutive (slot, nonzero) pairs.
+// Warps take runs of SCATTER_RUN consecutive (slot, nonzero) pairs; lane l
+// adds columns 4l .. 4l+3 of a nonzero's row with one vector atomic (Y rows
+// are RS = R rounded up to 4 floats, 16-byte aligned; the padding columns
+// receive zeros).
 constexpr int SCATTER_RUN = 32;
 
 __global__ void __launch_bounds__(256) fiber_scatter(LookupParams P, const int64_t* __restrict__ begin,
@@ -155,7 +159,15 @@ __global__ void __launch_bounds__(256) fiber_scatter(LookupParams P, const int64
             const int64_t n = __ldg(begin + h) + (w - __ldg(scan + h));
             const int64_t ij = __ldg(P.fidx + n);
             const float v = __ldg(P.fval + n);
-            for (int a = lane; a < P.R; a += 32) atomicAdd(P.Y + ij * P.R + a, v * __ldg(acc + h * P.R + a));
+            const float* ah = acc + h * P.R;
+            for (int a = 4 * lane; a < P.R; a += 128) {
+                float4 d;
+                d.x = v * __ldg(ah + a);
+                d.y = a + 1 < P.R ? v * __ldg(ah + a + 1) : 0.f;
+                d.z = a + 2 < P.R ? v * __ldg(ah + a + 2) : 0.f;
+                d.w = a + 3 < P.R ? v * __ldg(ah + a + 3) : 0.f;
+                atomicAdd(reinterpret_cast<float4*>(P.Y + ij * P.RS + a), d);
+            }
         }
     }
 }
@@ -179,7 +191,7 @@ struct MinvCfg {
 };
 
 template <int RP>
-__global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __restrict__ Y,
+__global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __restrict__ Y, int RSY,
                                                               const double* __restrict__ Minv, int64_t I, int R,
                                                               float* __restrict__ U, double* __restrict__ sumsq) {
     using C = MinvCfg<RP>;
@@ -200,9 +212,9 @@ __global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __res
         const int64_t r0 = tile * TM;
         const int nr = (int)min((int64_t)TM, I - r0);
         __syncthreads();   // the previous tile's reads of sY (and the writes of sM) are done
-        const float* src = Y + r0 * R;
+        const float* src = Y + r0 * RSY;
         for (int r = warp; r < nr; r += MINV_THREADS / 32)
-            for (int k = lane; k < R; k += 32) sY[r * RS + k] = src[(int64_t)r * R + k];
+            for (int k = lane; k < R; k += 32) sY[r * RS + k] = src[(int64_t)r * RSY + k];
         __syncthreads();
         float2 acc[RT][4];
 #pragma unroll
@@ -264,7 +276,7 @@ __global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __res
 }
 
 template <int RP>
-cudaError_t launch_minv_t(const float* Y, const double* Minv, int64_t I, int R, float* U, double* sumsq,
+cudaError_t launch_minv_t(const float* Y, int RSY, const double* Minv, int64_t I, int R, float* U, double* sumsq,
                           int num_sms, cudaStream_t st) {
     using C = MinvCfg<RP>;
     const size_t sm = C::smem(R);
@@ -272,16 +284,17 @@ cudaError_t launch_minv_t(const float* Y, const double* Minv, int64_t I, int R, 
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (I + C::TM - 1) / C::TM;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms * 2);
-    apply_minv<RP><<<(unsigned)grid, MINV_THREADS, sm, st>>>(Y, Minv, I, R, U, sumsq);
+    apply_minv<RP><<<(unsigned)grid, MINV_THREADS, sm, st>>>(Y, RSY, Minv, I, R, U, sumsq);
     count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_apply_minv(const float* Y, const double* Minv, int64_t I, int R, float* U, double* sumsq,
-                              int num_sms, cudaStream_t st) {
-    if (R <= 32) return launch_minv_t<32>(Y, Minv, I, R, U, sumsq, num_sms, st);
-    if (R <= 64) return launch_minv_t<64>(Y, Minv, I, R, U, sumsq, num_sms, st);
-    return launch_minv_t<128>(Y, Minv, I, R, U, sumsq, num_sms, st);
+// Y: I x RSY (row stride RSY >= R)
+cudaError_t launch_apply_minv(const float* Y, int RSY, const double* Minv, int64_t I, int R, float* U,
+                              double* sumsq, int num_sms, cudaStream_t st) {
+    if (R <= 32) return launch_minv_t<32>(Y, RSY, Minv, I, R, U, sumsq, num_sms, st);
+    if (R <= 64) return launch_minv_t<64>(Y, RSY, Minv, I, R, U, sumsq, num_sms, st);
+    return launch_minv_t<128>(Y, RSY, Minv, I, R, U, sumsq, num_sms, st);
 }
 
 // U[:, c] /= σ_c (a zero column stays zero), σ_c = sqrt(σ²_c) to sigma;
@@ -487,7 +500,8 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     for (int k = 0; k < s->N; ++k)
         if (t->I[k] != s->I[k]) return fail(s, KRP_EINVAL, "krp_solve_sparse: tensor dims differ from the factors");
     const int R = s->R;
-    const size_t ny = (size_t)s->I[j] * R;
+    const int RS = (R + 3) & ~3;   // Y's row stride: rows 16-byte aligned for the vector atomics
+    const size_t ny = (size_t)s->I[j] * RS;
     if (ny > t->Y_floats) {
         cudaFree(t->Y);
         t->Y = nullptr;
@@ -515,6 +529,7 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     P.J = J;
     P.R = R;
     P.Y = t->Y;
+    P.RS = RS;
     int log2H = 1;
     while (((int64_t)1 << log2H) < 2 * J) ++log2H;
     const int64_t H = (int64_t)1 << log2H;
@@ -552,7 +567,7 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     krp_status st = normal_inverse(s, J, SA, flags);
     if (st != KRP_OK) return st;
     const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
-    e = launch_apply_minv(t->Y, Minv, s->I[j], R, U_out, sumsq, s->num_sms, s->stream);
+    e = launch_apply_minv(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->num_sms, s->stream);
     if (e != cudaSuccess) return cuda_check(s, e, "apply_minv launch");
     return KRP_OK;
 }
