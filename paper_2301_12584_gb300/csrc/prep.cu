@@ -290,6 +290,27 @@ __device__ __forceinline__ void prep_pinv_body(const PrepParams& P, int N, int e
         for (int e = threadIdx.x; e < RR; e += blockDim.x) Gplus64[e] = Gi[e];
     } else {
         eig_fp32_refined(G, R, X, lam, w);
+        // The refinement's eigenvalues are first-order estimates from the
+        // unrefined vectors: a cluster of zero eigenvalues comes out near
+        // 1e-14 lambda_max, above the cutoff R 2^-52 lambda_max, and would be
+        // inverted.  Rayleigh quotients of the refined vectors are accurate to
+        // ~eps^2 there.  (T = G X into w.T, free after the refinement.)
+        for (int e = threadIdx.x; e < RR; e += blockDim.x) {
+            const int i = e / R, j = e % R;
+            double acc = 0.0;
+            for (int k = 0; k < R; ++k) acc = fma(G[i * R + k], X[k * R + j], acc);
+            w.T[e] = acc;
+        }
+        __syncthreads();
+        for (int u = threadIdx.x; u < R; u += blockDim.x) {
+            double num = 0.0, den = 0.0;
+            for (int i = 0; i < R; ++i) {
+                num = fma(X[i * R + u], w.T[i * R + u], num);
+                den = fma(X[i * R + u], X[i * R + u], den);
+            }
+            lam[u] = den > 0.0 ? num / den : 0.0;
+        }
+        __syncthreads();
         double lmax = 0.0;
         for (int i = 0; i < R; ++i) lmax = fmax(lmax, lam[i]);
         const double cut = R * 2.220446049250313e-16 * lmax;

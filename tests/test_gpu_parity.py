@@ -304,6 +304,49 @@ def test_branch_probabilities_r64(form):
     s.close()
 
 
+@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("dims,R,F,J,excl", [([30], 40, 40, 7, -1),              # one factor, one partial leaf, rank 30
+                                             ([20], 24, 24, 9, -1),              # R <= 32 path, rank 20
+                                             ([100, 61], 72, 24, 33, -1),         # F != R, ragged leaves
+                                             ([130, 140, 150], 120, 120, 1, 1)])  # J = 1, an excluded factor
+def test_large_r_edge_cases(form, dims, R, F, J, excl):
+    """Degenerate shapes of the R > 32 descents (team: form 1, node-major:
+    form 2) against the oracle, replaying the GPU's eigendecompositions."""
+    Us = synth.gaussian_factors(len(dims), dims, R, seed=sum(dims) + R)
+    s = sampler_for(Us, F)
+    s.set_descent_form(form)
+    out = draw(s, Us, excl, J, seed=77, draw_id=5, logq=True)
+    U64 = [U.astype(np.float64) for U in Us]
+    prep = O.SamplerPrep(U64, excl)
+    eig = {}
+    for k in prep.incl:
+        lam, V, _, _ = s.get_prep(k)
+        rec = (V * np.maximum(lam, 0.0)) @ V.T
+        assert np.abs(rec - prep.Ggt[k]).max() <= 1e-6 * np.abs(prep.Ggt[k]).max()
+        eig[k] = (lam, V)
+    ref = O.krp_sample(U64, excl, J, 77, 5, record=True, eig_override=eig)
+    mism = check_index_parity(out["idx"], ref, J)
+    assert mism <= max(1, J // 100), mism
+    same = ~(out["idx"] != ref["idx"]).any(axis=0)
+    np.testing.assert_allclose(out["weight"][same], ref["weight"][same], rtol=1e-4)
+    s.close()
+
+
+@pytest.mark.parametrize("I,R", [(30, 40), (20, 24)])
+def test_pinv_of_a_cluster_of_zero_eigenvalues(I, R):
+    """A = U_1 with fewer rows than columns: G has R - I zero eigenvalues.
+    The GPU's eigenvalues must resolve that cluster below the cutoff
+    R 2^-52 lambda_max (reading C7), giving the oracle's rank and G⁺."""
+    Us = synth.gaussian_factors(1, [I], R, seed=I + R)
+    s = sampler_for(Us, R)
+    draw(s, Us, -1, 16, seed=1, draw_id=0)
+    prep = O.SamplerPrep([Us[0].astype(np.float64)], -1)
+    lam, V, Gp, rank = s.get_prep(0)
+    assert rank == prep.rank == I
+    np.testing.assert_allclose(Gp, prep.Gplus, rtol=0, atol=1e-8 * np.abs(prep.Gplus).max())
+    s.close()
+
+
 def test_node_major_and_team_draws_agree():
     """The two descent forms differ only in the rounding of the masses: the
     same draws but for rare near-edge flips, and the same weights."""
