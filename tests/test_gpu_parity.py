@@ -307,6 +307,9 @@ def test_branch_probabilities_r64(form):
 @pytest.mark.parametrize("form", [1, 2])
 @pytest.mark.parametrize("dims,R,F,J,excl", [([30], 40, 40, 7, -1),              # one factor, one partial leaf, rank 30
                                              ([20], 24, 24, 9, -1),              # R <= 32 path, rank 20
+                                             ([50, 40], 8, 4, 1, 0),              # one included factor, J = 1
+                                             ([1, 64, 5], 6, 2, 300, -1),         # a one-row factor (depth 0)
+                                             ([1, 200, 70], 48, 48, 100, -1),     # the same at R > 32
                                              ([100, 61], 72, 24, 33, -1),         # F != R, ragged leaves
                                              ([130, 140, 150], 120, 120, 1, 1)])  # J = 1, an excluded factor
 def test_large_r_edge_cases(form, dims, R, F, J, excl):
