@@ -22,10 +22,12 @@ __device__ void jacobi_eig(Scalar* A, Scalar* V, int n, Scalar* cs, int* pr, dou
                            int max_sweeps, double tol) {
     const int m = n + (n & 1);  // players, a dummy when n is odd
     const int npair = m / 2;
-    // this thread's first (pair, column) item of the flattened npair x n
-    // rotation loops and the stride between its items, without dividing
-    const int k0 = threadIdx.x / n, c0 = threadIdx.x % n;
-    const int dk = blockDim.x / n, dc = blockDim.x % n;
+    // rotation loops: CH threads per pair, thread (kk, c0) applies pair kk to
+    // columns (rows) c0, c0 + CH, ...: the pair's indices and rotation are read
+    // once per step, and consecutive threads touch consecutive entries
+    const int CH = max(1, (int)blockDim.x / npair);
+    const int kk = threadIdx.x / CH, c0 = threadIdx.x % CH;
+    const bool has_pair = kk < npair;
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) V[e] = (e / n == e % n) ? Scalar(1) : Scalar(0);
     __syncthreads();
     double off_prev = INFINITY;
@@ -80,29 +82,27 @@ __device__ void jacobi_eig(Scalar* A, Scalar* V, int n, Scalar* cs, int* pr, dou
                 cs[2 * k + 1] = sn;
             }
             __syncthreads();
+            int p = -1, q = 0;
+            Scalar c = 1, sn = 0;
+            if (has_pair) {
+                p = pr[2 * kk];
+                q = pr[2 * kk + 1];
+                c = cs[2 * kk];
+                sn = cs[2 * kk + 1];
+            }
+            const bool act = p >= 0 && sn != Scalar(0);
             // rows: A <- Jᵀ A
-            for (int k = k0, col = c0; k < npair;) {
-                const int p = pr[2 * k], q = pr[2 * k + 1];
-                if (p >= 0 && cs[2 * k + 1] != Scalar(0)) {
-                    const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
+            if (act)
+                for (int col = c0; col < n; col += CH) {
                     const Scalar ap = A[p * n + col], aq = A[q * n + col];
                     A[p * n + col] = c * ap - sn * aq;
                     A[q * n + col] = sn * ap + c * aq;
                 }
-                col += dc;
-                k += dk;
-                if (col >= n) {
-                    col -= n;
-                    ++k;
-                }
-            }
             __syncthreads();
             // columns: A <- A J, V <- V J; the rotated pair's off-diagonal
             // entries (rows p and q) are set to their exact value, zero
-            for (int k = k0, row = c0; k < npair;) {
-                const int p = pr[2 * k], q = pr[2 * k + 1];
-                if (p >= 0 && cs[2 * k + 1] != Scalar(0)) {
-                    const Scalar c = cs[2 * k], sn = cs[2 * k + 1];
+            if (act)
+                for (int row = c0; row < n; row += CH) {
                     const Scalar ap = A[row * n + p], aq = A[row * n + q];
                     A[row * n + p] = row == q ? Scalar(0) : c * ap - sn * aq;
                     A[row * n + q] = row == p ? Scalar(0) : sn * ap + c * aq;
@@ -110,13 +110,6 @@ __device__ void jacobi_eig(Scalar* A, Scalar* V, int n, Scalar* cs, int* pr, dou
                     V[row * n + p] = c * vp - sn * vq;
                     V[row * n + q] = sn * vp + c * vq;
                 }
-                row += dc;
-                k += dk;
-                if (row >= n) {
-                    row -= n;
-                    ++k;
-                }
-            }
             __syncthreads();
         }
     }
