@@ -172,6 +172,22 @@ __global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restri
     tree_leaves_fp32_body<LB, VEC>(U, I, R, F, L, G, Tp, tree, top, copy_to, blockIdx.x);
 }
 
+// Entry e of node `node` of an input level as a double-float pair: the leaf
+// kernel's (hi, lo) FP32 pairs as they are, FP64 values split exactly enough
+// (hi = FP32 rounding, lo = FP32 rounding of the rest).
+__device__ __forceinline__ void load_up(bool from_pairs, const float* __restrict__ in_pairs,
+                                        const double* __restrict__ in64, int64_t node, int Tp, int e, float& hi,
+                                        float& lo) {
+    if (from_pairs) {
+        hi = in_pairs[(node * 2) * Tp + e];
+        lo = in_pairs[(node * 2 + 1) * Tp + e];
+    } else {
+        const double x = in64[node * Tp + e];
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    }
+}
+
 // Index of the entry of an ascending prefix array whose range holds x.
 __device__ __forceinline__ int prefix_find(const int64_t* __restrict__ pre, int n, int64_t x) {
     int lo = 0, hi = n - 1;  // pre[0] = 0 <= x < pre[n]
@@ -206,13 +222,12 @@ __global__ void tree_up_batch(const UpDesc* __restrict__ ups, const int64_t* __r
     const int lbb = u.lbb, Tp = u.Tp;
     const int64_t first = cta * lbb;
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
-        double v[16];
+        float vh[16], vl[16];
 #pragma unroll
-        for (int l = 0; l < 16; ++l)
-            v[l] = l >= lbb ? 0.0
-                            : (FROM_PAIRS ? (double)u.in_pairs[((first + l) * 2) * Tp + e] +
-                                                (double)u.in_pairs[((first + l) * 2 + 1) * Tp + e]
-                                          : u.in64[(first + l) * Tp + e]);
+        for (int l = 0; l < 16; ++l) {
+            vh[l] = vl[l] = 0.f;
+            if (l < lbb) load_up(FROM_PAIRS, u.in_pairs, u.in64, first + l, Tp, e, vh[l], vl[l]);
+        }
         int64_t h = u.n_in + first;
 #pragma unroll
         for (int n = 16; n > 1; n >>= 1) {
@@ -220,40 +235,40 @@ __global__ void tree_up_batch(const UpDesc* __restrict__ ups, const int64_t* __r
             h >>= 1;
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
-                v[l] = v[2 * l] + v[2 * l + 1];
-                store_node(u.tree, h + l, Tp, e, (float)v[l]);
+                df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
+                store_node(u.tree, h + l, Tp, e, vh[l]);
             }
         }
-        u.out[(size_t)cta * Tp + e] = v[0];
+        u.out[(size_t)cta * Tp + e] = (double)vh[0] + (double)vl[0];
     }
 }
 
-// Levels above the leaf kernel, summed in FP64: LBB nodes per CTA from `in`
-// (a full tree level with n_in nodes, heap ids n_in..2 n_in - 1; either the
-// leaf kernel's (hi, lo) FP32 pairs or FP64 values) to one FP64 node per CTA
-// in `out`.  Stores the FP32 rounding of every left child created.
+// Levels above the leaf kernel: LBB nodes per CTA from `in` (a full tree
+// level with n_in nodes, heap ids n_in..2 n_in - 1; either the leaf kernel's
+// (hi, lo) FP32 pairs or FP64 values) to one node per CTA in `out`, as the
+// exact FP64 value of a double-float sum (the leaf kernel's in-CTA sums are
+// double-float too, ~2^-44 relative; GB300 runs FP64 at ~1/64 of FP32, which
+// made FP64 adds the bound of the first of these levels at large R).  Stores
+// the FP32-rounded sum of every left child created.
 template <int LBB, bool FROM_PAIRS>
 __global__ void tree_up(const float* __restrict__ in_pairs, const double* __restrict__ in64, int64_t n_in, int Tp,
                         float* __restrict__ tree, double* __restrict__ out) {
     const int64_t first = (int64_t)blockIdx.x * LBB;
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
-        double v[LBB];
+        float vh[LBB], vl[LBB];
 #pragma unroll
-        for (int l = 0; l < LBB; ++l)
-            v[l] = FROM_PAIRS ? (double)in_pairs[((first + l) * 2) * Tp + e] +
-                                    (double)in_pairs[((first + l) * 2 + 1) * Tp + e]
-                              : in64[(first + l) * Tp + e];
+        for (int l = 0; l < LBB; ++l) load_up(FROM_PAIRS, in_pairs, in64, first + l, Tp, e, vh[l], vl[l]);
         int64_t h = n_in + first;
 #pragma unroll
         for (int n = LBB; n > 1; n >>= 1) {
             h >>= 1;
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
-                v[l] = v[2 * l] + v[2 * l + 1];
-                store_node(tree, h + l, Tp, e, (float)v[l]);
+                df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
+                store_node(tree, h + l, Tp, e, vh[l]);
             }
         }
-        out[(size_t)blockIdx.x * Tp + e] = v[0];
+        out[(size_t)blockIdx.x * Tp + e] = (double)vh[0] + (double)vl[0];
     }
 }
 
