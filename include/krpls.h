@@ -155,6 +155,14 @@ krp_status krp_sample_prepare(krp_sampler* s, int exclude_j);
 #define KRP_DESCENT_TEAM 1
 #define KRP_DESCENT_NODE_MAJOR 2
 krp_status krp_set_descent_form(krp_sampler* s, int form);
+
+/* Measurement helper (no counterpart in the paper): throughput of the current
+ * device on fixed, bounded probes, timed with CUDA events on `stream` (may be
+ * NULL): out_host[0] FP32 TFLOP/s with scalar FMA, [1] FP32 TFLOP/s with
+ * paired (f32x2) FMA, [2] FP64 TFLOP/s, [3] L2 read GB/s (64 MB buffer).
+ * Allocates and frees 64 MB of device memory; synchronous.  These are the
+ * denominators of the SIMT, FP64 and L2-bound rooflines. */
+krp_status krp_probe_peaks(double* out_host, void* stream);
 krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
                            int32_t* idx, float* weight, float* logq, float* SA);
 

@@ -35,6 +35,7 @@ SIGNATURES = [
     ("krp_sample", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_sample_prepare", _INT, [_P, _INT]),
     ("krp_set_descent_form", _INT, [_P, _INT]),
+    ("krp_probe_peaks", _INT, [_P, _P]),
     ("krp_sample_draw", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_launch_count", _I64, []),
     ("krp_debug_wait_timeout", _INT, [_P, _INT]),
@@ -267,6 +268,15 @@ class Sampler:
         self._check(self._lib.krp_get_prep(self.h, int(k), lam.ctypes.data_as(_P), V.ctypes.data_as(_P),
                                            Gp.ctypes.data_as(_P), C.byref(rank)))
         return lam, V, Gp, rank.value
+
+
+def probe_peaks(stream=None):
+    """FP32 (scalar, paired), FP64 TFLOP/s and L2 read GB/s of the current device."""
+    out = (C.c_double * 4)()
+    code = lib().krp_probe_peaks(C.cast(out, _P), _P(_stream_ptr(stream)))
+    if code != KRP_OK:
+        raise KrpError(code, "krp_probe_peaks failed")
+    return {"fp32_tflops": out[0], "fp32x2_tflops": out[1], "fp64_tflops": out[2], "l2_read_gbs": out[3]}
 
 
 def launch_count():

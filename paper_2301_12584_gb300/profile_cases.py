@@ -11,6 +11,7 @@
   python -m paper_2301_12584_gb300.profile_cases build100_tc # tree_leaves_tc_pipe<128,.> (BF16x3), same factor
   python -m paper_2301_12584_gb300.profile_cases prep100    # prep_pinv / prep_eig / prep_etree, R=100, N=3
   python -m paper_2301_12584_gb300.profile_cases minv100    # apply_minv<128>: U_0 = Y M⁻¹, 2^21 x 100
+  python -m paper_2301_12584_gb300.profile_cases peaks      # FP32 / FP64 FMA and L2 read throughput probes
 
 Each case runs its kernel a few times (the first launches warm up), checks the
 device status and exits 0.  Inputs are the seeded generators of synth.py.
@@ -118,10 +119,16 @@ def prep():
     assert s.sync_status() == 0, s.last_error()
 
 
+def peaks():
+    import json
+    from .krpls import probe_peaks
+    print(json.dumps(probe_peaks()))
+
+
 if __name__ == "__main__":
     {"descent": descent, "descent64": descent64, "descent100": descent100,
      "descent100_nm": lambda: descent100(2), "build": build, "build_tc": build_tc,
      "build100": lambda: build(0, 1 << 20, 100), "build100_tc": lambda: build(1, 1 << 20, 100),
-     "prep": prep, "prep100": prep100, "minv100": minv100}[sys.argv[1]]()
+     "prep": prep, "prep100": prep100, "minv100": minv100, "peaks": peaks}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")

@@ -203,3 +203,13 @@ def test_batch_rejects_unsupported_samplers():
     assert e.value.code == -8
     s.close()
     t.close()
+
+
+def test_throughput_probes_are_plausible():
+    """krp_probe_peaks: the SIMT FP32, FP64 and L2 rooflines' denominators
+    (positive, finite, FP64 well below FP32, L2 above the HBM copy rate)."""
+    from paper_2301_12584_gb300.krpls import probe_peaks
+    p = probe_peaks()
+    assert all(np.isfinite(v) and v > 0 for v in p.values()), p
+    assert p["fp64_tflops"] < p["fp32_tflops"], p
+    assert p["l2_read_gbs"] > 1000.0, p
