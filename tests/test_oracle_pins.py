@@ -517,3 +517,22 @@ def test_distortion_and_kronecker_residual():
     res, G, Atb = O.kron_lstsq_residual(Us, -1, cs, x)
     np.testing.assert_allclose(Atb, A.T @ b, rtol=1e-12)
     assert abs(res - np.linalg.norm(A @ x - b)) <= 1e-10 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("excl", [-1, 1])
+def test_sample_probability_is_leverage_over_rank(excl):
+    """sample_probability(q_s = ℓ_s / rank, Sec. 2.1) against the textbook
+    QR leverage scores of the materialised A (Thm 1.1): every tuple's q equals
+    the row's leverage over rank(A), and q sums to 1 over all tuples; also with
+    a factor excluded (A over the included factors) and rank-deficient."""
+    rng = np.random.default_rng(17)
+    Us = [rng.standard_normal((n, 3)) for n in (3, 4, 2)]
+    Us[2][:, 2] = Us[2][:, 0]                           # factor 2's Gram has rank 2
+    incl = [k for k in range(3) if k != excl]
+    A = O.khatri_rao([Us[k] for k in incl])
+    lev, r = O.leverage_scores_qr(A)
+    tuples = np.array(list(itertools.product(*[range(Us[k].shape[0]) for k in incl]))).T   # C order
+    q, rank = O.sample_probability(Us, excl, tuples)
+    assert rank == r
+    np.testing.assert_allclose(q, lev / r, rtol=1e-10, atol=1e-14)
+    assert abs(q.sum() - 1.0) < 1e-12
