@@ -60,5 +60,15 @@ def test_host_argument_checks_without_gpu(built_lib):
     assert L.krp_create(C.byref(h), 3, I, 8, 100, 0, None) == krpls.KRP_EINVAL    # F > 4R
     assert L.krp_create(C.byref(h), 3, I, 8, 0, 7, None) == krpls.KRP_EINVAL      # precision
     assert L.krp_create(None, 3, I, 8, 0, 0, None) == krpls.KRP_EINVAL
+    assert L.krp_create(C.byref(h), 17, (C.c_int64 * 17)(*([8] * 17)), 8, 0, 0, None) == krpls.KRP_EINVAL  # N > 16
+    assert L.krp_create(C.byref(h), 3, (C.c_int64 * 3)(64, 0, 64), 8, 0, 0, None) == krpls.KRP_EINVAL    # I_k = 0
+    assert L.krp_create(C.byref(h), 3, (C.c_int64 * 3)(64, 1 << 31, 64), 8, 0, 0, None) == krpls.KRP_EINVAL
+    assert L.krp_create(C.byref(h), 3, None, 8, 0, 0, None) == krpls.KRP_EINVAL                          # I_host
+    assert L.krp_create(C.byref(h), 3, I, 8, -1, 0, None) == krpls.KRP_EINVAL                            # F < 0
     assert h.value is None
+    # other entry points reject a NULL handle or output before any device work
+    assert L.krp_set_descent_form(None, 0) == krpls.KRP_EINVAL
+    assert L.krp_sample(None, -1, 16, 1, 0, None, None, None, None) != krpls.KRP_OK
+    assert L.krp_get_factor(None, 0, None, 0) == krpls.KRP_EINVAL
+    assert L.krp_probe_peaks(None, None) == krpls.KRP_EINVAL
     assert b"R" in L.krp_last_error(None) or L.krp_last_error(None)
