@@ -10,7 +10,7 @@ and every step streams a 512 MiB factor and its 277 MB tree, so no L2 flush is
 needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--precision fp32|bf16x3] [--no-cpu-baseline]
+                  [--precision fp32|bf16x3|exact] [--no-cpu-baseline]
                   [--workload sampler|batch512|rank_sweep|sparse_als|accuracy] [--rank R]
                   [--ranks 25,50,100] [--nnz N] [--sweeps S] [--trials T]
 
@@ -54,8 +54,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "exact"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="sampler: skip the other precision forms")
+    ap.add_argument("--sts-sweeps", type=int, default=12,
+                    help="sampler: STS-CP sweeps per precision at R=25 for the metric's second half (0 skips)")
     ap.add_argument("--e2e-steps", type=int, default=20)
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "batch512", "rank_sweep", "sparse_als", "accuracy"],
@@ -123,20 +126,29 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------ CPU oracle ----
-def oracle_samples_per_s(Us64, n_samples=240):
-    """The FP64 oracle as it stands on a bounded sample of one step: its
-    preparation (Grams, G⁺, eigendecompositions) plus n_samples draws, scaled
-    to a full draw of J samples.  Returns (samples/s, seconds, sample text)."""
+def oracle_tree_steps(Us64, fresh64, n_steps, n_samples, d_first=0):
+    """The FP64 oracle as it stands, stepping like the GPU workload: per step
+    the one-factor update (factor d mod 3 replaced by its fresh rows, FP64
+    segment tree rebuilt: Alg. 3), the per-draw preparation (Grams, G⁺,
+    eigendecompositions) and n_samples draws of Alg. 2/4 on the FP64 trees
+    (krp_sample_tree: samples d0 .. d0 + n_samples - 1 of the step's draw).
+    The trees of the factors not updated are built once, untimed.  Returns
+    (total samples, total seconds, per-step seconds)."""
     from oracle import krp_oracle as O
-    t0 = time.perf_counter()
-    prep = O.SamplerPrep(Us64, -1)
-    t1 = time.perf_counter()
-    O.krp_sample(Us64, -1, n_samples, 1, 0, prep=prep)
-    t2 = time.perf_counter()
-    per_sample = (t2 - t1) / n_samples
-    step_s = (t1 - t0) + J_DRAW * per_sample
-    return J_DRAW / step_s, t2 - t0, (f"oracle prepare + {n_samples} samples of one draw (N=3, I=2^22, R=32), "
-                                      f"extrapolated to J=2^16")
+    cur = list(Us64)
+    trees = {k: O.TreeFP64(cur[k], LEAF) for k in range(N_FACT)}
+    total, steps = 0, []
+    for d in range(d_first, d_first + n_steps):
+        k = d % N_FACT
+        t0 = time.perf_counter()
+        cur[k] = fresh64[k]
+        trees[k] = O.TreeFP64(cur[k], LEAF)
+        prep = O.SamplerPrep(cur, -1)
+        d0 = (d * n_samples) % J_DRAW
+        O.krp_sample_tree(cur, -1, n_samples, 1, d, F=LEAF, d0=d0, prep=prep, trees=trees)
+        steps.append(time.perf_counter() - t0)
+        total += n_samples
+    return total, sum(steps), steps
 
 
 def cores_used():
@@ -148,35 +160,30 @@ def cores_used():
     return n
 
 
+REF_SAMPLES_PER_STEP = 2048
+
+
 def run_reference(args, rank):
-    """Reference arm: the CPU oracle, timed on this machine's host cores.  Its
-    preparation (Grams, G⁺, eigendecompositions) is timed once; each step then
-    times a bounded sample of 4 draws, and the step's samples/s extrapolates to
-    one full draw: J / (t_prepare + J * t_per_sample)."""
+    """Reference arm: the CPU oracle timed on this machine's host cores, every
+    step the GPU workload's step with a bounded draw: a one-factor update
+    (FP64 tree rebuild), the preparation, and 2048 samples of the draw drawn
+    by Alg. 2/4 on the FP64 segment trees.  value = samples drawn / time."""
     if rank != 0:
         return
-    from oracle import krp_oracle as O
     from paper_2301_12584_gb300 import synth
     Us = synth.skewed_row_factors(N_FACT, I_ROWS, RANK, seed=0)
     Us64 = [U.astype(np.float64) for U in Us]
-    t0 = time.perf_counter()
-    prep = O.SamplerPrep(Us64, -1)
-    t_prep = time.perf_counter() - t0
-    n = 4
-    vals = []
-    for it in range(args.warmup + args.steps):
-        t1 = time.perf_counter()
-        O.krp_sample(Us64, -1, n, 1, it, prep=prep)
-        per = (time.perf_counter() - t1) / n
-        if it >= args.warmup:
-            vals.append(J_DRAW / (t_prep + J_DRAW * per))
-    v = statistics.median(vals)
-    ms = 1e3 * J_DRAW / v
-    sample = (f"oracle: preparation timed once ({t_prep:.2f} s), then {n} samples per step of one draw "
-              f"(N=3, I=2^22, R=32), extrapolated to J=2^16")
+    del Us
+    fresh64 = [synth.fresh_factor(I_ROWS, RANK, seed=1000 + d).astype(np.float64) for d in range(N_FACT)]
+    oracle_tree_steps(Us64, fresh64, args.warmup, REF_SAMPLES_PER_STEP)
+    n, secs, per = oracle_tree_steps(Us64, fresh64, args.steps, REF_SAMPLES_PER_STEP, d_first=args.warmup)
+    v = n / secs
+    sample = (f"oracle per step: one-factor update (FP64 tree rebuild), preparation, and {REF_SAMPLES_PER_STEP} "
+              f"samples of the step's J=2^16 draw by the FP64 tree descent (N=3, I=2^22, R=32, F=32); "
+              f"value = samples drawn / time")
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
         "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample},
@@ -394,22 +401,19 @@ def run_rank_sweep(args):
     }), flush=True)
 
 
-def run_sparse_als(args):
-    """STS-CP (Alg. 6) on a synthetic sparse 2^22 x 2^22 x 2^14 tensor with Zipf(1.1)
-    coordinates and rank-16 U(0,1) values x lognormal(0, 0.5) noise; J = 2^16
-    samples per least-squares solve; per rank: FP32 trees, BF16x3 trees, and
-    the FP32 sweep captured as a CUDA graph.  Reports the median sweep time of
-    sweeps 2..S and the fit after each sweep (fit not timed)."""
-    import torch
-    from paper_2301_12584_gb300 import krpls, synth
-    from paper_2301_12584_gb300.krpls import Sampler, SparseTensor
-    dims, J = (1 << 22, 1 << 22, 1 << 14), 1 << 16
-    dev = torch.device("cuda", 0)
-    krpls.lib()
+SPARSE_DIMS = (1 << 22, 1 << 22, 1 << 14)
+
+
+def sparse_setup(nnz, dev, stream):
+    """The synthetic 2^22 x 2^22 x 2^14 Zipf(1.1) tensor with nnz nonzeros
+    (rank-16 U(0,1) values x lognormal(0, 0.5) noise), its fiber index, and
+    the initial factors' row scales.  Returns (tensor, scales, seconds)."""
+    from paper_2301_12584_gb300 import synth
+    from paper_2301_12584_gb300.krpls import SparseTensor
+    dims = SPARSE_DIMS
     t0 = time.perf_counter()
-    coords, vals = synth.sparse_zipf_tensor(dims, int(args.nnz), seed=0, device=dev)
+    coords, vals = synth.sparse_zipf_tensor(dims, int(nnz), seed=0, device=dev)
     t_gen = time.perf_counter() - t0
-    stream = torch.cuda.Stream(device=dev)
     t0 = time.perf_counter()
     t = SparseTensor(dims, coords, vals, stream=stream)
     t_index = time.perf_counter() - t0
@@ -421,55 +425,81 @@ def run_sparse_als(args):
     for k in range(3):
         cnt = np.bincount(coords[k], minlength=dims[k]).astype(np.float64) + 0.01
         scales.append(np.sqrt(cnt / cnt.mean()).astype(np.float32))
-    del coords, vals
-    results = []
+    return t, scales, {"generate": t_gen, "index": t_index}
+
+
+def sparse_rank_runs(t, scales, R, S, modes, dev, stream):
+    """S STS-CP sweeps (Alg. 6, J = 2^16 per solve) at rank R from the same
+    start for each mode in `modes` (fp32, bf16x3, exact: the sampler's
+    precision; fp32_graph: FP32 with sweeps 2..S replayed from a CUDA graph).
+    Per mode: median sweep time of sweeps 2..S and the fit after each sweep
+    (fit not timed)."""
+    import torch
+    from paper_2301_12584_gb300 import krpls, synth
+    from paper_2301_12584_gb300.krpls import Sampler
+    dims, J = SPARSE_DIMS, 1 << 16
+    Us0 = synth.gaussian_factors(3, list(dims), R, seed=0)
+    Ud = [torch.from_numpy(U * sc[:, None]).to(dev) for U, sc in zip(Us0, scales)]
+    del Us0
+    row = {"R": R}
+    precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "exact": krpls.KRP_PREC_EXACT,
+             "fp32_graph": krpls.KRP_PREC_FP32}
+    for mode in modes:
+        s = Sampler(list(dims), R, 0, precs[mode], stream=stream)
+        for k in range(3):
+            s.set_factor(k, Ud[k])
+        sigma = torch.zeros(R, device=dev)
+        times, fits = [], []
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            for sw in range(S):
+                if mode == "fp32_graph" and sw == 1:
+                    s.capture_begin()
+                    s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
+                    s.capture_end()
+                torch.cuda.synchronize()
+                a.record(stream)
+                if mode == "fp32_graph" and sw >= 1:
+                    s.replay()
+                else:
+                    s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
+                b.record(stream)
+                torch.cuda.synchronize()
+                times.append(a.elapsed_time(b))
+                fits.append(s.cp_fit(t, sigma))
+        status = s.sync_status()
+        row[mode] = {"status": status, "sweep_ms_median_2_to_S": statistics.median(times[1:]),
+                     "first_sweep_ms": times[0], "fit_last": fits[-1],
+                     "fit_mean_second_half": statistics.mean(fits[S // 2:]), "fits": [round(f, 6) for f in fits]}
+        s.close()
+    base = row["fp32"]["fit_mean_second_half"] if "fp32" in row else None
+    for mode in modes:
+        if mode != "fp32" and base:
+            row[mode]["mean_fit_rel_diff_vs_fp32"] = abs(row[mode]["fit_mean_second_half"] - base) / abs(base)
+    del Ud
+    torch.cuda.empty_cache()
+    return row
+
+
+def run_sparse_als(args):
+    """STS-CP (Alg. 6) on a synthetic sparse 2^22 x 2^22 x 2^14 tensor with Zipf(1.1)
+    coordinates and rank-16 U(0,1) values x lognormal(0, 0.5) noise; J = 2^16
+    samples per least-squares solve; per rank: FP32 trees, BF16x3 trees, exact
+    decisions (R <= 32), and the FP32 sweep captured as a CUDA graph.  Reports
+    the median sweep time of sweeps 2..S and the fit after each sweep (fit not
+    timed)."""
+    import torch
+    from paper_2301_12584_gb300 import krpls
+    dev = torch.device("cuda", 0)
+    krpls.lib()
+    stream = torch.cuda.Stream(device=dev)
+    t, scales, setup_s = sparse_setup(args.nnz, dev, stream)
     ranks = [int(r) for r in str(args.ranks).split(",") if r]
     S = max(int(args.sweeps), 3)
+    results = []
     for R in ranks:
-        Us0 = synth.gaussian_factors(3, list(dims), R, seed=0)
-        Ud = [torch.from_numpy(U * sc[:, None]).to(dev) for U, sc in zip(Us0, scales)]
-        del Us0
-        row = {"R": R}
-        for mode in ("fp32", "bf16x3", "fp32_graph"):
-            prec = krpls.KRP_PREC_BF16X3 if mode == "bf16x3" else krpls.KRP_PREC_FP32
-            s = Sampler(list(dims), R, 0, prec, stream=stream)
-            for k in range(3):
-                s.set_factor(k, Ud[k])
-            sigma = torch.zeros(R, device=dev)
-            times, fits = [], []
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            with torch.cuda.stream(stream):
-                for sw in range(S):
-                    if mode == "fp32_graph" and sw == 1:
-                        s.capture_begin()
-                        s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
-                        s.capture_end()
-                    torch.cuda.synchronize()
-                    a.record(stream)
-                    if mode == "fp32_graph" and sw >= 1:
-                        s.replay()
-                    else:
-                        s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
-                    b.record(stream)
-                    torch.cuda.synchronize()
-                    times.append(a.elapsed_time(b))
-                    fits.append(s.cp_fit(t, sigma))
-            status = s.sync_status()
-            row[mode] = {"status": status, "sweep_ms_median_2_to_S": statistics.median(times[1:]), "first_sweep_ms": times[0],
-                         "fit_last": fits[-1], "fits": [round(f, 6) for f in fits]}
-            s.close()
-        row["bf16x3_fit_rel_diff"] = abs(row["bf16x3"]["fit_last"] - row["fp32"]["fit_last"]) / max(
-            1e-30, abs(row["fp32"]["fit_last"]))
-        # each sweep's fit is that of one random sketch: compare the means over
-        # the second half of the sweeps, next to FP32's own run-to-run spread
-        # (the FP32 graph replay differs from the FP32 run only by atomic order)
-        half = {m: statistics.mean(row[m]["fits"][S // 2:]) for m in ("fp32", "bf16x3", "fp32_graph")}
-        row["fit_mean_second_half"] = half
-        row["bf16x3_vs_fp32_mean_fit_rel_diff"] = abs(half["bf16x3"] - half["fp32"]) / max(1e-30, abs(half["fp32"]))
-        row["fp32_run_to_run_mean_fit_rel_diff"] = abs(half["fp32_graph"] - half["fp32"]) / max(1e-30, abs(half["fp32"]))
-        results.append(row)
-        del Ud
-        torch.cuda.empty_cache()
+        modes = ("fp32", "bf16x3", "exact", "fp32_graph") if R <= 32 else ("fp32", "bf16x3", "fp32_graph")
+        results.append(sparse_rank_runs(t, scales, R, S, modes, dev, stream))
     print(json.dumps({
         "metric": "STS-CP sweep time (median of sweeps 2..S), sparse 3-mode tensor",
         "value": results[0]["fp32"]["sweep_ms_median_2_to_S"], "unit": "ms per sweep",
@@ -478,7 +508,7 @@ def run_sparse_als(args):
         "config": {"workload": f"sparse_als_2^22x2^22x2^14_nnz{int(args.nnz)}_J2^16", "nnz": int(args.nnz),
                    "ranks": ranks, "sweeps": S,
                    "init": "N(0,1) rows x sqrt((nnz of the index + 0.01) / mean), seed 0"},
-        "setup_s": {"generate": t_gen, "index": t_index},
+        "setup_s": setup_s,
         "results": results,
     }), flush=True)
 
@@ -547,6 +577,77 @@ def run_accuracy(args):
 
 
 # ------------------------------------------------------------------ ours ----
+def sampler_run(prec, Ud, Fd, dev, stream, warmup, steps, draws, dist=None, clocks_index=None):
+    """The headline step (one-factor update from device rows, prepare, draw
+    with fused gather) on a sampler of the given precision: `warmup` untimed
+    steps, then `steps` timed with CUDA events on the sampler's stream
+    (barrier + synchronize on both sides), with per-phase events."""
+    import torch
+    from paper_2301_12584_gb300 import krpls, replicas
+    from paper_2301_12584_gb300.krpls import Sampler
+    s = Sampler([I_ROWS] * N_FACT, RANK, LEAF, prec, stream=stream)
+    for k in range(N_FACT):
+        s.set_factor(k, Ud[k])
+    J = J_DRAW
+    idx = torch.zeros((N_FACT, J), dtype=torch.int32, device=dev)
+    w = torch.zeros(J, dtype=torch.float32, device=dev)
+    SA = torch.zeros((J, RANK), dtype=torch.float32, device=dev)
+    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
+    phases = []
+
+    def step(d, timed):
+        if timed:
+            e = [ev() for _ in range(4)]
+            e[0].record(stream)
+        s.set_factor(d % N_FACT, Fd[d % N_FACT])
+        if timed:
+            e[1].record(stream)
+        s.sample_prepare(-1)
+        if timed:
+            e[2].record(stream)
+        s.sample_draw(-1, J, 1, draws[d], idx, w, None, SA)
+        if timed:
+            e[3].record(stream)
+            phases.append(e)
+
+    clk = None
+    with torch.cuda.stream(stream):
+        for d in range(warmup):
+            step(d, False)
+        torch.cuda.synchronize()
+        assert s.sync_status() == 0, s.last_error()
+        if dist:
+            dist.barrier()
+        clocks = ClockSampler(clocks_index) if clocks_index is not None else None
+        if clocks:
+            clocks.start()
+            time.sleep(0.2)
+        n0 = krpls.launch_count()
+        t_start, t_end = ev(), ev()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_start.record(stream)
+        for d in range(warmup, warmup + steps):
+            step(d, True)
+        t_end.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        n_launch = krpls.launch_count() - n0
+        if clocks:
+            clk = clocks.stop()
+    assert s.sync_status() == 0, s.last_error()
+    ms = replicas.max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
+    out = {"ms": ms, "n_launch": n_launch, "clocks": clk,
+           "phases_ms": {"update": statistics.mean(p[0].elapsed_time(p[1]) for p in phases),
+                         "prepare": statistics.mean(p[1].elapsed_time(p[2]) for p in phases),
+                         "draw": statistics.mean(p[2].elapsed_time(p[3]) for p in phases)},
+           "exact_redecisions_per_row_stage": s.exact_count() / float(J * N_FACT * (warmup + steps))
+           if prec == krpls.KRP_PREC_EXACT else None}
+    return s, idx, w, SA, out
+
+
 def main():
     args = parse()
     from paper_2301_12584_gb300 import replicas
@@ -566,7 +667,6 @@ def main():
 
     import torch
     from paper_2301_12584_gb300 import krpls, synth
-    from paper_2301_12584_gb300.krpls import Sampler
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
@@ -575,7 +675,7 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     krpls.lib()
-    prec = krpls.KRP_PREC_FP32 if args.precision == "fp32" else krpls.KRP_PREC_BF16X3
+    precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "exact": krpls.KRP_PREC_EXACT}
 
     # ---- inputs (seeded, synthetic): same generator as the tests
     Us = synth.skewed_row_factors(N_FACT, I_ROWS, RANK, seed=0)
@@ -585,64 +685,15 @@ def main():
     Fd = [torch.from_numpy(U).to(dev) for U in fresh]
     Fh = [torch.from_numpy(U).pin_memory() for U in fresh]
     torch.cuda.synchronize()
-    s = Sampler([I_ROWS] * N_FACT, RANK, LEAF, prec, stream=stream)
-    for k in range(N_FACT):
-        s.set_factor(k, Ud[k])
     J = J_DRAW
-    idx = torch.zeros((N_FACT, J), dtype=torch.int32, device=dev)
-    w = torch.zeros(J, dtype=torch.float32, device=dev)
-    SA = torch.zeros((J, RANK), dtype=torch.float32, device=dev)
     draws = replicas.draw_ids(rank, 0, args.warmup + args.steps)          # this rank's own Philox draw ids
     e2e_draws = replicas.draw_ids(rank, 500_000, max(args.e2e_steps, 0))
 
-    ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
-    phases = []
-
-    def step(d, timed):
-        if timed:
-            e = [ev() for _ in range(4)]
-            e[0].record(stream)
-        s.set_factor(d % N_FACT, Fd[d % N_FACT])
-        if timed:
-            e[1].record(stream)
-        s.sample_prepare(-1)
-        if timed:
-            e[2].record(stream)
-        s.sample_draw(-1, J, 1, draws[d], idx, w, None, SA)
-        if timed:
-            e[3].record(stream)
-            phases.append(e)
-
-    with torch.cuda.stream(stream):
-        for d in range(args.warmup):
-            step(d, False)
-        torch.cuda.synchronize()
-        assert s.sync_status() == 0, s.last_error()
-        if dist:
-            dist.barrier()
-        clocks = ClockSampler(local)
-        clocks.start()
-        time.sleep(0.2)
-        n0 = krpls.launch_count()
-        t_start, t_end = ev(), ev()
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        t_start.record(stream)
-        for d in range(args.warmup, args.warmup + args.steps):
-            step(d, True)
-        t_end.record(stream)
-        torch.cuda.synchronize()
-        if dist:
-            dist.barrier()
-        n_launch = krpls.launch_count() - n0
-        clk = clocks.stop()
-    assert s.sync_status() == 0, s.last_error()
-    ms = replicas.max_over_ranks(t_start.elapsed_time(t_end), dist, dev)
+    s, idx, w, SA, head = sampler_run(precs[args.precision], Ud, Fd, dev, stream, args.warmup, args.steps, draws,
+                                      dist, local)
+    ms = head["ms"]
     value = replicas.whole_job_rate(J * args.steps, world, ms)
-    upd = statistics.mean(p[0].elapsed_time(p[1]) for p in phases)
-    prep = statistics.mean(p[1].elapsed_time(p[2]) for p in phases)
-    drw = statistics.mean(p[2].elapsed_time(p[3]) for p in phases)
+    drw = head["phases_ms"]["draw"]
 
     # ---- roofline of the descent kernel (one launch per draw)
     peaks = {}
@@ -652,28 +703,34 @@ def main():
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     T = RANK * (RANK + 1) // 2
+    Tp = (T + 7) // 8 * 8
     depth = (I_ROWS // LEAF - 1).bit_length()
     bytes_per_sample = N_FACT * (4 * T * depth + 4 * LEAF * RANK)     # nominal tree path + leaf block
     achieved = bytes_per_sample * J / (drw / 1e3) / 1e9
-    roof = {"kernel": "krp_descent_fast<32>", "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-            "frac": achieved / hbm, "traffic": DESCENT_DRAM_BYTES,
-            "traffic_frac": DESCENT_DRAM_BYTES / (drw / 1e3) / 1e9 / hbm,
+    roof = {"kernel": "krp_descent_fast<32>" + (", exact decisions" if args.precision == "exact" else ""),
+            "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+            "frac": achieved / hbm, "traffic": DESCENT_DRAM_BYTES if args.precision == "fp32" else None,
+            "traffic_frac": DESCENT_DRAM_BYTES / (drw / 1e3) / 1e9 / hbm if args.precision == "fp32" else None,
             "algorithmic_bytes_per_launch": bytes_per_sample * J,
             "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
             "note": ("achieved/frac: nominal bytes (every sample reads its full root-to-leaf path); "
                      "traffic: ncu DRAM bytes per launch (upper levels are L2 hits); traffic_frac: that "
                      "traffic over the live launch time, against the same peak")}
-    # tree rebuild (update) roofline, informational
+    # tree rebuild (update): read the fresh rows once, write the sampler's copy and the tree
+    # (and the low parts in the exact-decision mode), informational
     L = 1 << depth
-    build_bytes = I_ROWS * RANK * 4 + L * ((T + 7) // 8 * 8) * 4 + 2 * I_ROWS * RANK * 4
+    build_bytes = 2 * I_ROWS * RANK * 4 + L * Tp * 4 * (2 if args.precision == "exact" else 1)
+    upd = head["phases_ms"]["update"]
     update_info = {"ms": upd, "bytes": build_bytes, "GBps": build_bytes / (upd / 1e3) / 1e9,
-                   "note": "copy of the fresh factor (read+write) + tree build (read U, write tree)"}
+                   "frac": build_bytes / (upd / 1e3) / 1e9 / hbm,
+                   "note": "read the fresh factor once, write the sampler's copy and the tree"}
 
     # ---- end to end through the C ABI with host buffers
     e2e = None
     if args.e2e_steps > 0:
         idx_h = torch.zeros((N_FACT, J), dtype=torch.int32).pin_memory()
         w_h = torch.zeros(J, dtype=torch.float32).pin_memory()
+        ev = lambda: torch.cuda.Event(enable_timing=True)  # noqa: E731
         with torch.cuda.stream(stream):
             torch.cuda.synchronize()
             a, b = ev(), ev()
@@ -689,12 +746,45 @@ def main():
         e_ms = replicas.max_over_ranks(a.elapsed_time(b), dist, dev)
         e2e = {"value": replicas.whole_job_rate(J * args.e2e_steps, world, e_ms), "unit": UNIT,
                "h2d_bytes_per_step": I_ROWS * RANK * 4, "d2h_bytes_per_step": J * (N_FACT * 4 + 4)}
+    s.close()
+
+    # ---- the other precision forms of the same step (rank 0 at N=1: extra keys)
+    forms = {args.precision: {"value": value, "ms_per_step": ms / args.steps, "phases_ms": head["phases_ms"],
+                              "exact_redecisions_per_row_stage": head["exact_redecisions_per_row_stage"]}}
+    if world == 1 and not args.no_forms:
+        for name in ("fp32", "bf16x3", "exact"):
+            if name == args.precision:
+                continue
+            sf, _, _, _, out = sampler_run(precs[name], Ud, Fd, dev, stream, args.warmup, args.steps, draws)
+            sf.close()
+            forms[name] = {"value": J * args.steps / (out["ms"] / 1e3), "ms_per_step": out["ms"] / args.steps,
+                           "phases_ms": out["phases_ms"],
+                           "exact_redecisions_per_row_stage": out["exact_redecisions_per_row_stage"]}
+    del Ud, Fd
+    torch.cuda.empty_cache()
+
+    # ---- the metric's second half: STS-CP sweep time, mixed vs FP32 (rank 0 at N=1)
+    sts = None
+    if world == 1 and args.sts_sweeps > 0:
+        t, scales, setup_s = sparse_setup(args.nnz, dev, stream)
+        row = sparse_rank_runs(t, scales, 25, max(3, args.sts_sweeps), ("fp32", "bf16x3", "exact"), dev, stream)
+        t.close()
+        sts = {"workload": f"sts_cp_2^22x2^22x2^14_nnz{int(args.nnz)}_R25_J2^16", "unit": "ms per sweep",
+               "sweeps": max(3, args.sts_sweeps), "setup_s": setup_s,
+               **{m: {"sweep_ms_median_2_to_S": row[m]["sweep_ms_median_2_to_S"],
+                      "fit_mean_second_half": row[m]["fit_mean_second_half"], "fit_last": row[m]["fit_last"],
+                      "mean_fit_rel_diff_vs_fp32": row[m].get("mean_fit_rel_diff_vs_fp32"),
+                      "status": row[m]["status"]} for m in ("fp32", "bf16x3", "exact")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Us64 = [U.astype(np.float64) for U in Us]
-        v, secs, sample = oracle_samples_per_s(Us64)
-        cpu = {"value": v, "unit": UNIT, "cores": cores_used(), "kind": "oracle", "sample": sample,
+        fresh64 = [U.astype(np.float64) for U in fresh]
+        n, secs, _ = oracle_tree_steps(Us64, fresh64, 1, J_DRAW)
+        cpu = {"value": n / secs, "unit": UNIT, "cores": cores_used(), "kind": "oracle",
+               "sample": ("one step of the workload by the FP64 oracle: one-factor update (FP64 segment-tree "
+                          "rebuild, Alg. 3), preparation, and the full J=2^16 draw by the FP64 tree descent "
+                          "(Alg. 2/4), no extrapolation"),
                "seconds": secs}
 
     if rank == 0:
@@ -705,15 +795,16 @@ def main():
             "config": {"workload": WORKLOAD, "precision": args.precision, "N": N_FACT, "I": I_ROWS, "R": RANK,
                        "F": LEAF, "J": J, "l2": "inputs larger than L2 (no flush needed)",
                        "parallelism": f"replicas x{world}"},
-            "phases_ms": {"update": upd, "prepare": prep, "draw": drw},
+            "phases_ms": head["phases_ms"],
             "update": update_info,
             "roofline": roof,
-            "clocks": clk,
-            "gpu_launches": n_launch,
+            "clocks": head["clocks"],
+            "gpu_launches": head["n_launch"],
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "forms": forms,
+            "sts_cp": sts,
         }), flush=True)
-    s.close()
     if dist:
         dist.destroy_process_group()
 

@@ -52,8 +52,15 @@ typedef enum {
 
 typedef enum {
     KRP_PREC_FP32 = 0,    /* segment-tree Grams by FP32 FMA                      */
-    KRP_PREC_BF16X3 = 1   /* Grams on tcgen05 tensor cores, BF16 hi/lo split,    */
+    KRP_PREC_BF16X3 = 1,  /* Grams on tcgen05 tensor cores, BF16 hi/lo split,    */
                           /* three products, FP32 accumulate                     */
+    KRP_PREC_EXACT = 2    /* exact decisions (sampler-wide, at krp_create, R <= 32): */
+                          /* leaf Grams accumulated without rounding error, every */
+                          /* tree slot kept as a double-float (hi, lo) pair, the  */
+                          /* top tree levels also stored as deviations from their */
+                          /* share of the parent, and every descent decision that */
+                          /* falls within 2e-9 C of a bin edge re-taken from      */
+                          /* double-float masses (Alg. 4 in near-FP64 arithmetic) */
 } krp_precision;
 
 #define KRP_PINV_FALLBACK 1  /* krp_solve_*: if Cholesky fails, use the FP64
@@ -70,6 +77,11 @@ typedef enum {
  * 1 <= N <= 16, 1 <= R <= 128, 1 <= I_k < 2^31, 1 <= F <= 4*R.
  * `stream` is a cudaStream_t (may be NULL).  Allocates all factor, tree and
  * sampler storage.  On failure *out is set to NULL.
+ * precision = KRP_PREC_EXACT makes the whole sampler draw as the FP64 Alg. 2/4
+ * would (indices equal to an FP64 replay except where a uniform lies within
+ * ~1e-12 of a bin edge): it needs R <= 32 (KRP_EINVAL otherwise), allocates a
+ * second array the size of each tree plus 2^10 slots per factor, builds
+ * every tree with exact leaves whatever precision krp_set_factor_prec names.
  * ---------------------------------------------------------------------- */
 krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, int F,
                       int precision, void* stream);
@@ -138,6 +150,8 @@ krp_status krp_sample(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed,
  * krp_sample_draw returns KRP_ESTATE if the last prepare was for another
  * exclude_j or a factor was set since. */
 krp_status krp_sample_prepare(krp_sampler* s, int exclude_j);
+krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
+                           int32_t* idx, float* weight, float* logq, float* SA);
 
 /* Form of the descent for 32 < R <= 128 (no effect at R <= 32): the same
  * draws up to the rounding of the masses (flips only where a uniform lies
@@ -155,16 +169,6 @@ krp_status krp_sample_prepare(krp_sampler* s, int exclude_j);
 #define KRP_DESCENT_TEAM 1
 #define KRP_DESCENT_NODE_MAJOR 2
 krp_status krp_set_descent_form(krp_sampler* s, int form);
-
-/* Measurement helper (no counterpart in the paper): throughput of the current
- * device on fixed, bounded probes, timed with CUDA events on `stream` (may be
- * NULL): out_host[0] FP32 TFLOP/s with scalar FMA, [1] FP32 TFLOP/s with
- * paired (f32x2) FMA, [2] FP64 TFLOP/s, [3] L2 read GB/s (64 MB buffer).
- * Allocates and frees 64 MB of device memory; synchronous.  These are the
- * denominators of the SIMT, FP64 and L2-bound rooflines. */
-krp_status krp_probe_peaks(double* out_host, void* stream);
-krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id,
-                           int32_t* idx, float* weight, float* logq, float* SA);
 
 /* Sampled-row gather: SA[s,:] = weight[s] * ⊛_{k != exclude_j} U_k[idx[k][s], :]
  * (the rows of S·A, Sec. 2.1).  idx/weight as produced by krp_sample.  Indices
@@ -197,9 +201,10 @@ krp_status krp_solve_dense(krp_sampler* s, int64_t J, const float* SA, const flo
  *   stream: cudaStream_t (NULL = legacy default stream).
  * Scratch: a fixed 2.13 MB array in the library's device image (512 partial
  * sums of SAᵀSA and SAᵀSB), needing no initial value.  R > 32 or nrhs > 16 is
- * rejected with KRP_EINVAL (message in krp_last_error(NULL)).  The first call
- * on each device looks up the array's device address (which may load the
- * library's device code), so make it before capturing any stream.  All calls
+ * rejected with KRP_EINVAL (message in krp_last_error(NULL)).  Every call
+ * looks up the array's device address in the current context; the first call
+ * in a context may load the library's device code there, so make it before
+ * capturing any stream.  All calls
  * on one device share the array: calls that overlap in time (other streams,
  * other host threads) race on it and must be serialised by the caller.
  * Returns KRP_OK once both kernels are enqueued. */
@@ -255,12 +260,25 @@ krp_status krp_sync_status(krp_sampler* s);
  * (all samplers; for accounting in benchmarks). */
 int64_t krp_launch_count(void);
 
+/* Exact-decision samplers (KRP_PREC_EXACT): number of row-stage descents that
+ * have switched to double-float masses since krp_create (a decision or a leaf
+ * scan within the near-edge band of Alg. 4's cutoffs; at most one per sample
+ * and included factor), written to *count_host after a stream
+ * synchronisation.  Zero for other samplers.  No counterpart in the paper. */
+krp_status krp_exact_count(krp_sampler* s, int64_t* count_host);
+
 /* Test hook for the device-side wait bound (no counterpart in the paper): the
  * descent's TMA waits give up after a bounded number of suspending tries and
  * set KRP_ETIMEOUT instead of hanging.  This launches one warp that waits on a
  * barrier nothing completes, with `tries` (1..1000) tries of up to ~0.1 ms
  * each; krp_sync_status then returns KRP_ETIMEOUT and the context stays usable. */
 krp_status krp_debug_wait_timeout(krp_sampler* s, int tries);
+
+/* Test hook for the stable radix sort behind krp_solve_sparse (no
+ * counterpart in the paper): sorts n (key, value) pairs of device uint32
+ * arrays in place by the low `bits` bits of the keys (1..32), equal keys in
+ * their input order.  Allocates temporary arrays; synchronous on `stream`. */
+krp_status krp_debug_sort_pairs(uint32_t* keys, uint32_t* vals, int64_t n, int bits, void* stream);
 
 /* Message for the most recent failure on this sampler; never NULL. */
 const char* krp_last_error(const krp_sampler* s);
@@ -286,6 +304,17 @@ krp_status krp_tree_info(const krp_sampler* s, int j, int64_t* L_host, int* dept
  * numbering (root 1, children 2v, 2v+1, leaf b = node L + b).  Each slot is
  * the upper triangle of G^v packed row by row, then zero padding.  Synchronous. */
 krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_floats);
+
+/* Exact-decision samplers (KRP_PREC_EXACT): copy factor j's low parts (the
+ * slot layout of krp_get_tree, L * node_stride floats: slot value = tree +
+ * low part, a double-float) and/or its delta-encoded top (2^Ke *
+ * node_stride floats, Ke = min(10, depth), in the tree's slot numbering: the
+ * root, then for slot c = 1 .. 2^Ke - 1 the FP32 rounding of G_{2c} - alpha_c
+ * G_c with alpha_c = rows(2c) / rows(c) rounded to FP32) to host; NULL skips
+ * either.
+ * KRP_EINVAL for other samplers or short buffers.  Synchronous. */
+krp_status krp_get_tree_exact(const krp_sampler* s, int j, float* lo_host, int64_t n_lo, float* dtop_host,
+                              int64_t n_dtop);
 
 /* Copy the sampler's copy of factor j (I_j x R row-major FP32, n_floats >=
  * I_j R) to host memory: what krp_set_factor stored, or what the last

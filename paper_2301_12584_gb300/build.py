@@ -2,6 +2,8 @@
 
 Usage: python -m paper_2301_12584_gb300.build   (or build() from Python)
 The library lands next to this file; objects go to _build/ at the repo root.
+Also builds libkrpprobe.so from measure/ (throughput probes for the rooflines'
+denominators; a measurement tool that the library does not link).
 """
 from __future__ import annotations
 
@@ -16,6 +18,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "libkrpls.so")
+PROBE_SRC = os.path.join(PKG, "measure", "probe.cu")
+PROBE_OUT = os.path.join(PKG, "libkrpprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include")]
@@ -45,8 +49,15 @@ def build(verbose: bool = False, extra_flags=None) -> str:
             print(r.stdout, r.stderr, file=sys.stderr)
         return obj
 
-    with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
+    with cf.ThreadPoolExecutor(max_workers=min(len(srcs) + 1, os.cpu_count() or 4)) as ex:
+        probe = ex.submit(compile_one, PROBE_SRC)
         objs = list(ex.map(compile_one, srcs))
+        probe_obj = probe.result()
+    r = subprocess.run([nvcc, *ARCH, "-shared", "-o", PROBE_OUT + ".tmp", probe_obj, "-lcudart"],
+                       capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"probe link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(PROBE_OUT + ".tmp", PROBE_OUT)
     tmp = OUT + ".tmp"
     cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -202,6 +202,10 @@ krp_status krp_batch_create(krp_batch** out, krp_sampler* const* samplers, int P
             delete b;
             return fail(nullptr, KRP_EINVAL, "krp_batch_create: batched problems need R <= 32 and F <= 32");
         }
+        if (s->exact) {
+            delete b;
+            return fail(nullptr, KRP_EINVAL, "krp_batch_create: exact-decision samplers are drawn one by one");
+        }
         for (int k = 0; k < s->N; ++k)
             if (!s->has_factor[k]) {
                 delete b;

@@ -73,6 +73,19 @@ __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
     return *reinterpret_cast<float2*>(&d);
 }
+// Paired FP32 add / subtract (one instruction each, round to nearest).
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+    uint64_t d;
+    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b);
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(ua), "l"(ub));
+    return *reinterpret_cast<float2*>(&d);
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+    uint64_t d;
+    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b);
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(ua), "l"(ub));
+    return *reinterpret_cast<float2*>(&d);
+}
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
     for (int m = 16; m > 0; m >>= 1) v += __shfl_xor_sync(0xffffffffu, v, m);
@@ -102,6 +115,16 @@ __device__ __forceinline__ df df_add(df a, df b) {
     return r;
 }
 __device__ __forceinline__ df df_neg(df a) { return df{-a.hi, -a.lo}; }
+// (double-float) + (float)
+__device__ __forceinline__ df df_add_f(df a, float b) {
+    float s, e;
+    two_sum(a.hi, b, s, e);
+    e += a.lo;
+    df r;
+    r.hi = s + e;
+    r.lo = e - (r.hi - s);
+    return r;
+}
 // (float) x (double-float)
 __device__ __forceinline__ df df_mul_f(df a, float b) {
     const float p = a.hi * b;
@@ -117,6 +140,51 @@ __device__ __forceinline__ bool df_le(df a, df b) {
     const df d = df_add(a, df_neg(b));
     return d.hi < 0.f || (d.hi == 0.f && d.lo <= 0.f);
 }
+// a * b = p + e exactly (TwoProduct by FMA).
+__device__ __forceinline__ df two_prod(float a, float b) {
+    const float p = a * b;
+    return df{p, fmaf(a, b, -p)};
+}
+// (double-float) x (double-float), about 2^-44 relative.
+__device__ __forceinline__ df df_mul(df a, df b) {
+    const float p = a.hi * b.hi;
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, e);
+    e = fmaf(a.lo, b.hi, e);
+    df r;
+    r.hi = p + e;
+    r.lo = e - (r.hi - p);
+    return r;
+}
+
+// ---------------------------------------------------------------------------
+// Rows of heap node h at depth t of a tree with L leaves of F rows over I
+// rows (Sec. 3.1: leaf b holds rows [bF, min((b+1)F, I)), padding leaves are
+// empty), and the share alpha_c = rows(2c) / rows(c) of node c's left child,
+// rounded to FP32 (1/2 for every full node).  The exact-decision mode stores
+// the top levels of a tree as D_c = G_{2c} - alpha_c G_c, so that the FP32
+// rounding falls on the small deviation of a child from its share of the
+// parent rather than on the child's whole Gram.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int64_t node_rows(int64_t h, int t, int64_t L, int F, int64_t I) {
+    const int64_t span = L >> t;
+    const int64_t b0 = (h - ((int64_t)1 << t)) * span;
+    const int64_t lo = b0 * F < I ? b0 * F : I;
+    const int64_t hi = (b0 + span) * F < I ? (b0 + span) * F : I;
+    return hi - lo;
+}
+__host__ __device__ __forceinline__ float node_alpha(int64_t c, int t, int64_t L, int F, int64_t I) {
+    const int64_t n = node_rows(c, t, L, F, I);
+    return n > 0 ? (float)node_rows(2 * c, t + 1, L, F, I) / (float)n : 0.5f;
+}
+// Top levels delta-encoded in exact-decision mode (decisions at depth < KRP_EXACT_TOP).
+constexpr int KRP_EXACT_TOP = 10;
+// Near-edge band of the exact-decision mode, relative to the stage total C:
+// a decision whose FP32-path gap |tau - low - m(L(c))| is within this band
+// is re-taken from double-float masses (the FP32 path with a delta-encoded
+// top is off by under 4e-10 C on 2^22-row trees).
+constexpr float KRP_EXACT_BAND = 2e-9f;
+
 // Butterfly sum of a double-float over the warp; every lane gets the same pair
 // (TwoSum gives the same exact error for either operand order).
 __device__ __forceinline__ df warp_sum_df(df v) {

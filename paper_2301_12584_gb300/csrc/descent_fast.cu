@@ -18,6 +18,18 @@
 // cutoff low + m(L(c)) are double-float, and so are h and h̃ (products of
 // FP32 rows and FP64 eigenvectors), so that a branch differs from an FP64
 // evaluation only when tau lies within ~1e-7 C of a cutoff.
+//
+// Exact-decision mode (EXACT, KRP_PREC_EXACT): the row stage starts from the
+// double-float root (C and tau to ~2^-44), takes the top levels from the
+// delta-encoded slots D_c = G_{2c} - alpha_c G_c (m(L(c)) = alpha_c m(c) +
+// wᵀD_c, whose FP32 error is that of the small deviation wᵀD_c), carries a
+// running bound on the FP32 path's error, and re-takes any decision whose gap
+// tau - low - m(L(c)) falls within that bound plus KRP_EXACT_BAND C from
+// double-float masses of the (hi, lo) slots with double-float weights of h̃:
+// the offset low is then recomputed from the path's right turns, and the
+// stage stays in that form to its leaf, whose rows are rescored in
+// double-float when the FP32 scan is near an edge.  The eigencomponent stage
+// (R bins) keeps the FP32 form.
 #include "common.cuh"
 #include "internal.h"
 
@@ -36,9 +48,10 @@ struct FastCfg {
     static constexpr int WARPS = 8;
     static constexpr int RPT = (4 * RMAX + 31) / 32;  // leaf rows per lane (F <= 4R)
     // per-warp shared memory: 3 staged nodes (slots 0..1 on a stage's first
-    // fetch, then slots c, 2c, 2c+1; also the leaf rows), h (hi, lo), h̃, mbarrier
+    // fetch, then slots c, 2c, 2c+1; also the leaf rows), h (hi, lo), h̃ (hi,
+    // lo), mbarrier
     static constexpr int STAGE = 3 * TPMAX;
-    static constexpr int WARP_BYTES = ((STAGE + 3 * RMAX) * 4 + 16 + 127) & ~127;
+    static constexpr int WARP_BYTES = ((STAGE + 4 * RMAX) * 4 + 16 + 127) & ~127;
     static constexpr int SMEM = WARPS * WARP_BYTES + 2 * TPMAX;
 };
 
@@ -71,9 +84,113 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int max_
     return false;
 }
 
+// Exact-decision mode: mass h̃ᵀ G h̃ of a node from its double-float slot (ghi,
+// glo: shared or global) with double-float weights of h̃ = (th, thl), ~2^-44
+// relative; every lane of the warp calls it and gets the same value.  It
+// serves the rare near-edge decisions, so its loops stay rolled: inlined in
+// the descent it then adds little to the loop's instruction footprint.
+template <int NCH>
+__device__ __forceinline__ df exact_mass_fn(const float* ghi, const float* glo, const float* th, const float* thl,
+                                         const uint8_t* s_i, const uint8_t* s_j, int T, int nc4) {
+    const int lane = threadIdx.x & 31;
+    df acc{0.f, 0.f};
+#pragma unroll 1
+    for (int m = 0; m < NCH; ++m) {
+        const int c4 = lane + 32 * m;
+        if (c4 < nc4) {
+            const float4 h4 = reinterpret_cast<const float4*>(ghi)[c4];
+            const float4 l4 = reinterpret_cast<const float4*>(glo)[c4];
+            const float gh[4] = {h4.x, h4.y, h4.z, h4.w}, gl[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll 1
+            for (int q = 0; q < 4; ++q) {
+                const int p = 4 * c4 + q;
+                if (p < T) {
+                    const int i = s_i[p], j = s_j[p];
+                    df w = two_prod(th[i], th[j]);
+                    w.lo = fmaf(th[i], thl[j], fmaf(thl[i], th[j], w.lo));
+                    if (i != j) {
+                        w.hi += w.hi;
+                        w.lo += w.lo;
+                    }
+                    df t = two_prod(w.hi, gh[q]);
+                    t.lo = fmaf(w.hi, gl[q], fmaf(w.lo, gh[q], t.lo));
+                    acc = df_add(acc, t);
+                }
+            }
+        }
+    }
+    return warp_sum_df(acc);
+}
+// low of node c at depth lvl: the exact masses of the left siblings of the
+// path's right turns (the left sibling of a right child n sits at slot n/2).
+template <int NCH>
+__device__ __forceinline__ df exact_low_fn(const float* tr, const float* tl, int64_t c, int lvl, int Tp,
+                                        const float* th, const float* thl, const uint8_t* s_i, const uint8_t* s_j,
+                                        int T) {
+    df lw{0.f, 0.f};
+    for (int t = 0; t < lvl; ++t) {
+        const int64_t n = c >> (lvl - 1 - t);   // path node at depth t + 1
+        if (n & 1)
+            lw = df_add(lw, exact_mass_fn<NCH>(tr + (n >> 1) * Tp, tl + (n >> 1) * Tp, th, thl, s_i, s_j, T, Tp >> 2));
+    }
+    return lw;
+}
+
+// Exact-decision mode: a leaf scan re-taken in double-float, every lane
+// calling with its rows t = lane rpt + r of the leaf (rows: nrows rows of R
+// floats, shared or global): q_t = (U[t] · h̃)^2 with h̃ = (th, thl),
+// cumulative right edges from low.  Returns this lane's first row whose edge
+// reaches tau (0x7fffffff if none) and its last row of positive weight (-1).
+template <int RPT>
+__device__ __forceinline__ int2 exact_leaf_scan(const float* rows, int R, int rpt, int nrows, const float* th,
+                                             const float* thl, df tau, df low) {
+    const int lane = threadIdx.x & 31;
+    df qd[RPT];
+#pragma unroll 1
+    for (int r = 0; r < RPT; ++r) {
+        const int t = lane * rpt + r;
+        df d{0.f, 0.f};
+        if (r < rpt && t < nrows) {
+            const float* row = rows + t * R;
+            for (int a = 0; a < R; ++a) {
+                const float x = row[a];
+                df pr = two_prod(x, th[a]);
+                pr.lo = fmaf(x, thl[a], pr.lo);
+                d = df_add(d, pr);
+            }
+        }
+        qd[r] = df_mul(d, d);
+    }
+    df acc{0.f, 0.f};
+#pragma unroll 1
+    for (int r = 0; r < RPT; ++r)
+        if (r < rpt && lane * rpt + r < nrows) acc = df_add(acc, qd[r]);
+    df incd = acc;
+#pragma unroll 1
+    for (int o = 1; o < 32; o <<= 1) {
+        const float vh = __shfl_up_sync(0xffffffffu, incd.hi, o);
+        const float vl = __shfl_up_sync(0xffffffffu, incd.lo, o);
+        if (lane >= o) incd = df_add(df{vh, vl}, incd);
+    }
+    df cd{__shfl_up_sync(0xffffffffu, incd.hi, 1), __shfl_up_sync(0xffffffffu, incd.lo, 1)};
+    if (lane == 0) cd = df{0.f, 0.f};
+    cd = df_add(cd, low);
+    int first = 0x7fffffff, lastpos = -1;
+#pragma unroll 1
+    for (int r = 0; r < RPT; ++r) {
+        const int t = lane * rpt + r;
+        if (r < rpt && t < nrows) {
+            cd = df_add(cd, qd[r]);
+            if (first == 0x7fffffff && df_le(tau, cd)) first = t;
+            if (qd[r].hi > 0.f) lastpos = t;
+        }
+    }
+    return make_int2(first, lastpos);
+}
+
 // The descent for samples cta*8 + warp, stepping by ncta*8 (ncta CTAs share
 // the J samples of one problem).  P may live in parameter or shared memory.
-template <int RMAX>
+template <int RMAX, bool EXACT = false>
 __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t cta, int64_t ncta) {
     using C = FastCfg<RMAX>;
     constexpr int NCH = C::NCH;
@@ -84,7 +201,8 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
     float* hh = stage + C::STAGE;
     float* hl = hh + RMAX;
     float* th = hl + RMAX;
-    uint64_t* mbar = reinterpret_cast<uint64_t*>(th + RMAX);
+    float* thl = th + RMAX;   // h̃'s low parts (exact-decision mode)
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(thl + RMAX);
     uint8_t* s_i = smem + C::WARPS * C::WARP_BYTES;
     uint8_t* s_j = s_i + C::TPMAX;
 
@@ -259,6 +377,137 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         return c;
     };
 
+    // ---------------------------------------------- exact-decision mode
+    auto exact_mass = [&](const float* ghi, const float* glo) -> df {
+        return exact_mass_fn<NCH>(ghi, glo, th, thl, s_i, s_j, T, nc4);
+    };
+    auto exact_low = [&](const float* tr, const float* tl, int64_t c, int lvl) -> df {
+        return exact_low_fn<NCH>(tr, tl, c, lvl, Tp, th, thl, s_i, s_j, T);
+    };
+    // Switch a row stage to exact masses at node c (depth lvl): C and tau from
+    // the double-float root, low from the path's right turns.
+    auto go_exact = [&](const float* tr, const float* tl, int64_t c, int lvl, float uu, df& tau, df& low) {
+        tau = df_mul_f(exact_mass(tr, tl), uu);
+        low = exact_low(tr, tl, c, lvl);
+        if (P.nexact && lane == 0) atomicAdd(P.nexact, 1ull);
+    };
+    // Alg. 4 in the exact-decision mode, for both stages of a factor (one
+    // code path, so that the loop's instruction footprint stays that of one
+    // descent): the row stage on Z_k (tl: its low parts; dt: its delta-encoded
+    // top, Ke levels) and the eigencomponent stage on E_k (tl null, Ke = 0:
+    // near-edge decisions from double-float sums of the FP32 lane partials,
+    // as in the FP32 form, since E_k has R leaves).  The first fetch (slots 0
+    // and 1 of dt) is in flight.  C and tau come from the FP32 root: the top
+    // levels' masses are chained from it (m(L(c)) = alpha_c m(c) + wᵀD_c), so
+    // its relative error scales tau and those masses alike and reaches the
+    // gaps only through the small D terms.  Returns the leaf heap index, with
+    // low its left edge, tau = u C, Cm the root mass, xs whether the stage
+    // switched to exact masses, elow a bound on low's FP32-path error.
+    auto descend_exact = [&](const float* tr, const float* tl, const float* dt, int depth, int Ke, int64_t Lk,
+                             int64_t Ik, int F, float uu, df& Cm, df& tau, df& low, bool& xs, float& elow,
+                             float* trc) -> int64_t {
+        low = df{0.f, 0.f};
+        xs = false;
+        elow = 0.f;
+        if (!fetch_wait()) return 1;
+        Cm = refine(partial(stage));
+        const float cf = Cm.hi + Cm.lo;
+        if (!(cf > 0.f) || !isfinite(cf)) return -1;
+        tau = df_mul_f(Cm, uu);
+        const float band = KRP_EXACT_BAND * cf;
+        const float coarse = 4e-7f * cf;   // error of the FP32 gap below: a few ulp(C)
+        // traced samples record the masses of the path's nodes (double-float of
+        // the (hi, lo) slots when there are low parts) and each node's mass as
+        // its parent's minus its left sibling's
+        const bool tracing = __any_sync(0xffffffffu, trc != nullptr);
+        df Mx = tracing && tl ? exact_mass(tr, tl) : Cm;
+        if (trc) trc[0] = Mx.hi;
+        constexpr float KAPPA = 9.5367431640625e-7f;   // 2^-20: bound on an FP32 mass's error / |mass|
+        int64_t c = 1;
+        int lvl = 0;
+        df M = Cm;         // mass of node c (top levels)
+        float eM = 0.f;    // bound on its error
+        const int64_t nfull = Ik / F;   // leaves holding F rows
+        // One decision at node c (depth lvl) from the lane partial of its
+        // staged left-child slot: chained (delta slot) above depth Ke, plain
+        // below.  The branch is taken from an FP32 estimate of m(L(c)) unless
+        // the gap is within the estimate's error; the double-float m(L(c))
+        // that the offset and the chain carry forward is formed beside it.
+        auto step = [&](float part) {
+            const float m = warp_sum(part);
+            const bool top = lvl < Ke;
+            float a = 0.5f;   // alpha_c: 1/2 unless c holds the rows' ragged end
+            if (top && (c - ((int64_t)1 << lvl) + 1) > (nfull >> (depth - lvl))) a = node_alpha(c, lvl, Lk, F, Ik);
+            const float mf = top ? fmaf(a, M.hi, m) : m;
+            float e = top ? fmaf(a, eM, KAPPA * fabsf(m)) : KAPPA * fabsf(m);
+            df mL = top ? df_add_f(a == 0.5f ? df{0.5f * M.hi, 0.5f * M.lo} : df_mul_f(M, a), m) : df{m, 0.f};
+            const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
+            bool left = true;
+            if (rfirst * F < Ik) {
+                const float gapf = (tau.hi - low.hi) - mf;
+                if (!xs && fabsf(gapf) > coarse + band + elow + e) {
+                    left = gapf < 0.f;
+                } else {
+                    if (!tl) mL = refine(part);
+                    df gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
+                    if (tl && !xs && fabsf(gap.hi) <= band + elow + e) {
+                        go_exact(tr, tl, c, lvl, uu, tau, low);
+                        xs = true;
+                        elow = e = 0.f;
+                    }
+                    if (xs) {
+                        mL = exact_mass(tr + c * Tp, tl + c * Tp);
+                        gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
+                    }
+                    left = gap.hi < 0.f || (gap.hi == 0.f && gap.lo <= 0.f);
+                }
+            }
+            if (tracing) {
+                const df mx = tl ? exact_mass(tr + c * Tp, tl + c * Tp) : refine(part);
+                if (trc) {
+                    trc[2 + 2 * lvl] = mx.hi;
+                    trc[3 + 2 * lvl] = Mx.hi;
+                }
+                Mx = left ? mx : df_add(Mx, df_neg(mx));
+            }
+            if (left) {
+                c = 2 * c;
+                if (top) {
+                    M = mL;
+                    eM = e;
+                }
+            } else {
+                c = 2 * c + 1;
+                low = df_add(low, mL);
+                if (top) {
+                    M = df_add(M, df_neg(mL));
+                    eM += e;
+                }
+                elow += e;
+            }
+            ++lvl;
+        };
+        // level 0 from the first fetch, then two levels per fetch (slot c,
+        // then the chosen one of slots 2c, 2c + 1); one call site for step
+        const float* node = stage + Tp;
+        bool staged = true;   // node holds this level's slot
+        while (lvl < depth && alive) {
+            bool have_next = false;
+            if (!staged) {
+                have_next = lvl + 2 <= depth;
+                const float* a = (lvl < Ke ? dt : tr) + c * Tp;
+                const float* b = have_next ? (lvl + 1 < Ke ? dt : tr) + 2 * c * Tp : nullptr;
+                if (!fetch(a, Tp * 4, b, have_next ? 2 * Tp * 4 : 0)) break;
+                node = stage;
+            }
+            const int64_t c0 = c;
+            step(partial(node));
+            staged = have_next;
+            if (have_next) node = stage + (c == 2 * c0 ? Tp : 2 * Tp);
+        }
+        return c;
+    };
+
     const bool leaf_tma = (R & 3) == 0 && P.F * R <= C::STAGE;
     const int64_t warps_total = ncta * C::WARPS;
     for (int64_t s = cta * C::WARPS + warp; s < P.J && alive; s += warps_total) {
@@ -285,13 +534,17 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
             float cf = 0.f, margin = 0.f;
             int64_t c = 1;
             int u = 0;
+            bool xs = false;    // exact-decision mode: the row stage switched to exact masses
+            float elow = 0.f;   // exact-decision mode: bound on the FP32 path's error in low
             for (int sg = 0; sg < 2; ++sg) {
+                const bool xrow = EXACT && sg == 1;
                 const float* tr = sg ? P.tree[k] : P.etree[k];
                 const int depth = sg ? P.depth[k] : P.dE;
-                // issue the first fetch (root and levels 0-1), then build the
-                // stage's weights while it is in flight
+                // issue the first fetch (root and levels 0-1; in the exact row
+                // stage the root and D_1), then build the stage's weights while
+                // it is in flight
                 const int nfirst = depth >= 1 ? 2 : 1;
-                fetch_issue(tr, (uint32_t)(nfirst * Tp * 4), nullptr, 0);
+                fetch_issue(xrow ? P.dtop[k] : tr, (uint32_t)(nfirst * Tp * 4), nullptr, 0);
                 if (sg == 0) {
                     if (lane < RMAX) th[lane] = hh[lane] + hl[lane];
                 } else if (lane < RMAX) {
@@ -301,14 +554,20 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                         vl = __ldg(P.Vlo[k] + (size_t)u * R + lane);
                     }
                     const df t = df_add(df_mul_f(df{hh[lane], hl[lane]}, vh), df_mul_f(df{hh[lane], hl[lane]}, vl));
-                    th[lane] = t.hi + t.lo;   // h̃ = h ∘ V[:,u], rounded once
+                    th[lane] = t.hi;   // h̃ = h ∘ V[:,u], rounded once (t is normalised)
+                    thl[lane] = t.lo;
                 }
                 __syncwarp();
                 make_weights(th);
                 if (trc && sg) trc += FAST_TRACE_STRIDE;
                 df Cm;
-                c = descend(tr, depth, sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, Cm,
-                            tau, low, trc);
+                if (EXACT)
+                    c = descend_exact(tr, sg ? P.tlo[k] : nullptr, xrow ? P.dtop[k] : tr, depth, sg ? P.Ke[k] : 0,
+                                      sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, Cm, tau, low,
+                                      xs, elow, trc);
+                else
+                    c = descend(tr, depth, sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, Cm,
+                                tau, low, trc);
                 if (!alive) break;
                 if (c < 0) {
                     const float cv = Cm.hi + Cm.lo;
@@ -366,6 +625,13 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
             if (lane == 0) cum = 0.f;
             int first = 0x7fffffff, lastpos = -1;
             bool near = false;
+            if (EXACT) {
+                // low's FP32-path error and the FP32 scan's own: each row weight
+                // is a squared R-term dot product (~R 2^-24 of the row's |terms|
+                // relative), then ~10 roundings of the running sums; 2^-14 of
+                // the leaf's total covers both
+                margin = KRP_EXACT_BAND * cf + elow + 6.103515625e-5f * __shfl_sync(0xffffffffu, inc, 31);
+            }
 #pragma unroll
             for (int r = 0; r < C::RPT; ++r) {
                 const int t = lane * rpt + r;
@@ -376,7 +642,18 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                     if (q[r] > 0.f) lastpos = t;
                 }
             }
-            if (__any_sync(0xffffffffu, near)) {
+            if (EXACT && __any_sync(0xffffffffu, near)) {
+                // re-take the leaf scan from the exact offset and rows rescored
+                // in double-float: q = (U[t] · h̃)^2 with h̃ = (th, thl)
+                if (!xs) {
+                    go_exact(P.tree[k], P.tlo[k], c, P.depth[k], u_row, tau, low);
+                    xs = true;
+                }
+                const int2 fl = exact_leaf_scan<C::RPT>(leaf_tma ? stage : Uk + row0 * R, R, rpt, nrows, th, thl,
+                                                       tau, low);
+                first = fl.x;
+                lastpos = fl.y;
+            } else if (__any_sync(0xffffffffu, near)) {
                 // redo the scan in double-float: edges low + cumulative weights
                 df acc{0.f, 0.f};
 #pragma unroll
@@ -462,25 +739,29 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
 // Four CTAs (32 samples) per SM where the registers allow it without spills
 // (RMAX <= 16: 63 registers); at RMAX = 32 a 64-register cap spills and the
 // draw slows from 1.24 to 1.34 ms, so three.
-template <int RMAX>
+template <int RMAX, bool EXACT>
 __global__ void __launch_bounds__(256, RMAX <= 16 ? 4 : 3) krp_descent_fast(const __grid_constant__ FastParams P) {
-    descent_fast_body<RMAX>(P, blockIdx.x, gridDim.x);
+    descent_fast_body<RMAX, EXACT>(P, blockIdx.x, gridDim.x);
 }
 
 namespace {
-template <int RMAX>
+template <int RMAX, bool EXACT>
 cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
     using C = FastCfg<RMAX>;
-    cudaFuncSetAttribute(krp_descent_fast<RMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
-    cudaFuncSetAttribute(krp_descent_fast<RMAX>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                         cudaSharedmemCarveoutMaxShared);
+    auto k = krp_descent_fast<RMAX, EXACT>;
+    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, krp_descent_fast<RMAX>, 256, C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, C::SMEM);
     per_sm = per_sm > 0 ? per_sm : 1;
     const int64_t need = (P.J + 7) / 8;
     const int64_t grid = need < (int64_t)num_sms * per_sm ? need : (int64_t)num_sms * per_sm;
-    krp_descent_fast<RMAX><<<(unsigned)grid, 256, C::SMEM, st>>>(P); count_launch();
+    k<<<(unsigned)grid, 256, C::SMEM, st>>>(P); count_launch();
     return cudaGetLastError();
+}
+template <int RMAX>
+cudaError_t launch_fast_r(const FastParams& P, bool exact, int num_sms, cudaStream_t st) {
+    return exact ? launch_fast_t<RMAX, true>(P, num_sms, st) : launch_fast_t<RMAX, false>(P, num_sms, st);
 }
 }  // namespace
 
@@ -510,6 +791,11 @@ void fast_params_for(const krp_sampler* s, int exclude_j, FastParams* out) {
     for (int k = 0; k < s->N; ++k) {
         P.U[k] = s->U[k];
         P.tree[k] = s->tree[k];
+        if (s->exact) {
+            P.tlo[k] = s->tree_lo[k];
+            P.dtop[k] = s->dtop[k];
+            P.Ke[k] = s->Ke[k];
+        }
         P.etree[k] = s->etree + (size_t)k * s->Rp * s->Tp;
         P.Vhi[k] = s->V32 + (size_t)k * s->R * s->R;
         P.Vlo[k] = s->V32lo + (size_t)k * s->R * s->R;
@@ -544,12 +830,14 @@ bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
     P.SA = SA;
     P.trace = trace;
     P.n_trace = trace ? n_trace : 0;
+    P.nexact = s->exact ? s->nexact : nullptr;
+    const bool x = s->exact != 0;
     if (s->R <= 8)
-        *err = launch_fast_t<8>(P, s->num_sms, s->stream);
+        *err = launch_fast_r<8>(P, x, s->num_sms, s->stream);
     else if (s->R <= 16)
-        *err = launch_fast_t<16>(P, s->num_sms, s->stream);
+        *err = launch_fast_r<16>(P, x, s->num_sms, s->stream);
     else
-        *err = launch_fast_t<32>(P, s->num_sms, s->stream);
+        *err = launch_fast_r<32>(P, x, s->num_sms, s->stream);
     return true;
 }
 

@@ -22,6 +22,13 @@ struct krp_sampler {
     std::vector<float*> tree;   // L_k slots x Tp
     std::vector<double*> root64;  // FP64 root Gram G_k (packed upper, Tp) per factor
     std::vector<char> has_factor;
+    // exact-decision mode (KRP_PREC_EXACT): every tree slot's low part, and the
+    // delta-encoded top levels [root | D_1 .. D_{2^Ke - 1}] (the tree's slot numbering)
+    int exact = 0;
+    std::vector<float*> tree_lo;  // L_k slots x Tp
+    std::vector<float*> dtop;     // 2^Ke_k slots x Tp
+    std::vector<int> Ke;          // delta-encoded levels: min(KRP_EXACT_TOP, depth_k)
+    unsigned long long* nexact = nullptr;  // device count of exact re-decisions (row stages)
     // per-draw sampler state (written by the prep kernels)
     double* G64 = nullptr;      // N x R x R : FP64 copies of the root Grams
     double* Gplus64 = nullptr;  // R x R
@@ -46,6 +53,7 @@ struct krp_sampler {
     float* als_w = nullptr;
     float* als_SA = nullptr;
     double* als_sumsq = nullptr;
+    double* als_part = nullptr;   // per-CTA partial sums (column norms, fit), summed in a fixed order
     int64_t als_J = 0;
     std::string last_error;
     int last_exclude = -2;      // exclude_j of the last prep (for inspection)
@@ -72,15 +80,27 @@ struct krp_sptensor {
     double normT2 = 0.0;               // ||T||_F^2 (host, FP64)
     float* Y = nullptr;                // scratch: max I_j x R
     size_t Y_floats = 0;
-    // lookup scratch: per sample its fiber; a hash table of H >= 2J slots (fiber
-    // key, summed w_s SA[s, :]); per slot the fiber's start, length and their scan
-    int64_t* lk_fiber = nullptr;
-    unsigned long long* lk_keys = nullptr;
-    int64_t* lk_begin = nullptr;
-    int64_t* lk_len = nullptr;
-    int64_t* lk_scan = nullptr;
-    float* lk_acc = nullptr;
-    size_t lk_n = 0, lk_acc_n = 0;
+    // per mode, the fibers' lengths as (length, count) pairs, longest first:
+    // the longest J fibers bound the (fiber, nonzero) pairs a J-sample solve reads
+    std::vector<std::vector<std::pair<int64_t, int64_t>>> len_hist;
+    // lookup scratch of the deterministic solve (sized for lk_J samples and
+    // lk_pairs pairs): the samples sorted by fiber; per distinct sampled fiber
+    // its run of samples, fiber id, summed w_s SA[s, :] and the scan of the
+    // fiber lengths; the (fiber, nonzero) pairs sorted by mode-j row
+    uint32_t* sk[2] = {nullptr, nullptr};
+    uint32_t* sv[2] = {nullptr, nullptr};
+    uint32_t* flag = nullptr;    // J + 1
+    int64_t* useg = nullptr;     // 2 J
+    int64_t* ufib = nullptr;     // J
+    int64_t* poff = nullptr;     // J + 1
+    int64_t* cnt = nullptr;      // distinct sampled fibers, pairs
+    float* uacc = nullptr;       // J x R
+    uint32_t* pk[2] = {nullptr, nullptr};
+    uint32_t* pv[2] = {nullptr, nullptr};
+    uint32_t* pu = nullptr;      // per pair: distinct-fiber index
+    uint32_t* pn = nullptr;      // per pair: nonzero (fiber order)
+    uint32_t* hist = nullptr;
+    size_t lk_J = 0, lk_pairs = 0, lk_hist = 0, lk_R = 0;
 };
 
 namespace krp {
@@ -93,6 +113,7 @@ struct PrepParams {
     const double* roots[16];  // FP64 root Gram G_k of each factor (packed upper)
     int incl[16];             // included factors, ascending
     int n_incl;
+    int extra_refine;         // eigen-refinement steps beyond the first (samplers: 1; batches: 0)
 };
 
 struct PrepItem {  // everything prep_pinv / prep_eig read and write for one problem
@@ -114,6 +135,9 @@ struct PrepItem {  // everything prep_pinv / prep_eig read and write for one pro
 struct FastParams {  // the R <= 32 descent of one problem
     const float* U[16];
     const float* tree[16];
+    const float* tlo[16];     // exact-decision mode: tree low parts
+    const float* dtop[16];    // exact-decision mode: delta-encoded top levels
+    int Ke[16];               // exact-decision mode: delta-encoded levels
     const float* etree[16];
     const float* Vhi[16];
     const float* Vlo[16];
@@ -134,6 +158,7 @@ struct FastParams {  // the R <= 32 descent of one problem
     float* SA;
     float* trace;
     int64_t n_trace;
+    unsigned long long* nexact;   // exact-decision mode: count of exact re-decisions (may be null)
 };
 
 struct FastCall {  // per-call arguments of the batched descent
@@ -189,8 +214,11 @@ void count_launch();
 int64_t launch_counter();
 krp_status cuda_check(krp_sampler* s, cudaError_t e, const char* what);
 
-// a1: build factor j's segment tree from s->U[j] (FP32 or BF16x3 Grams).
+// a1: build factor j's segment tree from s->U[j] (FP32 or BF16x3 Grams; exact
+// leaves and low parts in an exact-decision sampler).
 krp_status build_tree(krp_sampler* s, int j, int precision, const float* src = nullptr);
+// The delta-encoded top of factor j's tree from its (hi, lo) slots (exact mode).
+cudaError_t launch_build_dtop(const krp_sampler* s, int j, cudaStream_t st);
 // a2 + a3: G, G⁺, G_{>k}, eigendecompositions, E_k trees for the given exclusion.
 krp_status sampler_prep(krp_sampler* s, int exclude_j);
 // a4 + a5 (+a6 fused): the batched conditional descent.

@@ -61,6 +61,9 @@ int log2i(int64_t p) {
 namespace krp {
 krp_status als_buffers(krp_sampler* s, int64_t J, int32_t** idx, float** w, float** SA, double** sumsq) {
     if (!s->als_sumsq && !dalloc(&s->als_sumsq, 2 * 128 + 8)) return fail(s, KRP_ENOMEM, "ALS scratch allocation failed");
+    // per-CTA partials: 2 CTAs per SM x 128 columns (Y M⁻¹), 8 CTAs per SM (fit)
+    if (!s->als_part && !dalloc(&s->als_part, (size_t)s->num_sms * 2 * 128 + (size_t)s->num_sms * 8))
+        return fail(s, KRP_ENOMEM, "ALS scratch allocation failed");
     if (J > s->als_J) {
         cudaFree(s->als_idx);
         cudaFree(s->als_w);
@@ -93,6 +96,8 @@ void krp_destroy(krp_sampler* s) {
     if (s->graph) cudaGraphDestroy(s->graph);
     for (float* p : s->U) cudaFree(p);
     for (float* p : s->tree) cudaFree(p);
+    for (float* p : s->tree_lo) cudaFree(p);
+    for (float* p : s->dtop) cudaFree(p);
     for (double* p : s->root64) cudaFree(p);
     cudaFree(s->G64);
     cudaFree(s->Gplus64);
@@ -105,6 +110,7 @@ void krp_destroy(krp_sampler* s) {
     cudaFree(s->V32lo);
     cudaFree(s->rank_dev);
     cudaFree(s->status);
+    cudaFree(s->nexact);
     cudaFree(s->build_scratch);
     cudaFree(s->solve_scratch);
     cudaFree(s->solve64);
@@ -112,6 +118,7 @@ void krp_destroy(krp_sampler* s) {
     cudaFree(s->als_w);
     cudaFree(s->als_SA);
     cudaFree(s->als_sumsq);
+    cudaFree(s->als_part);
     delete s;
 }
 
@@ -127,9 +134,12 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     for (int k = 0; k < N; ++k)
         if (I_host[k] < 1 || I_host[k] >= ((int64_t)1 << 31))
             return fail(nullptr, KRP_EINVAL, "krp_create: need 1 <= I_k < 2^31");
-    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3)
+    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3 && precision != KRP_PREC_EXACT)
         return fail(nullptr, KRP_EINVAL, "krp_create: unknown precision");
+    if (precision == KRP_PREC_EXACT && R > 32)
+        return fail(nullptr, KRP_EINVAL, "krp_create: the exact-decision mode needs R <= 32");
     krp_sampler* s = new krp_sampler();
+    s->exact = precision == KRP_PREC_EXACT ? 1 : 0;
     s->N = N;
     s->R = R;
     s->F = F;
@@ -152,6 +162,9 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     s->U.assign(N, nullptr);
     s->tree.assign(N, nullptr);
     s->root64.assign(N, nullptr);
+    s->tree_lo.assign(N, nullptr);
+    s->dtop.assign(N, nullptr);
+    s->Ke.assign(N, 0);
     s->has_factor.assign(N, 0);
     bool ok = true;
     for (int k = 0; k < N && ok; ++k) {
@@ -161,6 +174,13 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
         ok = dalloc(&s->U[k], (size_t)s->I[k] * R) && dalloc(&s->tree[k], (size_t)s->L[k] * s->Tp) &&
              dalloc(&s->root64[k], (size_t)s->Tp);
         if (ok) ok = cudaMemsetAsync(s->tree[k], 0, (size_t)s->L[k] * s->Tp * 4, s->stream) == cudaSuccess;
+        if (ok && s->exact) {
+            s->Ke[k] = std::min(KRP_EXACT_TOP, s->depth[k]);
+            const size_t nd = ((size_t)1 << s->Ke[k]) * s->Tp;
+            ok = dalloc(&s->tree_lo[k], (size_t)s->L[k] * s->Tp) && dalloc(&s->dtop[k], nd);
+            if (ok) ok = cudaMemsetAsync(s->tree_lo[k], 0, (size_t)s->L[k] * s->Tp * 4, s->stream) == cudaSuccess;
+            if (ok) ok = cudaMemsetAsync(s->dtop[k], 0, nd * 4, s->stream) == cudaSuccess;
+        }
     }
     const size_t RR = (size_t)R * R;
     ok = ok && dalloc(&s->G64, N * RR) && dalloc(&s->Gplus64, RR) && dalloc(&s->lam64, (size_t)N * R) &&
@@ -169,6 +189,8 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
          dalloc(&s->V32, N * RR) && dalloc(&s->V32lo, N * RR) && dalloc(&s->rank_dev, 2) && dalloc(&s->status, 1) &&
          dalloc(&s->solve64, 3 * RR + 128 * (size_t)R);
     if (ok) ok = cudaMemsetAsync(s->status, 0, sizeof(int), s->stream) == cudaSuccess;
+    if (ok && s->exact) ok = dalloc(&s->nexact, 1) &&
+                             cudaMemsetAsync(s->nexact, 0, sizeof(unsigned long long), s->stream) == cudaSuccess;
     if (ok) ok = cudaMemsetAsync(s->etree, 0, (size_t)N * s->Rp * s->Tp * 4, s->stream) == cudaSuccess;
     if (ok) ok = cudaStreamSynchronize(s->stream) == cudaSuccess;
     if (!ok) {
@@ -182,8 +204,10 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
 krp_status krp_set_factor_prec(krp_sampler* s, int j, const float* U, int precision) {
     if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");
     if (j < 0 || j >= s->N || !U) return fail(s, KRP_EINVAL, "krp_set_factor: bad factor index or NULL U");
-    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3)
+    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3 && precision != KRP_PREC_EXACT)
         return fail(s, KRP_EINVAL, "krp_set_factor: unknown precision");
+    if (precision == KRP_PREC_EXACT && !s->exact)
+        return fail(s, KRP_EINVAL, "krp_set_factor: KRP_PREC_EXACT needs a sampler created with it");
     // Device-resident rows are read once by the build, which also writes the
     // sampler's copy; host rows are copied first.
     cudaPointerAttributes attr{};
@@ -309,6 +333,18 @@ krp_status krp_sync_status(krp_sampler* s) {
 
 int64_t krp_launch_count(void) { return krp::launch_counter(); }
 
+krp_status krp_exact_count(krp_sampler* s, int64_t* count_host) {
+    if (!s || !count_host) return fail(s, KRP_EINVAL, "krp_exact_count: NULL sampler or output");
+    *count_host = 0;
+    if (!s->exact) return KRP_OK;
+    unsigned long long n = 0;
+    cudaError_t e = cudaStreamSynchronize(s->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(&n, s->nexact, sizeof(n), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_check(s, e, "krp_exact_count");
+    *count_host = (int64_t)n;
+    return KRP_OK;
+}
+
 krp_status krp_capture_begin(krp_sampler* s) {
     if (!s) return fail(nullptr, KRP_EINVAL, "krp_capture_begin: NULL sampler");
     if (s->capturing) return fail(s, KRP_ESTATE, "krp_capture_begin: already capturing");
@@ -364,6 +400,18 @@ krp_status krp_get_tree(const krp_sampler* s, int j, float* out_host, int64_t n_
     if (n_floats < n) return KRP_EINVAL;
     if (cudaStreamSynchronize(s->stream) != cudaSuccess) return KRP_ECUDA;
     return cudaMemcpy(out_host, s->tree[j], n * 4, cudaMemcpyDeviceToHost) == cudaSuccess ? KRP_OK : KRP_ECUDA;
+}
+
+krp_status krp_get_tree_exact(const krp_sampler* s, int j, float* lo_host, int64_t n_lo, float* dtop_host,
+                              int64_t n_dtop) {
+    if (!s || j < 0 || j >= s->N || !s->exact) return KRP_EINVAL;
+    const int64_t nl = s->L[j] * s->Tp, nd = ((int64_t)1 << s->Ke[j]) * s->Tp;
+    if ((lo_host && n_lo < nl) || (dtop_host && n_dtop < nd)) return KRP_EINVAL;
+    if (cudaStreamSynchronize(s->stream) != cudaSuccess) return KRP_ECUDA;
+    if (lo_host && cudaMemcpy(lo_host, s->tree_lo[j], nl * 4, cudaMemcpyDeviceToHost) != cudaSuccess) return KRP_ECUDA;
+    if (dtop_host && cudaMemcpy(dtop_host, s->dtop[j], nd * 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return KRP_ECUDA;
+    return KRP_OK;
 }
 
 krp_status krp_get_factor(const krp_sampler* s, int j, float* out_host, int64_t n_floats) {

@@ -14,8 +14,6 @@
 #include "common.cuh"
 #include "internal.h"
 
-#include <mutex>
-
 namespace krp {
 
 // kernels defined in solve.cu
@@ -42,28 +40,17 @@ constexpr int NA_MAX_OUT = NA_MAX_R * (NA_MAX_R + 1) / 2 + NA_MAX_R * NA_MAX_NRH
 // initial value.
 static __device__ __align__(256) float g_krp_noalloc_scratch[NA_MAX_PARTS * NA_MAX_OUT + NA_MAX_PARTS];
 
-// Device address of the scratch, resolved once per device (the symbol's name
-// is only a host-side stand-in and must not be passed to a kernel).
-std::mutex g_mu;
-float* g_scratch[64] = {};
-
-float* scratch_for(int dev, cudaError_t* err) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (dev < 0 || dev >= 64) {
-        *err = cudaErrorInvalidDevice;
-        return nullptr;
-    }
-    if (!g_scratch[dev]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_krp_noalloc_scratch);
-        if (e != cudaSuccess) {
-            *err = e;
-            return nullptr;
-        }
-        g_scratch[dev] = static_cast<float*>(p);
-    }
-    *err = cudaSuccess;
-    return g_scratch[dev];
+// Device address of the scratch in the current device's context (the
+// symbol's name is only a host-side stand-in and must not be passed to a
+// kernel).  Looked up on every call: the address is fixed within a context,
+// but a context made after cudaDeviceReset, or another context on the same
+// device, may hold the library's device code elsewhere, so no address is
+// kept between calls.  After the first lookup in a context (which may load
+// the device code) a lookup is a host-side table read.
+float* scratch_for(cudaError_t* err) {
+    void* p = nullptr;
+    *err = cudaGetSymbolAddress(&p, g_krp_noalloc_scratch);
+    return *err == cudaSuccess ? static_cast<float*>(p) : nullptr;
 }
 
 }  // namespace
@@ -83,7 +70,7 @@ extern "C" krp_status krp_solve_dense_noalloc(int64_t J, int R, const float* SA,
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return fail(nullptr, KRP_ECUDA, std::string("krp_solve_dense_noalloc: ") + cudaGetErrorString(e));
-    float* base = scratch_for(dev, &e);
+    float* base = scratch_for(&e);
     if (!base) return fail(nullptr, KRP_ECUDA, std::string("krp_solve_dense_noalloc: scratch address: ") +
                                                    cudaGetErrorString(e));
     float* part = base;

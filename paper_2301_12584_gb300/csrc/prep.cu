@@ -90,66 +90,71 @@ __device__ double eig_fp32_start(const double* __restrict__ A, int n, double* __
     return scale;
 }
 
+// steps: refinement steps (each roughly squares the eigenvectors' error, down to
+// FP64 rounding over the eigenvalue gaps).
 __device__ void eig_fp32_refined(const double* __restrict__ A, int n, double* __restrict__ X, double* __restrict__ lam,
-                                 EigWork w) {
+                                 EigWork w, int steps = 1) {
     const int nn = n * n;
     const double scale = eig_fp32_start(A, n, X, w);
-    // Rm = I - XᵀX ; T = As X
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        double r = (i == j) ? 1.0 : 0.0, t = 0.0;
-        for (int k = 0; k < n; ++k) {
-            r -= X[k * n + i] * X[k * n + j];
-            t += w.As[i * n + k] * X[k * n + j];
+    for (int step = 0; step < steps; ++step) {
+        // Rm = I - XᵀX ; T = As X
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            double r = (i == j) ? 1.0 : 0.0, t = 0.0;
+            for (int k = 0; k < n; ++k) {
+                r -= X[k * n + i] * X[k * n + j];
+                t += w.As[i * n + k] * X[k * n + j];
+            }
+            w.Rm[e] = r;
+            w.T[e] = t;
         }
-        w.Rm[e] = r;
-        w.T[e] = t;
+        __syncthreads();
+        // S = Xᵀ T
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            double acc = 0.0;
+            for (int k = 0; k < n; ++k) acc += X[k * n + i] * w.T[k * n + j];
+            w.S[e] = acc;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = w.S[i * n + i] / (1.0 - w.Rm[i * n + i]);
+        __syncthreads();
+        double off = 0.0, an = 0.0, rn = 0.0;
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            const double sd = w.S[e] - (i == j ? lam[i] : 0.0);
+            off += sd * sd;
+            an += w.As[e] * w.As[e];
+            rn += w.Rm[e] * w.Rm[e];
+        }
+        off = block_sum(off, w.red);
+        an = block_sum(an, w.red);
+        rn = block_sum(rn, w.red);
+        const double delta = 2.0 * (sqrt(off) + sqrt(an) * sqrt(rn));
+        // E into T
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            double E;
+            if (i == j)
+                E = 0.5 * w.Rm[e];
+            else if (fabs(lam[i] - lam[j]) > delta)
+                E = (w.S[e] + lam[j] * w.Rm[e]) / (lam[j] - lam[i]);
+            else
+                E = 0.5 * w.Rm[e];
+            w.T[e] = E;
+        }
+        __syncthreads();
+        // X <- X + X E (into S, then copy)
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) {
+            const int i = e / n, j = e % n;
+            double acc = X[e];
+            for (int k = 0; k < n; ++k) acc += X[i * n + k] * w.T[k * n + j];
+            w.S[e] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < nn; e += blockDim.x) X[e] = w.S[e];
+        __syncthreads();
     }
-    __syncthreads();
-    // S = Xᵀ T
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        double acc = 0.0;
-        for (int k = 0; k < n; ++k) acc += X[k * n + i] * w.T[k * n + j];
-        w.S[e] = acc;
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] = w.S[i * n + i] / (1.0 - w.Rm[i * n + i]);
-    __syncthreads();
-    double off = 0.0, an = 0.0, rn = 0.0;
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        const double sd = w.S[e] - (i == j ? lam[i] : 0.0);
-        off += sd * sd;
-        an += w.As[e] * w.As[e];
-        rn += w.Rm[e] * w.Rm[e];
-    }
-    off = block_sum(off, w.red);
-    an = block_sum(an, w.red);
-    rn = block_sum(rn, w.red);
-    const double delta = 2.0 * (sqrt(off) + sqrt(an) * sqrt(rn));
-    // E into T
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        double E;
-        if (i == j)
-            E = 0.5 * w.Rm[e];
-        else if (fabs(lam[i] - lam[j]) > delta)
-            E = (w.S[e] + lam[j] * w.Rm[e]) / (lam[j] - lam[i]);
-        else
-            E = 0.5 * w.Rm[e];
-        w.T[e] = E;
-    }
-    __syncthreads();
-    // X <- X + X E (into S, then copy)
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) {
-        const int i = e / n, j = e % n;
-        double acc = X[e];
-        for (int k = 0; k < n; ++k) acc += X[i * n + k] * w.T[k * n + j];
-        w.S[e] = acc;
-    }
-    __syncthreads();
-    for (int e = threadIdx.x; e < nn; e += blockDim.x) X[e] = w.S[e];
     for (int i = threadIdx.x; i < n; i += blockDim.x) lam[i] *= scale;
     __syncthreads();
 }
@@ -413,7 +418,7 @@ __device__ __forceinline__ void prep_eig_body(const PrepParams& P, int N, int R,
         if (threadIdx.x == 0) scales[p] = scale;
         return;
     }
-    eig_fp32_refined(A64, R, X, lam, w);
+    eig_fp32_refined(A64, R, X, lam, w, 1 + P.extra_refine);
     eig_output(k, R, X, lam, pos, lam64, V64, V32, V32lo);
 }
 
@@ -666,6 +671,11 @@ krp_status sampler_prep(krp_sampler* s, int exclude_j) {
     const int R = s->R, N = s->N;
     PrepParams P{};
     P.n_incl = 0;
+    // a second refinement step takes the eigenvectors to FP64 rounding over
+    // the eigenvalue gaps (one step leaves ~1e-8 where the gaps are ~1e-4 of
+    // lambda_max, enough to move the eigencomponent stage's branch
+    // probabilities by ~1e-4)
+    P.extra_refine = 1;
     for (int k = 0; k < N; ++k) {
         P.roots[k] = s->root64[k];
         if (k != exclude_j) P.incl[P.n_incl++] = k;

@@ -1,4 +1,4 @@
-// a7 + a8 (sparse) + a9: sampled-fiber lookup, scatter SpMM, Y M⁻¹, column
+// a7 + a8 (sparse) + a9: sampled-fiber lookup, SBᵀSA, Y M⁻¹, column
 // normalisation, and the STS-CP sweep (Sec. 3.3; Alg. 6; App. A.9; fit of
 // Sec. 4.3).
 //
@@ -6,16 +6,20 @@
 // nonzero gets the key packing its coordinates in the modes k != j (ascending
 // k, ceil(log2 I_k) bits each); nonzeros are sorted by key, equal keys form a
 // mode-j fiber (one row of mat(T, j)ᵀ restricted to its nonzeros).
-// Lookup: a thread per sampled tuple binary-searches its key among the fiber
-// keys.  Samples of the same fiber are then merged (their contributions
-// differ only in the sketched row, so Σ_s w_s SA[s, :] per fiber is formed
-// first, in a hash table keyed by the fiber, with H >= 2J slots); an
-// exclusive scan of the merged fibers' lengths numbers the (fiber, nonzero)
-// pairs, and warps take equal runs of those pairs, adding
-// Y[i_j, :] += v · (Σ_s w_s SA[s, :])  (Y = SBᵀ SA, I_j x R) for each
-// nonzero (i_j, v).  Repeated Zipf-hot fibers are so scattered once, and
-// fibers of very different lengths spread over all warps.
-// Then U_j = Y M⁻¹ with M = SAᵀ SA (FP64 Cholesky inverse, applied in FP32).
+//
+// Solve, with every sum taken in a fixed order (the result does not depend on
+// scheduling, so a sweep and its CUDA-graph replay are bit-identical):
+//   1. a thread per sampled tuple binary-searches its key among the fiber keys;
+//   2. the samples are sorted by fiber id (stable radix sort, radix_sort.cu):
+//      samples of one fiber differ only in their sketched row, so each
+//      distinct sampled fiber u gets acc_u = Σ_s w_s SA[s, :] over its run of
+//      samples, in sample order (a warp per fiber);
+//   3. its (fiber, nonzero) pairs are numbered by a scan of the fibers'
+//      lengths and sorted by the nonzero's mode-j row;
+//   4. a warp per row run forms Y[i_j, :] = Σ v acc_u over the run, in order,
+//      and stores it (Y = SBᵀ SA, I_j x R; untouched rows stay zero);
+//   5. U_j = Y M⁻¹ with M = SAᵀ SA (FP64 Cholesky inverse, applied in FP32),
+//      the column sums of squares as per-CTA partials summed in CTA order.
 #include "common.cuh"
 #include "internal.h"
 
@@ -23,9 +27,17 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <vector>
 
 namespace krp {
+
+// radix_sort.cu
+size_t radix_sort_hist_words(int64_t n);
+cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t* v1, uint32_t* hist, int64_t n,
+                             const int64_t* n_dev, int bits, int grid, bool* in_work, cudaStream_t st);
+cudaError_t exclusive_scan_u32(uint32_t* a, int64_t n, cudaStream_t st);
+cudaError_t exclusive_scan_i64(int64_t* a, const int64_t* n_dev, int64_t* total, cudaStream_t st);
 
 struct LookupParams {
     const uint64_t* fkeys;
@@ -41,140 +53,151 @@ struct LookupParams {
     const float* SA;     // J x R
     int64_t J;
     int R;
-    float* Y;            // I_j x RS, RS = R rounded up to 4 (columns >= R unused)
+    float* Y;            // I_j x RS, RS = R rounded up to 4 (columns >= R stay zero)
     int RS;
 };
 
-__global__ void __launch_bounds__(256) fiber_find(LookupParams P, int64_t* __restrict__ fiber) {
+// Step 1: per sample, its fiber id (nfib when the tuple has no nonzero) as a
+// sort key, and its index as the value.
+__global__ void __launch_bounds__(256) fiber_find(LookupParams P, uint32_t* __restrict__ key,
+                                                  uint32_t* __restrict__ val) {
     for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < P.J; s += (int64_t)gridDim.x * blockDim.x) {
-        uint64_t key = 0;
+        uint64_t k = 0;
         for (int q = 0; q < P.n_other; ++q)
-            key = (key << P.kbits[q]) | (uint64_t)(uint32_t)P.idx[(int64_t)P.other[q] * P.J + s];
+            k = (k << P.kbits[q]) | (uint64_t)(uint32_t)P.idx[(int64_t)P.other[q] * P.J + s];
         int64_t lo = 0, hi = P.nfib;  // lower_bound over the sorted fiber keys
         while (lo < hi) {
             const int64_t mid = (lo + hi) >> 1;
-            if (__ldg(P.fkeys + mid) < key)
+            if (__ldg(P.fkeys + mid) < k)
                 lo = mid + 1;
             else
                 hi = mid;
         }
-        fiber[s] = (lo < P.nfib && __ldg(P.fkeys + lo) == key) ? lo : -1;  // -1: the SB row is zero
+        key[s] = (uint32_t)((lo < P.nfib && __ldg(P.fkeys + lo) == k) ? lo : P.nfib);
+        val[s] = (uint32_t)s;
     }
 }
 
-constexpr unsigned long long SLOT_EMPTY = ~0ull;
+// Step 2a: run heads of the sorted fiber ids (flag 1 at the first sample of
+// each distinct sampled fiber), to be scanned into distinct-fiber numbers.
+__global__ void __launch_bounds__(256) run_heads(const uint32_t* __restrict__ key, int64_t J, uint32_t nfib,
+                                                 uint32_t* __restrict__ flag) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p <= J; p += (int64_t)gridDim.x * blockDim.x)
+        flag[p] = p < J && key[p] != nfib && (p == 0 || key[p] != key[p - 1]) ? 1u : 0u;
+}
 
-// A warp per sample: find (or claim) the fiber's slot by linear probing, then
-// add w_s SA[s, :] to the slot's R-vector.
-__global__ void __launch_bounds__(256) merge_samples(LookupParams P, const int64_t* __restrict__ fiber,
-                                                     unsigned long long* __restrict__ keys, float* __restrict__ acc,
-                                                     int log2H) {
-    const int lane = threadIdx.x & 31;
-    const int64_t H = (int64_t)1 << log2H;
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t s = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); s < P.J; s += warps) {
-        const int64_t f = fiber[s];
-        if (f < 0) continue;
-        int64_t slot = -1;
-        if (lane == 0) {
-            int64_t h = (int64_t)(((unsigned long long)f * 0x9E3779B97F4A7C15ull) >> (64 - log2H));
-            for (int64_t probe = 0; probe < H; ++probe) {  // H >= 2J: a slot is always found
-                const unsigned long long old = atomicCAS(keys + h, SLOT_EMPTY, (unsigned long long)f);
-                if (old == SLOT_EMPTY || old == (unsigned long long)f) {
-                    slot = h;
-                    break;
-                }
-                h = (h + 1) & (H - 1);
-            }
+// Step 2b: with scan = the exclusive scan of the head flags, distinct fiber
+// u = (heads before p) owns positions useg[2u] .. useg[2u + 1] - 1; its fiber
+// id and length (poff[u], scanned next); cnt[0] = the number of distinct fibers.
+__global__ void __launch_bounds__(256) run_segments(const uint32_t* __restrict__ key, int64_t J, uint32_t nfib,
+                                                    const uint32_t* __restrict__ scan,
+                                                    const int64_t* __restrict__ fptr, int64_t* __restrict__ useg,
+                                                    int64_t* __restrict__ ufib, int64_t* __restrict__ poff,
+                                                    int64_t* __restrict__ cnt) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < J; p += (int64_t)gridDim.x * blockDim.x) {
+        if (p == 0) cnt[0] = scan[J];
+        const uint32_t f = key[p];
+        if (f == nfib) continue;
+        const bool head = p == 0 || key[p - 1] != f;
+        const bool tail = p == J - 1 || key[p + 1] != f;
+        const int64_t u = head ? scan[p] : (int64_t)scan[p] - 1;
+        if (head) {
+            useg[2 * u] = p;
+            ufib[u] = f;
+            poff[u] = __ldg(fptr + f + 1) - __ldg(fptr + f);
         }
-        slot = __shfl_sync(0xffffffffu, slot, 0);
-        if (slot < 0) continue;
-        const float ws = __ldg(P.weight + s);
-        for (int a = lane; a < P.R; a += 32) atomicAdd(acc + slot * P.R + a, ws * __ldg(P.SA + s * P.R + a));
+        if (tail) useg[2 * u + 1] = p + 1;
     }
 }
 
-// Per slot: first nonzero and length of its fiber (0 for an empty slot).
-__global__ void __launch_bounds__(256) slot_lengths(LookupParams P, const unsigned long long* __restrict__ keys,
-                                                    int64_t H, int64_t* __restrict__ begin,
-                                                    int64_t* __restrict__ len) {
-    for (int64_t h = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; h < H; h += (int64_t)gridDim.x * blockDim.x) {
-        const unsigned long long f = keys[h];
-        const bool used = f != SLOT_EMPTY;
-        begin[h] = used ? __ldg(P.fptr + f) : 0;
-        len[h] = used ? __ldg(P.fptr + f + 1) - __ldg(P.fptr + f) : 0;
-    }
-}
-
-// Exclusive scan of len[0..n) into scan[0..n] (scan[n] = total), one CTA.
-__global__ void __launch_bounds__(1024) scan_lengths(const int64_t* __restrict__ len, int64_t* __restrict__ scan,
-                                                     int64_t n) {
-    __shared__ int64_t part[1024];
-    const int64_t per = (n + blockDim.x - 1) / blockDim.x;
-    const int64_t a = threadIdx.x * per, b = min(n, a + per);
-    int64_t sum = 0;
-    for (int64_t i = a; i < b; ++i) sum += len[i];
-    part[threadIdx.x] = sum;
-    __syncthreads();
-    for (int off = 1; off < (int)blockDim.x; off <<= 1) {  // inclusive Hillis-Steele scan
-        const int64_t v = threadIdx.x >= (unsigned)off ? part[threadIdx.x - off] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int64_t run = part[threadIdx.x] - sum;
-    for (int64_t i = a; i < b; ++i) {
-        scan[i] = run;
-        run += len[i];
-    }
-    if (threadIdx.x == blockDim.x - 1) scan[n] = part[threadIdx.x];
-}
-
-// Warps take runs of SCATTER_RUN consecutive (slot, nonzero) pairs; lane l
-// adds columns 4l .. 4l+3 of a nonzero's row with one vector atomic (Y rows
-// are RS = R rounded up to 4 floats, 16-byte aligned; the padding columns
-// receive zeros).
-constexpr int SCATTER_RUN = 32;
-
-__global__ void __launch_bounds__(256) fiber_scatter(LookupParams P, const int64_t* __restrict__ begin,
-                                                     const int64_t* __restrict__ scan, int64_t H,
-                                                     const float* __restrict__ acc) {
+// Step 2c: acc_u = Σ w_s SA[s, :] over distinct fiber u's samples in order, a
+// warp per fiber (lanes over columns).
+__global__ void __launch_bounds__(256) fiber_acc(LookupParams P, const uint32_t* __restrict__ sval,
+                                                 const int64_t* __restrict__ useg, const int64_t* __restrict__ cnt,
+                                                 float* __restrict__ acc) {
     const int lane = threadIdx.x & 31;
-    const int64_t total = scan[H];
-    const int64_t nrun = (total + SCATTER_RUN - 1) / SCATTER_RUN;
+    const int64_t U = cnt[0];
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t run = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); run < nrun; run += warps) {
-        const int64_t w0 = run * SCATTER_RUN, w1 = min(total, w0 + SCATTER_RUN);
-        int64_t lo = 0, hi = H - 1;  // last slot with scan[h] <= w0
+    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += warps) {
+        float a[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int64_t p = useg[2 * u]; p < useg[2 * u + 1]; ++p) {
+            const int64_t s = sval[p];
+            const float ws = __ldg(P.weight + s);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (lane + 32 * q < P.R) a[q] = fmaf(ws, __ldg(P.SA + s * P.R + lane + 32 * q), a[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            if (lane + 32 * q < P.R) acc[u * P.R + lane + 32 * q] = a[q];
+    }
+}
+
+// Step 3: pair w (of cnt[1]) belongs to distinct fiber u (poff[u] <= w <
+// poff[u + 1]) and is its nonzero w - poff[u]: key = that nonzero's mode-j
+// row, value = w, and its fiber and nonzero on the side.
+__global__ void __launch_bounds__(256) pair_fill(LookupParams P, const int64_t* __restrict__ ufib,
+                                                 const int64_t* __restrict__ poff, const int64_t* __restrict__ cnt,
+                                                 uint32_t* __restrict__ key, uint32_t* __restrict__ val,
+                                                 uint32_t* __restrict__ pu, uint32_t* __restrict__ pn) {
+    const int64_t U = cnt[0], npairs = cnt[1];
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < npairs; w += (int64_t)gridDim.x * blockDim.x) {
+        int64_t lo = 0, hi = U - 1;   // last u with poff[u] <= w
         while (lo < hi) {
             const int64_t mid = (lo + hi + 1) >> 1;
-            if (__ldg(scan + mid) <= w0)
+            if (poff[mid] <= w)
                 lo = mid;
             else
                 hi = mid - 1;
         }
-        int64_t h = lo;
-        for (int64_t w = w0; w < w1; ++w) {
-            while (__ldg(scan + h + 1) <= w) ++h;
-            const int64_t n = __ldg(begin + h) + (w - __ldg(scan + h));
-            const int64_t ij = __ldg(P.fidx + n);
-            const float v = __ldg(P.fval + n);
-            const float* ah = acc + h * P.R;
-            for (int a = 4 * lane; a < P.R; a += 128) {
-                float4 d;
-                d.x = v * __ldg(ah + a);
-                d.y = a + 1 < P.R ? v * __ldg(ah + a + 1) : 0.f;
-                d.z = a + 2 < P.R ? v * __ldg(ah + a + 2) : 0.f;
-                d.w = a + 3 < P.R ? v * __ldg(ah + a + 3) : 0.f;
-                atomicAdd(reinterpret_cast<float4*>(P.Y + ij * P.RS + a), d);
+        const int64_t n = __ldg(P.fptr + ufib[lo]) + (w - poff[lo]);
+        key[w] = (uint32_t)__ldg(P.fidx + n);
+        val[w] = (uint32_t)w;
+        pu[w] = (uint32_t)lo;
+        pn[w] = (uint32_t)n;
+    }
+}
+
+// Step 4: Y[i, :] = Σ v acc_u over the sorted run of row i's pairs, in order.
+// Warps take chunks of 32 sorted positions and own the runs that start there
+// (a run may extend past the chunk); lanes over columns.
+__global__ void __launch_bounds__(256) row_sums(LookupParams P, const uint32_t* __restrict__ key,
+                                                const uint32_t* __restrict__ val, const uint32_t* __restrict__ pu,
+                                                const uint32_t* __restrict__ pn, const int64_t* __restrict__ cnt,
+                                                const float* __restrict__ acc) {
+    const int lane = threadIdx.x & 31;
+    const int64_t npairs = cnt[1];
+    const int64_t nchunk = (npairs + 31) / 32;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunk; ch += warps) {
+        const int64_t p = ch * 32 + lane;
+        const bool head = p < npairs && (p == 0 || key[p] != key[p - 1]);
+        unsigned heads = __ballot_sync(0xffffffffu, head);
+        while (heads) {
+            const int h = __ffs(heads) - 1;
+            heads &= heads - 1;
+            const int64_t p0 = ch * 32 + h;
+            const uint32_t row = key[p0];
+            float a[4] = {0.f, 0.f, 0.f, 0.f};
+            for (int64_t q = p0; q < npairs && key[q] == row; ++q) {
+                const uint32_t w = val[q];
+                const int64_t u = pu[w];
+                const float v = __ldg(P.fval + pn[w]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    if (lane + 32 * c < P.R) a[c] = fmaf(v, acc[u * P.R + lane + 32 * c], a[c]);
             }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (lane + 32 * c < P.R) P.Y[(int64_t)row * P.RS + lane + 32 * c] = a[c];
         }
     }
 }
 
-// U[i, :] = Y[i, :] M⁻¹ (M⁻¹ FP64 -> FP32 in shared memory) and, when sumsq
-// is non-null, σ²[c] += Σ_i U[i, c]² (double-float partials per thread, one
-// FP64 atomic per column and CTA).  Persistent CTAs walk tiles of TM rows of
+// U[i, :] = Y[i, :] M⁻¹ (M⁻¹ FP64 -> FP32 in shared memory) and, when part
+// is non-null, the CTA's Σ_i U[i, c]² over its rows into part[cta][c]
+// (double-float partials per thread, summed in thread order; the CTAs'
+// partials are then summed in CTA order by sumsq_reduce).  Persistent CTAs walk tiles of TM rows of
 // Y, staged in shared memory with row stride R | 1 (the rows a warp reads
 // fall in distinct banks); thread (ty, tx) accumulates RT rows x 8 columns,
 // {4tx .. 4tx+3} and {RP/2 + 4tx ..}, against float4 rows of M⁻¹ (columns
@@ -193,7 +216,7 @@ struct MinvCfg {
 template <int RP>
 __global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __restrict__ Y, int RSY,
                                                               const double* __restrict__ Minv, int64_t I, int R,
-                                                              float* __restrict__ U, double* __restrict__ sumsq) {
+                                                              float* __restrict__ U, double* __restrict__ part) {
     using C = MinvCfg<RP>;
     constexpr int TX = C::TX, RT = C::RT, TM = C::TM;
     extern __shared__ __align__(16) float sm[];
@@ -252,16 +275,15 @@ __global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __res
                     for (int q = 0; q < 4; ++q)
                         if (c0 + q < R) dst[c0 + q] = v[q];
                 }
-                if (sumsq) {
+                if (part) {
 #pragma unroll
                     for (int q = 0; q < 4; ++q) ss[4 * h + q] = df_add(ss[4 * h + q], df{v[q] * v[q], 0.f});
                 }
             }
         }
     }
-    if (!sumsq) return;
-    // column totals: the TY threads of a column group in fixed order, then one
-    // FP64 atomic per column
+    if (!part) return;
+    // column totals: the TY threads of a column group in fixed order
     __syncthreads();
     double* red = reinterpret_cast<double*>(sY);   // [TY][8 x TX] doubles <= TM * RS floats
 #pragma unroll
@@ -271,30 +293,44 @@ __global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __res
         const int h = col / (RP / 2), rem = col % (RP / 2), t = rem / 4, q = 4 * h + rem % 4;
         double a = 0.0;
         for (int y = 0; y < C::TY; ++y) a += red[y * 8 * TX + q * TX + t];
-        atomicAdd(sumsq + col, a);
+        part[(size_t)blockIdx.x * 128 + col] = a;
+    }
+}
+
+// σ²[c] = the CTAs' partials of column c, summed in CTA order.
+__global__ void sumsq_reduce(const double* __restrict__ part, int nparts, int R, double* __restrict__ sumsq) {
+    for (int c = threadIdx.x; c < R; c += blockDim.x) {
+        double a = 0.0;
+        for (int b = 0; b < nparts; ++b) a += part[(size_t)b * 128 + c];
+        sumsq[c] = a;
     }
 }
 
 template <int RP>
 cudaError_t launch_minv_t(const float* Y, int RSY, const double* Minv, int64_t I, int R, float* U, double* sumsq,
-                          int num_sms, cudaStream_t st) {
+                          double* part, int num_sms, cudaStream_t st) {
     using C = MinvCfg<RP>;
     const size_t sm = C::smem(R);
     cudaError_t e = cudaFuncSetAttribute(apply_minv<RP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     const int64_t ntiles = (I + C::TM - 1) / C::TM;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms * 2);
-    apply_minv<RP><<<(unsigned)grid, MINV_THREADS, sm, st>>>(Y, RSY, Minv, I, R, U, sumsq);
+    apply_minv<RP><<<(unsigned)grid, MINV_THREADS, sm, st>>>(Y, RSY, Minv, I, R, U, sumsq ? part : nullptr);
     count_launch();
+    if (sumsq) {
+        sumsq_reduce<<<1, 128, 0, st>>>(part, (int)grid, R, sumsq);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
-// Y: I x RSY (row stride RSY >= R)
+// Y: I x RSY (row stride RSY >= R); sumsq (may be null): the column sums of
+// squares of U, via part (2 x SMs x 128 doubles)
 cudaError_t launch_apply_minv(const float* Y, int RSY, const double* Minv, int64_t I, int R, float* U,
-                              double* sumsq, int num_sms, cudaStream_t st) {
-    if (R <= 32) return launch_minv_t<32>(Y, RSY, Minv, I, R, U, sumsq, num_sms, st);
-    if (R <= 64) return launch_minv_t<64>(Y, RSY, Minv, I, R, U, sumsq, num_sms, st);
-    return launch_minv_t<128>(Y, RSY, Minv, I, R, U, sumsq, num_sms, st);
+                              double* sumsq, double* part, int num_sms, cudaStream_t st) {
+    if (R <= 32) return launch_minv_t<32>(Y, RSY, Minv, I, R, U, sumsq, part, num_sms, st);
+    if (R <= 64) return launch_minv_t<64>(Y, RSY, Minv, I, R, U, sumsq, part, num_sms, st);
+    return launch_minv_t<128>(Y, RSY, Minv, I, R, U, sumsq, part, num_sms, st);
 }
 
 // U[:, c] /= σ_c (a zero column stays zero), σ_c = sqrt(σ²_c) to sigma;
@@ -322,7 +358,7 @@ struct FitParams {
     const float* sigma;
     int64_t nnz;
     int N, R;
-    double* out;
+    double* out;   // one partial per CTA
 };
 
 __global__ void __launch_bounds__(256) fit_inner(FitParams P) {
@@ -343,7 +379,7 @@ __global__ void __launch_bounds__(256) fit_inner(FitParams P) {
     if (threadIdx.x == 0) {
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
-        atomicAdd(P.out, t);
+        P.out[blockIdx.x] = t;   // the CTAs' partials are summed in order on the host
     }
 }
 
@@ -385,6 +421,29 @@ bool dmalloc(T** p, size_t n) {
 }
 
 thread_local std::string g_tensor_error;
+
+void free_lookup_scratch(krp_sptensor* t) {
+    for (int q = 0; q < 2; ++q) {
+        cudaFree(t->sk[q]);
+        cudaFree(t->sv[q]);
+        cudaFree(t->pk[q]);
+        cudaFree(t->pv[q]);
+        t->sk[q] = t->sv[q] = t->pk[q] = t->pv[q] = nullptr;
+    }
+    cudaFree(t->flag);
+    cudaFree(t->useg);
+    cudaFree(t->ufib);
+    cudaFree(t->poff);
+    cudaFree(t->cnt);
+    cudaFree(t->uacc);
+    cudaFree(t->pu);
+    cudaFree(t->pn);
+    cudaFree(t->hist);
+    t->flag = t->pu = t->pn = t->hist = nullptr;
+    t->useg = t->ufib = t->poff = t->cnt = nullptr;
+    t->uacc = nullptr;
+    t->lk_J = t->lk_pairs = t->lk_hist = t->lk_R = 0;
+}
 
 }  // namespace
 
@@ -453,6 +512,19 @@ extern "C" krp_status krp_sptensor_create(krp_sptensor** out, int N, const int64
         }
         fp.push_back(nnz);
         t->nfib[j] = (int64_t)fk.size();
+        {   // fiber lengths as (length, count), longest first
+            std::vector<int64_t> lens(fk.size());
+            for (size_t f = 0; f < fk.size(); ++f) lens[f] = fp[f + 1] - fp[f];
+            std::sort(lens.begin(), lens.end(), std::greater<int64_t>());
+            std::vector<std::pair<int64_t, int64_t>> h;
+            for (size_t f = 0; f < lens.size(); ++f) {
+                if (h.empty() || h.back().first != lens[f])
+                    h.push_back({lens[f], 1});
+                else
+                    ++h.back().second;
+            }
+            t->len_hist.push_back(std::move(h));
+        }
         ok = dmalloc(&t->fkeys[j], fk.size()) && dmalloc(&t->fptr[j], fp.size()) && dmalloc(&t->fidx[j], (size_t)nnz) &&
              dmalloc(&t->fval[j], (size_t)nnz);
         ok = ok && cudaMemcpy(t->fkeys[j], fk.data(), fk.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
@@ -480,17 +552,12 @@ extern "C" void krp_sptensor_destroy(krp_sptensor* t) {
         cudaFree(t->fval[j]);
     }
     cudaFree(t->Y);
-    cudaFree(t->lk_fiber);
-    cudaFree(t->lk_keys);
-    cudaFree(t->lk_begin);
-    cudaFree(t->lk_len);
-    cudaFree(t->lk_scan);
-    cudaFree(t->lk_acc);
+    free_lookup_scratch(t);
     delete t;
 }
 
 namespace krp {
-// krp_solve_sparse, plus σ²[c] += Σ_i U_out[i, c]² when sumsq is non-null
+// krp_solve_sparse, plus σ²[c] = Σ_i U_out[i, c]² when sumsq is non-null
 krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int64_t J, const int32_t* idx,
                              const float* weight, const float* SA, float* U_out, int flags, double* sumsq) {
     if (!s || !tc || !idx || !weight || !SA || !U_out) return s ? fail(s, KRP_EINVAL, "null argument") : KRP_EINVAL;
@@ -500,7 +567,7 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     for (int k = 0; k < s->N; ++k)
         if (t->I[k] != s->I[k]) return fail(s, KRP_EINVAL, "krp_solve_sparse: tensor dims differ from the factors");
     const int R = s->R;
-    const int RS = (R + 3) & ~3;   // Y's row stride: rows 16-byte aligned for the vector atomics
+    const int RS = (R + 3) & ~3;   // Y's row stride: rows 16-byte aligned for Y M⁻¹
     const size_t ny = (size_t)s->I[j] * RS;
     if (ny > t->Y_floats) {
         cudaFree(t->Y);
@@ -530,44 +597,78 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     P.R = R;
     P.Y = t->Y;
     P.RS = RS;
-    int log2H = 1;
-    while (((int64_t)1 << log2H) < 2 * J) ++log2H;
-    const int64_t H = (int64_t)1 << log2H;
-    if ((size_t)H + 1 > t->lk_n || (size_t)H * R > t->lk_acc_n) {
-        cudaFree(t->lk_fiber);
-        cudaFree(t->lk_keys);
-        cudaFree(t->lk_begin);
-        cudaFree(t->lk_len);
-        cudaFree(t->lk_scan);
-        cudaFree(t->lk_acc);
-        t->lk_fiber = t->lk_begin = t->lk_len = t->lk_scan = nullptr;
-        t->lk_keys = nullptr;
-        t->lk_acc = nullptr;
-        t->lk_n = t->lk_acc_n = 0;
-        if (!dmalloc(&t->lk_fiber, H + 1) || !dmalloc(&t->lk_keys, H + 1) || !dmalloc(&t->lk_begin, H + 1) ||
-            !dmalloc(&t->lk_len, H + 1) || !dmalloc(&t->lk_scan, H + 1) || !dmalloc(&t->lk_acc, (size_t)H * R))
-            return fail(s, KRP_ENOMEM, "sparse lookup scratch allocation failed");
-        t->lk_n = (size_t)H + 1;
-        t->lk_acc_n = (size_t)H * R;
+    // (fiber, nonzero) pairs a J-sample solve can read: the longest J fibers'
+    // total length (at most nnz)
+    int64_t pbound = 0, left = J;
+    for (const auto& lc : t->len_hist[j]) {
+        const int64_t take = std::min(left, lc.second);
+        pbound += take * lc.first;
+        left -= take;
+        if (left == 0) break;
     }
-    e = cudaMemsetAsync(t->lk_keys, 0xFF, (size_t)H * sizeof(unsigned long long), s->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(t->lk_acc, 0, (size_t)H * R * sizeof(float), s->stream);
-    if (e != cudaSuccess) return cuda_check(s, e, "lookup table memset");
-    const int64_t g0 = std::min<int64_t>((J + 255) / 256, (int64_t)s->num_sms * 8);
-    fiber_find<<<(unsigned)g0, 256, 0, s->stream>>>(P, t->lk_fiber); count_launch();
-    const int64_t g1 = std::min<int64_t>((J + 7) / 8, (int64_t)s->num_sms * 16);
-    merge_samples<<<(unsigned)g1, 256, 0, s->stream>>>(P, t->lk_fiber, t->lk_keys, t->lk_acc, log2H); count_launch();
-    const int64_t gs = std::min<int64_t>((H + 255) / 256, (int64_t)s->num_sms * 8);
-    slot_lengths<<<(unsigned)gs, 256, 0, s->stream>>>(P, t->lk_keys, H, t->lk_begin, t->lk_len); count_launch();
-    scan_lengths<<<1, 1024, 0, s->stream>>>(t->lk_len, t->lk_scan, H); count_launch();
-    fiber_scatter<<<(unsigned)(s->num_sms * 16), 256, 0, s->stream>>>(P, t->lk_begin, t->lk_scan, H, t->lk_acc);
+    pbound = std::max<int64_t>(pbound, 1);
+    const size_t nhist = std::max(radix_sort_hist_words(J), radix_sort_hist_words(pbound));
+    if ((size_t)J > t->lk_J || (size_t)pbound > t->lk_pairs || nhist > t->lk_hist || (size_t)R > t->lk_R) {
+        const size_t nJ = std::max<size_t>(J, t->lk_J), nP = std::max<size_t>(pbound, t->lk_pairs);
+        const size_t nH = std::max(nhist, t->lk_hist), nR = std::max<size_t>(R, t->lk_R);
+        free_lookup_scratch(t);
+        bool ok = true;
+        for (int q = 0; q < 2; ++q)
+            ok = ok && dmalloc(&t->sk[q], nJ) && dmalloc(&t->sv[q], nJ) && dmalloc(&t->pk[q], nP) &&
+                 dmalloc(&t->pv[q], nP);
+        ok = ok && dmalloc(&t->flag, nJ + 1) && dmalloc(&t->useg, 2 * nJ) && dmalloc(&t->ufib, nJ) &&
+             dmalloc(&t->poff, nJ + 1) && dmalloc(&t->cnt, 2) && dmalloc(&t->uacc, nJ * nR) &&
+             dmalloc(&t->pu, nP) && dmalloc(&t->pn, nP) && dmalloc(&t->hist, nH);
+        if (!ok) {
+            free_lookup_scratch(t);
+            return fail(s, KRP_ENOMEM, "sparse lookup scratch allocation failed");
+        }
+        t->lk_J = nJ;
+        t->lk_pairs = nP;
+        t->lk_hist = nH;
+        t->lk_R = nR;
+    }
+    const cudaStream_t cs = s->stream;
+    const int grid = s->num_sms * 4;
+    const uint32_t nfib = (uint32_t)t->nfib[j];
+    int fbits = 1;
+    while (fbits < 32 && ((uint64_t)1 << fbits) <= nfib) ++fbits;   // fiber ids 0 .. nfib
+    const unsigned g0 = (unsigned)std::min<int64_t>((J + 256) / 256, (int64_t)s->num_sms * 8);
+    // 1 - 2: samples by fiber, the distinct fibers' runs and summed rows
+    fiber_find<<<g0, 256, 0, cs>>>(P, t->sk[0], t->sv[0]);
+    count_launch();
+    bool in1 = false;
+    e = radix_sort_pairs(t->sk[0], t->sv[0], t->sk[1], t->sv[1], t->hist, J, nullptr, fbits, grid, &in1, cs);
+    if (e != cudaSuccess) return cuda_check(s, e, "sample sort launch");
+    const uint32_t* skey = t->sk[in1 ? 1 : 0];
+    const uint32_t* sval = t->sv[in1 ? 1 : 0];
+    run_heads<<<g0, 256, 0, cs>>>(skey, J, nfib, t->flag);
+    count_launch();
+    e = exclusive_scan_u32(t->flag, J + 1, cs);
+    if (e != cudaSuccess) return cuda_check(s, e, "run scan launch");
+    run_segments<<<g0, 256, 0, cs>>>(skey, J, nfib, t->flag, P.fptr, t->useg, t->ufib, t->poff, t->cnt);
+    count_launch();
+    fiber_acc<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, sval, t->useg, t->cnt, t->uacc);
+    count_launch();
+    // 3: the pairs, sorted by mode-j row
+    e = exclusive_scan_i64(t->poff, t->cnt, t->cnt + 1, cs);
+    if (e != cudaSuccess) return cuda_check(s, e, "pair scan launch");
+    pair_fill<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->ufib, t->poff, t->cnt, t->pk[0], t->pv[0], t->pu,
+                                                        t->pn);
+    count_launch();
+    e = radix_sort_pairs(t->pk[0], t->pv[0], t->pk[1], t->pv[1], t->hist, pbound, t->cnt + 1, t->kbits[j], grid,
+                         &in1, cs);
+    if (e != cudaSuccess) return cuda_check(s, e, "pair sort launch");
+    // 4: Y rows
+    row_sums<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->pk[in1 ? 1 : 0], t->pv[in1 ? 1 : 0], t->pu, t->pn,
+                                                        t->cnt, t->uacc);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "fiber lookup launch");
     krp_status st = normal_inverse(s, J, SA, flags);
     if (st != KRP_OK) return st;
     const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
-    e = launch_apply_minv(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->num_sms, s->stream);
+    e = launch_apply_minv(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->als_part, s->num_sms, s->stream);
     if (e != cudaSuccess) return cuda_check(s, e, "apply_minv launch");
     return KRP_OK;
 }
@@ -595,14 +696,12 @@ extern "C" krp_status krp_cp_als_sweep(krp_sampler* s, const krp_sptensor* t, in
     for (int j = 0; j < s->N; ++j) {
         st = krp_sample(s, j, J, seed, draw_base + (uint64_t)j, idx, w, nullptr, SA);
         if (st != KRP_OK) return st;
-        cudaError_t e = cudaMemsetAsync(sumsq, 0, R * sizeof(double), s->stream);
-        if (e != cudaSuccess) return cuda_check(s, e, "sumsq memset");
         // U_j = Y M⁻¹ with its column sums of squares from the same pass
         st = solve_sparse_impl(s, t, j, J, idx, w, SA, s->U[j], KRP_PINV_FALLBACK, sumsq);
         if (st != KRP_OK) return st;
         const int64_t g2 = std::min<int64_t>((s->I[j] + 7) / 8, (int64_t)s->num_sms * 8);
         col_scale<<<(unsigned)g2, 256, 0, s->stream>>>(s->U[j], s->I[j], R, sumsq, sigma); count_launch();
-        e = cudaGetLastError();
+        const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(s, e, "normalise launch");
         st = build_tree(s, j, s->prec);
         if (st != KRP_OK) return st;
@@ -620,8 +719,7 @@ extern "C" krp_status krp_cp_fit(krp_sampler* s, const krp_sptensor* t, const fl
     double* scratch;
     krp_status st = als_buffers(s, 1, &idx, &w, &SA, &scratch);
     if (st != KRP_OK) return st;
-    double* inner = scratch + R;
-    cudaMemsetAsync(inner, 0, sizeof(double), s->stream);
+    double* inner = s->als_part + (size_t)s->num_sms * 2 * 128;   // one partial per CTA
     FitParams P{};
     for (int k = 0; k < N; ++k) P.U[k] = s->U[k];
     P.coords = t->coords;
@@ -636,13 +734,15 @@ extern "C" krp_status krp_cp_fit(krp_sampler* s, const krp_sptensor* t, const fl
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "fit launch");
     std::vector<float> roots((size_t)N * s->Tp), sg(R);
-    double in_h = 0.0;
+    std::vector<double> parts(g);
     for (int k = 0; k < N; ++k)
         cudaMemcpyAsync(roots.data() + (size_t)k * s->Tp, s->tree[k], s->Tp * 4, cudaMemcpyDeviceToHost, s->stream);
     cudaMemcpyAsync(sg.data(), sigma, R * 4, cudaMemcpyDeviceToHost, s->stream);
-    cudaMemcpyAsync(&in_h, inner, 8, cudaMemcpyDeviceToHost, s->stream);
+    cudaMemcpyAsync(parts.data(), inner, g * sizeof(double), cudaMemcpyDeviceToHost, s->stream);
     e = cudaStreamSynchronize(s->stream);
     if (e != cudaSuccess) return cuda_check(s, e, "fit sync");
+    double in_h = 0.0;
+    for (int64_t b = 0; b < g; ++b) in_h += parts[b];
     // ||T̃||² = σᵀ (⊛_k G_k) σ from the trees' roots
     double m2 = 0.0;
     for (int a = 0; a < R; ++a)

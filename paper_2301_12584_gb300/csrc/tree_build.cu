@@ -17,6 +17,12 @@
 // every left child it creates.  The CTA's subtree root goes to scratch.
 // Kernel 2 (tree_up): the same pairwise sums over LBB nodes per CTA for the
 // levels above, until the root.
+//
+// Exact-decision mode (KRP_PREC_EXACT): the leaf Grams are accumulated
+// without rounding error (see leaf_grams_fp32), every stored slot keeps the
+// low part of its double-float value in a second array (tree_lo), and the
+// top levels are also written delta-encoded (build_dtop), for the descent's
+// near-edge decisions.
 #include "common.cuh"
 #include "internal.h"
 #include "tree_reduce.cuh"
@@ -57,10 +63,30 @@ __device__ __forceinline__ void stage_rows(float* sU, const float* __restrict__ 
     }
 }
 
+// Anchor of an exactly accumulated sum of products a_f b_f over one leaf:
+// M = 1.5 * 2^e with 2^e > 4.5 sqrt(na) sqrt(nb) (na, nb the FP32 sums of
+// squares of the two columns).  By Cauchy-Schwarz every partial sum lies
+// within 2^e / 4 of 0, so M + partial stays in M's binade [2^e, 2^(e+1)),
+// where FP32 numbers are multiples of one quantum ulp(M).
+__device__ __forceinline__ float sum_anchor(float na, float nb) {
+    int e;
+    frexpf(4.5f * sqrtf(na) * sqrtf(nb), &e);
+    return ldexpf(1.5f, e);
+}
+
 // Leaf Grams of LB leaves (F rows each) from sU into sG (LB x Tp), FP32 FMA,
-// 4x4 register tiles over the upper triangle of 4-column blocks.
-template <int LB, bool VEC>
-__device__ __forceinline__ void leaf_grams_fp32(const float* sU, float* sG, int R, int F, int Tp) {
+// 4x4 register tiles over the upper triangle of 4-column blocks, two entries
+// of a tile row per paired (f32x2) instruction.
+// EXACT: each entry is accumulated on its anchor M (above), s = M + sum:
+// t = fma(a, b, s) keeps a b to the quantum, s - t = -(what was kept) is
+// exact (same binade), r = fma(a, b, s - t) is what was dropped (to 2^-24 of
+// itself, |r| <= ulp(M)), and c accumulates r.  The entry is then (s - M) +
+// c, written as a double-float (hi into sG, lo into sGlo): its error is at
+// most F (F + 1) 2^-24 ulp(M) <= 9 F (F + 1) 2^-47 sqrt(G_ii G_jj), against
+// FP32's 2^-24 F |partial sums|.
+template <int LB, bool VEC, bool EXACT = false>
+__device__ __forceinline__ void leaf_grams_fp32(const float* sU, float* sG, int R, int F, int Tp,
+                                                float* sGlo = nullptr) {
     const int nt = (R + 3) >> 2;
     const int ntile = nt * (nt + 1) / 2;
     for (int task = threadIdx.x; task < LB * ntile; task += blockDim.x) {
@@ -72,14 +98,8 @@ __device__ __forceinline__ void leaf_grams_fp32(const float* sU, float* sG, int 
             ++ti;
         }
         const int tj = ti + t;
-        float acc[4][4];
-#pragma unroll
-        for (int x = 0; x < 4; ++x)
-#pragma unroll
-            for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
         const float* base = sU + (size_t)leaf * F * R;
-        for (int f = 0; f < F; ++f) {
-            float a[4], b[4];
+        auto load = [&](int f, float* a, float* b) {
             if (VEC) {
                 const float4 va = *reinterpret_cast<const float4*>(base + f * R + 4 * ti);
                 const float4 vb = *reinterpret_cast<const float4*>(base + f * R + 4 * tj);
@@ -92,10 +112,55 @@ __device__ __forceinline__ void leaf_grams_fp32(const float* sU, float* sG, int 
                     b[x] = (4 * tj + x < R) ? base[f * R + 4 * tj + x] : 0.f;
                 }
             }
+        };
+        // acc[x][h] holds entries (x, 2h) and (x, 2h + 1) of the tile
+        float2 acc[4][2], cor[4][2];
+        float na[4] = {0.f, 0.f, 0.f, 0.f}, nb[4] = {0.f, 0.f, 0.f, 0.f};
+        if (EXACT) {
+            float2 na2[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)}, nb2[2] = {na2[0], na2[0]};
+            for (int f = 0; f < F; ++f) {
+                float a[4], b[4];
+                load(f, a, b);
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const float2 ah = make_float2(a[2 * h], a[2 * h + 1]), bh = make_float2(b[2 * h], b[2 * h + 1]);
+                    na2[h] = ffma2(ah, ah, na2[h]);
+                    nb2[h] = ffma2(bh, bh, nb2[h]);
+                }
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                na[2 * h] = na2[h].x;
+                na[2 * h + 1] = na2[h].y;
+                nb[2 * h] = nb2[h].x;
+                nb[2 * h + 1] = nb2[h].y;
+            }
+        }
+#pragma unroll
+        for (int x = 0; x < 4; ++x)
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                acc[x][h] = EXACT ? make_float2(sum_anchor(na[x], nb[2 * h]), sum_anchor(na[x], nb[2 * h + 1]))
+                                  : make_float2(0.f, 0.f);
+                cor[x][h] = make_float2(0.f, 0.f);
+            }
+        for (int f = 0; f < F; ++f) {
+            float a[4], b[4];
+            load(f, a, b);
 #pragma unroll
             for (int x = 0; x < 4; ++x)
 #pragma unroll
-                for (int y = 0; y < 4; ++y) acc[x][y] = fmaf(a[x], b[y], acc[x][y]);
+                for (int h = 0; h < 2; ++h) {
+                    const float2 ax = make_float2(a[x], a[x]), bh = make_float2(b[2 * h], b[2 * h + 1]);
+                    if (EXACT) {
+                        const float2 tt = ffma2(ax, bh, acc[x][h]);
+                        const float2 nq = fsub2(acc[x][h], tt);
+                        cor[x][h] = fadd2(cor[x][h], ffma2(ax, bh, nq));
+                        acc[x][h] = tt;
+                    } else {
+                        acc[x][h] = ffma2(ax, bh, acc[x][h]);
+                    }
+                }
         }
         float* g = sG + (size_t)leaf * Tp;
 #pragma unroll
@@ -103,7 +168,18 @@ __device__ __forceinline__ void leaf_grams_fp32(const float* sU, float* sG, int 
 #pragma unroll
             for (int y = 0; y < 4; ++y) {
                 const int i = 4 * ti + x, j = 4 * tj + y;
-                if (i <= j && j < R) g[tri_index(i, j, R)] = acc[x][y];
+                const float v = (y & 1) ? acc[x][y >> 1].y : acc[x][y >> 1].x;
+                if (i <= j && j < R) {
+                    if (EXACT) {
+                        const float hi = v - sum_anchor(na[x], nb[y]);   // exact: same binade
+                        float sh, sl;
+                        two_sum(hi, (y & 1) ? cor[x][y >> 1].y : cor[x][y >> 1].x, sh, sl);
+                        g[tri_index(i, j, R)] = sh;
+                        sGlo[(size_t)leaf * Tp + tri_index(i, j, R)] = sl;
+                    } else {
+                        g[tri_index(i, j, R)] = v;
+                    }
+                }
             }
     }
 }
@@ -125,20 +201,25 @@ __device__ __forceinline__ void copy_rows_out(const float* sU, float* __restrict
 }
 
 // Block blk: leaves [blk G LB, (blk+1) G LB), subtree root to top slot blk.
-template <int LB, bool VEC>
+// EXACT: exactly accumulated leaf Grams, low parts stored into tree_lo.
+template <int LB, bool VEC, bool EXACT = false>
 __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ U, int64_t I, int R, int F, int64_t L,
                                                       int G, int Tp, float* __restrict__ tree,
                                                       float* __restrict__ top, float* __restrict__ copy_to,
-                                                      int64_t blk) {
+                                                      int64_t blk, float* __restrict__ tree_lo = nullptr) {
     extern __shared__ __align__(16) float smem[];
     const int rows = LB * F;
     const int T = tri_size(R);
     float* sU0 = smem;
     float* sU1 = sU0 + (size_t)rows * R;
     float* sG = (VEC ? sU1 : sU0) + (size_t)rows * R;
-    float* stk = sG + (size_t)LB * Tp;
+    float* sGlo = EXACT ? sG + (size_t)LB * Tp : nullptr;
+    float* stk = sG + (size_t)(EXACT ? 2 : 1) * LB * Tp;
     for (int e = threadIdx.x; e < LB * Tp; e += blockDim.x)
-        if (e % Tp >= T) sG[e] = 0.f;  // packed tail stays zero
+        if (e % Tp >= T) {  // packed tail stays zero
+            sG[e] = 0.f;
+            if (EXACT) sGlo[e] = 0.f;
+        }
     const int64_t leaf0 = blk * G * LB;
     stage_rows<VEC>(sU0, U, I, R, leaf0 * F, rows);
     if (VEC) cp_async_commit();
@@ -155,9 +236,9 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
         }
         __syncthreads();
         if (copy_to) copy_rows_out<VEC>(cur, copy_to, I, R, (leaf0 + (int64_t)g * LB) * F, rows);
-        leaf_grams_fp32<LB, VEC>(cur, sG, R, F, Tp);
+        leaf_grams_fp32<LB, VEC, EXACT>(cur, sG, R, F, Tp, sGlo);
         __syncthreads();
-        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk);
+        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk, sGlo, tree_lo);
         if (!VEC && g + 1 < G) {
             __syncthreads();
             stage_rows<VEC>(sU0, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);
@@ -165,11 +246,12 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
     }
 }
 
-template <int LB, bool VEC>
+template <int LB, bool VEC, bool EXACT>
 __global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
                                                         int64_t L, int G, int Tp, float* __restrict__ tree,
-                                                        float* __restrict__ top, float* __restrict__ copy_to) {
-    tree_leaves_fp32_body<LB, VEC>(U, I, R, F, L, G, Tp, tree, top, copy_to, blockIdx.x);
+                                                        float* __restrict__ top, float* __restrict__ copy_to,
+                                                        float* __restrict__ tree_lo) {
+    tree_leaves_fp32_body<LB, VEC, EXACT>(U, I, R, F, L, G, Tp, tree, top, copy_to, blockIdx.x, tree_lo);
 }
 
 // Entry e of node `node` of an input level as a double-float pair: the leaf
@@ -252,7 +334,7 @@ __global__ void tree_up_batch(const UpDesc* __restrict__ ups, const int64_t* __r
 // the FP32-rounded sum of every left child created.
 template <int LBB, bool FROM_PAIRS>
 __global__ void tree_up(const float* __restrict__ in_pairs, const double* __restrict__ in64, int64_t n_in, int Tp,
-                        float* __restrict__ tree, double* __restrict__ out) {
+                        float* __restrict__ tree, double* __restrict__ out, float* __restrict__ tree_lo) {
     const int64_t first = (int64_t)blockIdx.x * LBB;
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         float vh[LBB], vl[LBB];
@@ -265,7 +347,7 @@ __global__ void tree_up(const float* __restrict__ in_pairs, const double* __rest
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
                 df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
-                store_node(tree, h + l, Tp, e, vh[l]);
+                store_node2(tree, tree_lo, h + l, Tp, e, vh[l], vl[l]);
             }
         }
         out[(size_t)blockIdx.x * Tp + e] = (double)vh[0] + (double)vl[0];
@@ -307,13 +389,50 @@ __global__ void __launch_bounds__(256) gram64_partial(const float* __restrict__ 
 // Sum the partials in a fixed order into the FP64 root; also refresh the
 // stored FP32 root (slot 0) with the rounding of the exact value.
 __global__ void gram64_finish(const double* __restrict__ part, int nparts, int Tp, double* __restrict__ root64,
-                              float* __restrict__ slot0) {
+                              float* __restrict__ slot0, float* __restrict__ slot0_lo) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < Tp; e += gridDim.x * blockDim.x) {
         double a = 0.0;
         for (int p = 0; p < nparts; ++p) a += part[(size_t)p * Tp + e];
         root64[e] = a;
         slot0[e] = (float)a;
+        if (slot0_lo) slot0_lo[e] = (float)(a - (double)(float)a);
     }
+}
+
+// Delta-encoded top of a tree for the exact-decision descent (levels < Ke):
+// dtop = [root | D_1 | ... | D_{2^Ke - 1}] with the tree's slot numbering
+// (slot c at offset c Tp), D_c = G_{2c} - alpha_c G_c (node_alpha) formed in
+// double-float from the tree's (hi, lo) slots and rounded to FP32.  G_c of a
+// right child is its parent's Gram minus its left sibling's, walked down from
+// the root.  One CTA per slot.
+__global__ void build_dtop(const float* __restrict__ tree, const float* __restrict__ tlo, int64_t I, int F,
+                           int64_t L, int Tp, float* __restrict__ dtop) {
+    const int64_t c = blockIdx.x;
+    for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
+        if (c == 0) {
+            dtop[e] = tree[e];
+            continue;
+        }
+        df G{tree[e], tlo[e]};
+        const int dc = 63 - __clzll((unsigned long long)c);
+        for (int t = 1; t <= dc; ++t) {
+            const int64_t n = c >> (dc - t);
+            const int64_t par = n >> 1;   // left child of par is stored at slot par
+            const df gl{tree[par * Tp + e], tlo[par * Tp + e]};
+            G = (n & 1) ? df_add(G, df_neg(gl)) : gl;
+        }
+        const df GL{tree[c * Tp + e], tlo[c * Tp + e]};
+        const df D = df_add(GL, df_neg(df_mul_f(G, node_alpha(c, dc, L, F, I))));
+        dtop[c * Tp + e] = D.hi + D.lo;
+    }
+}
+
+cudaError_t launch_build_dtop(const krp_sampler* s, int j, cudaStream_t st) {
+    const int Ke = s->Ke[j];
+    build_dtop<<<(unsigned)((int64_t)1 << Ke), 256, 0, st>>>(s->tree[j], s->tree_lo[j], s->I[j], s->F, s->L[j],
+                                                           s->Tp, s->dtop[j]);
+    count_launch();
+    return cudaGetLastError();
 }
 
 // BF16x3 tensor-core leaf kernel (tree_build_tc.cu).
@@ -326,29 +445,39 @@ cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64
 
 namespace {
 
-template <int LB, bool VEC>
+template <int LB, bool VEC, bool EXACT>
 cudaError_t launch_leaves(const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree,
-                          float* top, float* copy_to, int64_t ctas, int threads, size_t smem, cudaStream_t st) {
-    auto k = tree_leaves_fp32<LB, VEC>;
+                          float* top, float* copy_to, int64_t ctas, int threads, size_t smem, cudaStream_t st,
+                          float* tree_lo) {
+    auto k = tree_leaves_fp32<LB, VEC, EXACT>;
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k<<<(unsigned)ctas, threads, smem, st>>>(U, I, R, F, L, G, Tp, tree, top, copy_to); count_launch();
+    k<<<(unsigned)ctas, threads, smem, st>>>(U, I, R, F, L, G, Tp, tree, top, copy_to, tree_lo); count_launch();
     return cudaGetLastError();
 }
 
 template <int LB>
 cudaError_t dispatch_vec(bool vec, const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp,
                          float* tree, float* top, float* copy_to, int64_t ctas, int threads, size_t smem,
-                         cudaStream_t st) {
-    return vec ? launch_leaves<LB, true>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st)
-               : launch_leaves<LB, false>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st);
+                         cudaStream_t st, float* tree_lo) {
+    if (tree_lo)
+        return vec ? launch_leaves<LB, true, true>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st,
+                                                   tree_lo)
+                   : launch_leaves<LB, false, true>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem,
+                                                    st, tree_lo);
+    return vec ? launch_leaves<LB, true, false>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st,
+                                                nullptr)
+               : launch_leaves<LB, false, false>(U, I, R, F, L, G, Tp, tree, top, copy_to, ctas, threads, smem, st,
+                                                 nullptr);
 }
 
 }  // namespace
 
 // Leaf-kernel geometry: LB leaves per group (power of two, <= 16, <= L, one
-// group of rows <= 32 KB), G groups per CTA (power of two, <= 8).
+// group of rows <= 32 KB), G groups per CTA (power of two, <= 8).  Exact
+// leaves keep a second LB x Tp array of low parts and stay within 110 KB, so
+// that two CTAs share an SM.
 void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* G_out, int* threads_out,
-                   size_t* smem_out) {
+                   size_t* smem_out, bool exact = false) {
     const size_t leaf_bytes = (size_t)F * R * 4;
     int LB = 1;
     while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * leaf_bytes <= 32 * 1024) LB *= 2;
@@ -360,9 +489,11 @@ void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* 
     auto smem_of = [&](int g) {
         int lv = 0;
         while ((1 << lv) < g) ++lv;
-        return (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)LB * Tp * 4 + (size_t)2 * (lv + 1) * Tp * 4;
+        return (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)(exact ? 2 : 1) * LB * Tp * 4 +
+               (size_t)2 * (lv + 1) * Tp * 4;
     };
-    while (G < 8 && (int64_t)G * 2 <= groups && smem_of(G * 2) <= 160 * 1024) G *= 2;
+    const size_t cap = exact ? 110 * 1024 : 160 * 1024;
+    while (G < 8 && (int64_t)G * 2 <= groups && smem_of(G * 2) <= cap) G *= 2;
     *LB_out = LB;
     *G_out = G;
     *threads_out = threads;
@@ -416,14 +547,16 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     const int R = s->R, F = s->F, Tp = s->Tp;
     const int64_t I = s->I[j], L = s->L[j];
     const bool vec = (R % 4) == 0;
-    const bool tc = precision == KRP_PREC_BF16X3 && tree_tc_supported(R, F);
+    // exact-decision samplers build every tree with exactly accumulated leaves
+    float* tree_lo = s->exact ? s->tree_lo[j] : nullptr;
+    const bool tc = !s->exact && precision == KRP_PREC_BF16X3 && tree_tc_supported(R, F);
     const bool tc_pipe = tc && tree_tc_pipelined(R, F, src);
     int LB, G, threads = 128;
     size_t smem;
     if (tc)
         tree_tc_geometry(R, F, L, Tp, tc_pipe, &LB, &G, &smem);
     else
-        tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem);
+        tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem, s->exact);
     const int64_t ctas = L / ((int64_t)LB * G);
     const int T = tri_size(R);
     const bool exact_root = (double)I * T <= (double)(1 << 22);
@@ -451,11 +584,11 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     } else {
         cudaError_t e;
         switch (LB) {
-            case 1: e = dispatch_vec<1>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
-            case 2: e = dispatch_vec<2>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
-            case 4: e = dispatch_vec<4>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
-            case 8: e = dispatch_vec<8>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
-            default: e = dispatch_vec<16>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream); break;
+            case 1: e = dispatch_vec<1>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream, tree_lo); break;
+            case 2: e = dispatch_vec<2>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream, tree_lo); break;
+            case 4: e = dispatch_vec<4>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream, tree_lo); break;
+            case 8: e = dispatch_vec<8>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream, tree_lo); break;
+            default: e = dispatch_vec<16>(vec, src, I, R, F, L, G, Tp, s->tree[j], top, copy_to, ctas, threads, smem, s->stream, tree_lo); break;
         }
         if (e != cudaSuccess) return cuda_check(s, e, "tree leaf kernel launch");
     }
@@ -472,9 +605,9 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
         double* out = (n / lbb == 1) ? s->root64[j] : outs[which];
 #define KRP_UP(LBBV)                                                                                          \
     if (first)                                                                                                \
-        tree_up<LBBV, true><<<grid, up_threads, 0, s->stream>>>(top, nullptr, n, Tp, s->tree[j], out);       \
+        tree_up<LBBV, true><<<grid, up_threads, 0, s->stream>>>(top, nullptr, n, Tp, s->tree[j], out, tree_lo); \
     else                                                                                                      \
-        tree_up<LBBV, false><<<grid, up_threads, 0, s->stream>>>(nullptr, in64, n, Tp, s->tree[j], out);
+        tree_up<LBBV, false><<<grid, up_threads, 0, s->stream>>>(nullptr, in64, n, Tp, s->tree[j], out, tree_lo);
         switch (lbb) {
             case 1: KRP_UP(1) break;
             case 2: KRP_UP(2) break;
@@ -496,9 +629,14 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
         const int64_t rpc = (I + nparts - 1) / nparts;
         const dim3 grid(nparts, (Tp + 255) / 256);
         gram64_partial<<<grid, 256, 64 * R * 4, s->stream>>>(s->U[j], I, R, rpc, up0); count_launch();
-        gram64_finish<<<(Tp + 255) / 256, 256, 0, s->stream>>>(up0, nparts, Tp, s->root64[j], s->tree[j]); count_launch();
+        gram64_finish<<<(Tp + 255) / 256, 256, 0, s->stream>>>(up0, nparts, Tp, s->root64[j], s->tree[j], tree_lo);
+        count_launch();
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_check(s, e, "exact root Gram launch");
+    }
+    if (s->exact) {
+        const cudaError_t e = launch_build_dtop(s, j, s->stream);
+        if (e != cudaSuccess) return cuda_check(s, e, "delta-encoded top launch");
     }
     return KRP_OK;
 }

@@ -10,6 +10,15 @@ namespace krp {
 __device__ __forceinline__ void store_node(float* __restrict__ tree, int64_t h, int Tp, int e, float v) {
     if (tree_stored(h)) tree[tree_slot(h) * Tp + e] = v;
 }
+// The same with the low part of a double-float value into `tree_lo` (the
+// exact-decision mode's second array), when given.
+__device__ __forceinline__ void store_node2(float* __restrict__ tree, float* __restrict__ tree_lo, int64_t h, int Tp,
+                                           int e, float hi, float lo) {
+    if (tree_stored(h)) {
+        tree[tree_slot(h) * Tp + e] = hi;
+        if (tree_lo) tree_lo[tree_slot(h) * Tp + e] = lo;
+    }
+}
 
 // Double-float addition (Knuth TwoSum, then a fast renormalisation): the pair
 // (hi, lo) carries the sum to about 2^-44 relative, so that the sums above the
@@ -26,23 +35,25 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
 // Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
 // merge across the CTA's groups, in double-float (DF) or plain FP32 (for leaf
 // Grams that carry ~1e-5 error of their own, where the sums' 2^-24 per level
-// is immaterial).  Stores the FP32 value of every left child created; the
-// subtree root of the G groups (the CTA's, or the block `top_slot` of a
-// persistent CTA) goes to top as (hi, lo).
+// is immaterial).  Stores the FP32 value of every left child created (and its
+// low part into tree_lo, if given); the subtree root of the G groups (the
+// CTA's, or the block `top_slot` of a persistent CTA) goes to top as (hi, lo).
+// sGlo: the leaf Grams' low parts (exactly accumulated leaves), or nullptr.
 template <int LB, bool DF = true>
 __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
                                              float* __restrict__ top, int64_t L, int64_t first_leaf,
-                                             int g, int G, int Tp, int64_t top_slot) {
+                                             int g, int G, int Tp, int64_t top_slot,
+                                             const float* sGlo = nullptr, float* __restrict__ tree_lo = nullptr) {
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         float vh[LB], vl[LB];
 #pragma unroll
         for (int l = 0; l < LB; ++l) {
             vh[l] = sG[l * Tp + e];
-            vl[l] = 0.f;
+            vl[l] = sGlo ? sGlo[l * Tp + e] : 0.f;
         }
         int64_t h = L + first_leaf;
 #pragma unroll
-        for (int l = 0; l < LB; ++l) store_node(tree, h + l, Tp, e, vh[l]);
+        for (int l = 0; l < LB; ++l) store_node2(tree, tree_lo, h + l, Tp, e, vh[l], vl[l]);
 #pragma unroll
         for (int n = LB; n > 1; n >>= 1) {
             h >>= 1;
@@ -52,7 +63,7 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
                     df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
                 else
                     vh[l] = vh[2 * l] + vh[2 * l + 1];
-                store_node(tree, h + l, Tp, e, vh[l]);
+                store_node2(tree, tree_lo, h + l, Tp, e, vh[l], vl[l]);
             }
         }
         float hi = vh[0], lo = vl[0];
@@ -65,7 +76,7 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
             h >>= 1;
             idx >>= 1;
             ++lvl;
-            store_node(tree, h, Tp, e, hi);
+            store_node2(tree, tree_lo, h, Tp, e, hi, lo);
         }
         if (G > 1) {   // with one group the stack is never read (and may have no space)
             stk[(2 * lvl) * Tp + e] = hi;

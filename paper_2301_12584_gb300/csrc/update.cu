@@ -15,7 +15,10 @@
 namespace krp {
 namespace {
 
+// tree_lo (exact-decision mode, else null): the slots' low parts; each stored
+// entry then takes the change in double-float, (hi, lo) + change.
 __global__ void __launch_bounds__(256) update_entries(float* __restrict__ U, float* __restrict__ tree,
+                                                      float* __restrict__ tree_lo,
                                                       double* __restrict__ root64, int64_t I, int R, int F,
                                                       int64_t L, int depth, int Tp, int64_t n,
                                                       const int32_t* __restrict__ rows,
@@ -48,7 +51,15 @@ __global__ void __launch_bounds__(256) update_entries(float* __restrict__ U, flo
         for (int t = threadIdx.x; t < m * R; t += blockDim.x) {
             const int node = t / R, k = t % R;
             const int e = k < c ? tri_index(k, c, R) : tri_index(c, k, R);
-            tree[slots[node] * (int64_t)Tp + e] += (float)dv[k];
+            const int64_t at = slots[node] * (int64_t)Tp + e;
+            if (tree_lo) {
+                const double v = (double)tree[at] + (double)tree_lo[at] + dv[k];
+                const float hi = (float)v;
+                tree[at] = hi;
+                tree_lo[at] = (float)(v - (double)hi);
+            } else {
+                tree[at] += (float)dv[k];
+            }
         }
         for (int k = threadIdx.x; k < R; k += blockDim.x)
             root64[k < c ? tri_index(k, c, R) : tri_index(c, k, R)] += dv[k];
@@ -72,9 +83,12 @@ extern "C" krp_status krp_update_entries(krp_sampler* s, int j, int64_t n, const
         return fail(s, KRP_EINVAL, "krp_update_entries: need n >= 0 and device rows, cols, values");
     if (!s->has_factor[j]) return fail(s, KRP_ESTATE, "krp_update_entries: factor not set");
     if (n == 0) return KRP_OK;
-    update_entries<<<1, 256, 0, s->stream>>>(s->U[j], s->tree[j], s->root64[j], s->I[j], s->R, s->F, s->L[j],
-                                             s->depth[j], s->Tp, n, rows, cols, values, s->status);
+    update_entries<<<1, 256, 0, s->stream>>>(s->U[j], s->tree[j], s->exact ? s->tree_lo[j] : nullptr, s->root64[j],
+                                             s->I[j], s->R, s->F, s->L[j], s->depth[j], s->Tp, n, rows, cols, values,
+                                             s->status);
     count_launch();
     s->last_exclude = -2;  // the per-draw preparation depends on G_j
-    return cuda_check(s, cudaGetLastError(), "krp_update_entries launch");
+    krp_status st = cuda_check(s, cudaGetLastError(), "krp_update_entries launch");
+    if (st == KRP_OK && s->exact) st = cuda_check(s, launch_build_dtop(s, j, s->stream), "delta-encoded top launch");
+    return st;
 }

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libkrpls.so")
 
 KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EZERO, KRP_ESINGULAR, KRP_ENUMERIC, KRP_ETIMEOUT, KRP_ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
-KRP_PREC_FP32, KRP_PREC_BF16X3 = 0, 1
+KRP_PREC_FP32, KRP_PREC_BF16X3, KRP_PREC_EXACT = 0, 1, 2
 KRP_PINV_FALLBACK = 1
 KRP_DESCENT_AUTO, KRP_DESCENT_TEAM, KRP_DESCENT_NODE_MAJOR = 0, 1, 2
 
@@ -35,10 +35,11 @@ SIGNATURES = [
     ("krp_sample", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_sample_prepare", _INT, [_P, _INT]),
     ("krp_set_descent_form", _INT, [_P, _INT]),
-    ("krp_probe_peaks", _INT, [_P, _P]),
     ("krp_sample_draw", _INT, [_P, _INT, _I64, _U64, _U64, _P, _P, _P, _P]),
     ("krp_launch_count", _I64, []),
+    ("krp_exact_count", _INT, [_P, C.POINTER(_I64)]),
     ("krp_debug_wait_timeout", _INT, [_P, _INT]),
+    ("krp_debug_sort_pairs", _INT, [_P, _P, _I64, _INT, _P]),
     ("krp_gather", _INT, [_P, _INT, _I64, _P, _P, _P]),
     ("krp_solve_dense", _INT, [_P, _I64, _P, _P, _P, _INT, _P, _INT]),
     ("krp_solve_dense_noalloc", _INT, [_I64, _INT, _P, _P, _P, _INT, _P, _INT, _P, _P]),
@@ -53,6 +54,7 @@ SIGNATURES = [
     ("krp_tree_info", _INT, [_P, _INT, C.POINTER(_I64), C.POINTER(_INT), C.POINTER(_INT)]),
     ("krp_get_tree", _INT, [_P, _INT, _P, _I64]),
     ("krp_get_factor", _INT, [_P, _INT, _P, _I64]),
+    ("krp_get_tree_exact", _INT, [_P, _INT, _P, _I64, _P, _I64]),
     ("krp_get_prep", _INT, [_P, _INT, _P, _P, _P, C.POINTER(_INT)]),
     ("krp_planted_rows", _INT, [_P, _INT, _I64, _P, _P, _INT, C.c_float, _U64, _P]),
     ("krp_update_entries", _INT, [_P, _INT, _I64, _P, _P, _P]),
@@ -258,6 +260,23 @@ class Sampler:
         self._check(self._lib.krp_get_tree(self.h, int(j), out.ctypes.data_as(_P), out.size))
         return out.reshape(L, st)
 
+    def get_tree_exact(self, j):
+        """Exact-decision samplers: (low parts shaped like get_tree, delta-encoded top)."""
+        import numpy as np
+        L, d, st = self.tree_info(j)
+        ke = min(10, d)
+        lo = np.zeros(L * st, dtype=np.float32)
+        top = np.zeros((1 << ke) * st, dtype=np.float32)
+        self._check(self._lib.krp_get_tree_exact(self.h, int(j), lo.ctypes.data_as(_P), lo.size,
+                                                 top.ctypes.data_as(_P), top.size))
+        return lo.reshape(L, st), top.reshape(1 << ke, st)
+
+    def exact_count(self):
+        """Row-stage descents switched to double-float masses so far (exact-decision samplers)."""
+        n = _I64()
+        self._check(self._lib.krp_exact_count(self.h, C.byref(n)))
+        return n.value
+
     def get_prep(self, k):
         import numpy as np
         R = self.R
@@ -270,13 +289,12 @@ class Sampler:
         return lam, V, Gp, rank.value
 
 
-def probe_peaks(stream=None):
-    """FP32 (scalar, paired), FP64 TFLOP/s and L2 read GB/s of the current device."""
-    out = (C.c_double * 4)()
-    code = lib().krp_probe_peaks(C.cast(out, _P), _P(_stream_ptr(stream)))
+def debug_sort_pairs(keys, vals, bits, stream=None):
+    """krp_debug_sort_pairs on device uint32 tensors (given as int32 torch tensors)."""
+    code = lib().krp_debug_sort_pairs(_P(_ptr(keys)), _P(_ptr(vals)), int(keys.numel()), int(bits),
+                                      _P(_stream_ptr(stream)))
     if code != KRP_OK:
-        raise KrpError(code, "krp_probe_peaks failed")
-    return {"fp32_tflops": out[0], "fp32x2_tflops": out[1], "fp64_tflops": out[2], "l2_read_gbs": out[3]}
+        raise KrpError(code, lib().krp_last_error(None).decode())
 
 
 def launch_count():

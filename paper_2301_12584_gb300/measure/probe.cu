@@ -1,16 +1,32 @@
-// Throughput probes for the rooflines the driver does not measure: FP32 FMA
-// (scalar and paired f32x2), FP64 FMA, and L2 read bandwidth.  Each runs a
-// fixed, bounded amount of work on every SM and is timed with CUDA events on
-// the caller's stream; results are whole-GPU rates.
-#include "common.cuh"
-#include "internal.h"
-
+// Throughput probes (a measurement tool, not part of libkrpls): FP32 FMA
+// (scalar and paired f32x2), FP64 FMA, and L2 read bandwidth, the
+// denominators of the SIMT-, FP64- and L2-bound rooflines.  Each runs a fixed,
+// bounded amount of work on every SM and is timed with CUDA events on the
+// caller's stream; results are whole-GPU rates.  Built on its own into
+// libkrpprobe.so and called by `python -m paper_2301_12584_gb300.profile_cases
+// peaks`.
+//
+// int krp_probe_peaks(double* out_host, void* stream): out_host[0] FP32
+// TFLOP/s with scalar FMA, [1] FP32 TFLOP/s with paired (f32x2) FMA, [2] FP64
+// TFLOP/s, [3] L2 read GB/s (64 MB buffer).  Allocates and frees 64 MB of
+// device memory; synchronous.  Returns 0, or -1 (NULL output), -2 (allocation
+// failed), -3 (a CUDA call failed).
 #include <cuda_runtime.h>
+#include <stdint.h>
 
 #include <algorithm>
 
-namespace krp {
+namespace krpprobe {
 namespace {
+
+// Two FP32 fused multiply-adds in one instruction.
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    uint64_t d;
+    const uint64_t ua = *reinterpret_cast<uint64_t*>(&a), ub = *reinterpret_cast<uint64_t*>(&b),
+                   uc = *reinterpret_cast<uint64_t*>(&c);
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(ua), "l"(ub), "l"(uc));
+    return *reinterpret_cast<float2*>(&d);
+}
 
 constexpr int PROBE_THREADS = 256;
 
@@ -72,17 +88,17 @@ __global__ void __launch_bounds__(PROBE_THREADS) probe_l2(const float4* __restri
 }
 
 }  // namespace
-}  // namespace krp
+}  // namespace krpprobe
 
-using namespace krp;
+using namespace krpprobe;
 
-extern "C" krp_status krp_probe_peaks(double* out_host, void* stream) {
-    if (!out_host) return KRP_EINVAL;
+extern "C" int krp_probe_peaks(double* out_host, void* stream) {
+    if (!out_host) return -1;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
                                                   cudaSuccess)
-        return KRP_ECUDA;
+        return -3;
     const int blocks = sms * 8;
     const int64_t nthreads = (int64_t)blocks * PROBE_THREADS;
     const int64_t l2_bytes = 64ll << 20;   // 64 MB, inside GB300's 129 MB L2
@@ -90,10 +106,10 @@ extern "C" krp_status krp_probe_peaks(double* out_host, void* stream) {
     float* sink = nullptr;
     float4* buf = nullptr;
     cudaEvent_t e0, e1;
-    if (cudaMalloc(&sink, nthreads * sizeof(double)) != cudaSuccess) return KRP_ENOMEM;
+    if (cudaMalloc(&sink, nthreads * sizeof(double)) != cudaSuccess) return -2;
     if (cudaMalloc(&buf, l2_bytes) != cudaSuccess) {
         cudaFree(sink);
-        return KRP_ENOMEM;
+        return -2;
     }
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -113,17 +129,16 @@ extern "C" krp_status krp_probe_peaks(double* out_host, void* stream) {
     const double t32x2 = timed([&] { probe_fp32x2<<<blocks, PROBE_THREADS, 0, st>>>(sink, it32); });
     const double t64 = timed([&] { probe_fp64<<<blocks, PROBE_THREADS, 0, st>>>(reinterpret_cast<double*>(sink), it64); });
     const double tl2 = timed([&] { probe_l2<<<blocks, PROBE_THREADS, 0, st>>>(buf, n4, passes, sink); });
-    for (int q = 0; q < 8; ++q) count_launch();
     const cudaError_t err = cudaGetLastError();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(sink);
     cudaFree(buf);
-    if (err != cudaSuccess) return KRP_ECUDA;
+    if (err != cudaSuccess) return -3;
     const double fma32 = (double)nthreads * it32 * 8, fma64 = (double)nthreads * it64 * 8;
     out_host[0] = 2.0 * fma32 / t32 * 1e-12;          // FP32 TFLOP/s, scalar FMA
     out_host[1] = 2.0 * 2.0 * fma32 / t32x2 * 1e-12;  // FP32 TFLOP/s, paired f32x2 FMA
     out_host[2] = 2.0 * fma64 / t64 * 1e-12;          // FP64 TFLOP/s
     out_host[3] = (double)l2_bytes * passes / tl2 * 1e-9;   // L2 read GB/s
-    return KRP_OK;
+    return 0;
 }

@@ -1,8 +1,10 @@
 """Small, fixed workloads for profiling single kernels of libkrpls with ncu.
 
   python -m paper_2301_12584_gb300.profile_cases descent   # krp_descent_fast, N=3, I=2^20, R=32, J=2^16
+  python -m paper_2301_12584_gb300.profile_cases descent_exact # the same draws in the exact-decision mode
   python -m paper_2301_12584_gb300.profile_cases build     # tree_leaves_fp32, one factor 2^21 x 32
   python -m paper_2301_12584_gb300.profile_cases build_tc  # tree_leaves_tc (BF16x3 on tcgen05), same factor
+  python -m paper_2301_12584_gb300.profile_cases build_exact # exactly accumulated leaves + build_dtop, same factor
   python -m paper_2301_12584_gb300.profile_cases prep      # prep_pinv / prep_eig, R=32, N=3
   python -m paper_2301_12584_gb300.profile_cases descent64 # krp_descent<64,2> (team kernel), N=4, I=2^18, J=2^15
   python -m paper_2301_12584_gb300.profile_cases descent100 # team descent (default form), N=3, I=2^20, R=100, J=2^14
@@ -24,10 +26,10 @@ from . import synth
 from .krpls import Sampler
 
 
-def descent():
+def descent(precision=0):
     I, R, J = 1 << 20, 32, 1 << 16
     Us = synth.skewed_row_factors(3, I, R, seed=0)
-    s = Sampler([I] * 3, R, 32)
+    s = Sampler([I] * 3, R, 32, precision)
     for k in range(3):
         s.set_factor(k, torch.from_numpy(Us[k]).cuda())
     idx = torch.zeros((3, J), dtype=torch.int32, device="cuda")
@@ -119,14 +121,29 @@ def prep():
     assert s.sync_status() == 0, s.last_error()
 
 
+def probe_peaks():
+    """FP32 (scalar, paired), FP64 TFLOP/s and L2 read GB/s of the current
+    device, from libkrpprobe.so (measure/probe.cu)."""
+    import ctypes as C
+    import os
+    lib = C.CDLL(os.path.join(os.path.dirname(os.path.abspath(__file__)), "libkrpprobe.so"))
+    lib.krp_probe_peaks.restype = C.c_int
+    lib.krp_probe_peaks.argtypes = [C.c_void_p, C.c_void_p]
+    out = (C.c_double * 4)()
+    code = lib.krp_probe_peaks(C.cast(out, C.c_void_p), C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    if code != 0:
+        raise RuntimeError(f"krp_probe_peaks failed ({code})")
+    return {"fp32_tflops": out[0], "fp32x2_tflops": out[1], "fp64_tflops": out[2], "l2_read_gbs": out[3]}
+
+
 def peaks():
     import json
-    from .krpls import probe_peaks
     print(json.dumps(probe_peaks()))
 
 
 if __name__ == "__main__":
-    {"descent": descent, "descent64": descent64, "descent100": descent100,
+    {"descent": descent, "descent_exact": lambda: descent(2), "build_exact": lambda: build(2),
+     "descent64": descent64, "descent100": descent100,
      "descent100_nm": lambda: descent100(2), "build": build, "build_tc": build_tc,
      "build100": lambda: build(0, 1 << 20, 100), "build100_tc": lambda: build(1, 1 << 20, 100),
      "prep": prep, "prep100": prep100, "minv100": minv100, "peaks": peaks}[sys.argv[1]]()

@@ -70,5 +70,4 @@ def test_host_argument_checks_without_gpu(built_lib):
     assert L.krp_set_descent_form(None, 0) == krpls.KRP_EINVAL
     assert L.krp_sample(None, -1, 16, 1, 0, None, None, None, None) != krpls.KRP_OK
     assert L.krp_get_factor(None, 0, None, 0) == krpls.KRP_EINVAL
-    assert L.krp_probe_peaks(None, None) == krpls.KRP_EINVAL
     assert b"R" in L.krp_last_error(None) or L.krp_last_error(None)

@@ -206,9 +206,10 @@ def test_batch_rejects_unsupported_samplers():
 
 
 def test_throughput_probes_are_plausible():
-    """krp_probe_peaks: the SIMT FP32, FP64 and L2 rooflines' denominators
-    (positive, finite, FP64 well below FP32, L2 above the HBM copy rate)."""
-    from paper_2301_12584_gb300.krpls import probe_peaks
+    """The measurement build's krp_probe_peaks (libkrpprobe.so): the SIMT FP32,
+    FP64 and L2 rooflines' denominators (positive, finite, FP64 well below FP32,
+    L2 above the HBM copy rate)."""
+    from paper_2301_12584_gb300.profile_cases import probe_peaks
     p = probe_peaks()
     assert all(np.isfinite(v) and v > 0 for v in p.values()), p
     assert p["fp64_tflops"] < p["fp32_tflops"], p

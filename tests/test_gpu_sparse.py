@@ -157,15 +157,10 @@ def test_bounded_wait_reports_timeout_and_context_survives():
 
 
 def test_graph_replay_of_sampler_calls():
-    """Sampler calls captured as a CUDA graph: a dense sketch-and-solve sequence
-    (no atomics) replays bit for bit; a whole STS-CP sweep replays to a valid
-    sweep close to the direct one.  The sparse scatter's atomic additions
-    reorder FP32 sums, which can move a sample across a bin edge in the next
-    mode, so the two sweeps share most but not all samples: every replayed
-    factor has unit columns (Gram diagonal 1 to 1e-5), its other Gram entries
-    lie within 0.2 of the direct sweep's (a quarter of the spread between two
-    independent sketches of this problem, median 0.8 over 8 oracle seeds;
-    0.07 measured between a sweep and its replay), and the fit within 1e-2."""
+    """Sampler calls captured as a CUDA graph replay bit for bit: a dense
+    sketch-and-solve sequence, and a whole STS-CP sweep (the sparse solve adds
+    in a fixed order: sorted runs instead of atomics), whose factors, trees,
+    sigma and fit equal the direct sweep's exactly."""
     from paper_2301_12584_gb300.krpls import Sampler, SparseTensor
     dims, R, J = (40, 30, 20), 4, 2000
     coords, vals = synth.sparse_zipf_tensor(dims, 3000, seed=8)
@@ -215,7 +210,9 @@ def test_graph_replay_of_sampler_calls():
     reset()
     s.cp_als_sweep(t, J, 5, 10, sigma)
     assert s.sync_status() == 0
-    direct_roots = [s.get_tree(k)[0].copy() for k in range(3)]
+    direct_trees = [s.get_tree(k).copy() for k in range(3)]
+    direct_factors = [s.get_factor(k).copy() for k in range(3)]
+    direct_sigma = sigma.clone()
     direct_fit = s.cp_fit(t, sigma)
     reset()
     sigma.zero_()
@@ -226,11 +223,113 @@ def test_graph_replay_of_sampler_calls():
     assert float(sigma.abs().sum()) == 0.0
     s.replay()
     assert s.sync_status() == 0
-    diag = [i * R - i * (i - 1) // 2 for i in range(R)]   # packed positions of (i, i)
     for k in range(3):
-        root = s.get_tree(k)[0]
-        np.testing.assert_allclose(root[diag], 1.0, rtol=0, atol=1e-5)
-        np.testing.assert_allclose(root, direct_roots[k], rtol=0, atol=0.2)
-    assert abs(s.cp_fit(t, sigma) - direct_fit) <= 1e-2 * max(abs(direct_fit), 1e-3)
+        assert np.array_equal(s.get_factor(k), direct_factors[k])
+        assert np.array_equal(s.get_tree(k), direct_trees[k])
+    assert torch.equal(sigma, direct_sigma)
+    assert s.cp_fit(t, sigma) == direct_fit
+    s.close()
+    t.close()
+
+
+@pytest.mark.parametrize("n,bits", [(1, 8), (100, 8), (2047, 13), (2048, 22), (2049, 32), (100003, 22),
+                                    (1 << 20, 32)])
+def test_radix_sort_is_stable(n, bits):
+    """The sort behind the deterministic sparse solve against NumPy's stable
+    argsort, on keys with many repeats (values = input positions)."""
+    from paper_2301_12584_gb300.krpls import debug_sort_pairs
+    rng = np.random.default_rng(n + bits)
+    hi = min(1 << bits, max(2, n // 7))
+    keys = rng.integers(0, hi, n, dtype=np.uint64).astype(np.uint32)
+    keys[rng.random(n) < 0.1] = np.uint32((1 << bits) - 1)          # the largest key, repeated
+    kd = torch.from_numpy(keys.view(np.int32).copy()).to(DEV)
+    vd = torch.arange(n, dtype=torch.int32, device=DEV)
+    debug_sort_pairs(kd, vd, bits)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(kd.cpu().numpy().view(np.uint32), keys[order])
+    assert np.array_equal(vd.cpu().numpy(), order.astype(np.int32))
+
+
+def test_sparse_solve_repeats_bit_for_bit():
+    """The same sparse solve twice (and a fresh tensor index) gives identical
+    U_j: every sum of the solve is taken in a fixed order."""
+    from paper_2301_12584_gb300.krpls import SparseTensor
+    dims, R, J = (3000, 2000, 60), 24, 1 << 15
+    coords, vals = synth.sparse_zipf_tensor(dims, 200000, seed=21)
+    Us = synth.gaussian_factors(3, list(dims), R, seed=22)
+    s, t = make(dims, R, coords, vals, Us)
+    t2 = SparseTensor(dims, coords, vals)
+    for j in range(3):
+        idx = torch.zeros((3, J), dtype=torch.int32, device=DEV)
+        w = torch.zeros(J, device=DEV)
+        SA = torch.zeros((J, R), device=DEV)
+        s.sample(j, J, 3, j, idx, w, None, SA)
+        outs = []
+        for tt in (t, t, t2):
+            Uo = torch.zeros((dims[j], R), device=DEV)
+            s.solve_sparse(tt, j, J, idx, w, SA, Uo)
+            assert s.sync_status() == 0, s.last_error()
+            outs.append(Uo)
+        assert torch.equal(outs[0], outs[1]) and torch.equal(outs[0], outs[2])
+    for x in (s, t, t2):
+        x.close()
+
+
+def test_sparse_solve_full_key_width():
+    """Dims 2^22 x 2^22 x 2^14 (keys of 22 + 22 and 22 + 14 bits), J = 2^16
+    samples per solve.  The factors are N(0,1) on 40 rows per mode spread over
+    the whole index range (the largest index included) and zero elsewhere, so
+    every sample lands on a tuple of those rows, and the ~7000 nonzeros lie on
+    them too, several fibers holding every one of their mode's 40 rows.  Each
+    mode's U_j against the FP64 lstsq on the GPU's own samples, restricted to
+    the rows the sampled fibers touch (every other row of U_j must be 0)."""
+    dims = (1 << 22, 1 << 22, 1 << 14)
+    R, J, nsup = 8, 1 << 16, 40
+    rng = np.random.default_rng(51)
+    sup = [np.sort(np.concatenate([rng.choice(d - 1, nsup - 1, replace=False), [d - 1]])) for d in dims]
+    full = set()
+    for _ in range(25):                      # long fibers: all 40 rows of the third mode
+        a, b = rng.integers(nsup, size=2)
+        full.update((int(sup[0][a]), int(sup[1][b]), int(sup[2][c])) for c in range(nsup))
+    for _ in range(25):                      # and of the first
+        b, c = rng.integers(nsup, size=2)
+        full.update((int(sup[0][a]), int(sup[1][b]), int(sup[2][c])) for a in range(nsup))
+    while len(full) < 7000:
+        a, b, c = rng.integers(nsup, size=3)
+        full.add((int(sup[0][a]), int(sup[1][b]), int(sup[2][c])))
+    coords = np.array(sorted(full), dtype=np.int32).T.copy()
+    vals = rng.lognormal(0.0, 0.5, coords.shape[1]).astype(np.float32)
+    Us = []
+    for k, d in enumerate(dims):
+        U = np.zeros((d, R), np.float32)
+        U[sup[k]] = rng.standard_normal((nsup, R)).astype(np.float32)
+        Us.append(U)
+    s, t = make(dims, R, coords, vals, Us)
+    for j in range(3):
+        idx = torch.zeros((3, J), dtype=torch.int32, device=DEV)
+        w = torch.zeros(J, device=DEV)
+        SA = torch.zeros((J, R), device=DEV)
+        s.sample(j, J, 11, j, idx, w, None, SA)
+        Uo = torch.zeros((dims[j], R), device=DEV)
+        s.solve_sparse(t, j, J, idx, w, SA, Uo)
+        assert s.sync_status() == 0, s.last_error()
+        gi = idx.cpu().numpy().astype(np.int64)[[k for k in range(3) if k != j]]
+        wg = w.cpu().numpy().astype(np.float64)
+        SAg = SA.cpu().numpy().astype(np.float64)
+        table = O.fiber_table(coords, vals.astype(np.float64), j)
+        cols = {int(x): q for q, x in enumerate(sup[j])}
+        SB = np.zeros((J, nsup))
+        hits = 0
+        for sm in range(J):
+            fib = table.get(tuple(int(x) for x in gi[:, sm]), ())
+            hits += bool(fib)
+            for (ij, v) in fib:
+                SB[sm, cols[ij]] += wg[sm] * v
+        assert hits > J // 10, hits              # the sampled tuples do reach the fibers
+        X = O.lstsq(SAg, SB).T                    # rows of U_j at the support rows
+        got = Uo.cpu().numpy()
+        err = np.linalg.norm(got[sup[j]] - X) / np.linalg.norm(X)
+        assert err < 1e-4, (j, err)
+        assert np.abs(got).sum() == np.abs(got[sup[j]]).sum()   # every other row is exactly 0
     s.close()
     t.close()

@@ -1,6 +1,8 @@
 """krp_solve_dense_noalloc (the dense sketched solve with fixed device scratch)
-against krp_solve_dense on the same inputs: two calls in a row, different
-shapes, then the status word's reset after a singular system.
+against krp_solve_dense and against the FP64 oracle's lstsq of the same
+weighted sketch: two calls in a row, different shapes (including one whose
+partial sums fill the most CTAs the solve uses, 2 per SM), then the status
+word's reset after a singular system.
 
 Tolerance: 1e-4 relative Frobenius, the dense solve's bar.  Collected last so
 that it also runs after every other GPU test in one process.
@@ -9,6 +11,7 @@ import numpy as np
 import pytest
 import torch
 
+from oracle import krp_oracle as O
 from paper_2301_12584_gb300 import synth
 
 DEV = "cuda:0"
@@ -46,13 +49,17 @@ def rel(a, b):
 
 @pytest.mark.gpu
 def test_noalloc_matches_solve_dense_twice(krpls):
-    cases = [(32, 16, 30001, 3), (13, 3, 777, 4)]   # (R, nrhs, J, seed): the limits, then a small ragged case
+    # (R, nrhs, J, seed): the limits; the limits with J >= 256 x 2 x SMs (every
+    # partial the solve can use, exponents at the end of the used scratch);
+    # a small ragged case
+    cases = [(32, 16, 30001, 3), (32, 16, 1 << 18, 5), (13, 3, 777, 4)]
     for R, nrhs, J, seed in cases:
         Us = synth.gaussian_factors(3, 40, R, seed=seed)
         s, SA, w, B = sketch(krpls, Us, J, seed, nrhs)
         X_ref = torch.zeros((R, nrhs), device=DEV)
         s.solve_dense(J, SA, w, B, nrhs, X_ref)
         assert s.sync_status() == 0
+        X_o = O.lstsq(SA.double().cpu().numpy(), (w[:, None] * B).double().cpu().numpy())
         status = torch.full((1,), 12345, dtype=torch.int32, device=DEV)
         for _ in range(2):
             X = torch.full((R, nrhs), float("nan"), device=DEV)
@@ -61,6 +68,8 @@ def test_noalloc_matches_solve_dense_twice(krpls):
             assert int(status.item()) == 0
             assert torch.isfinite(X).all()
             assert rel(X, X_ref) <= 1e-4
+            Xn = X.double().cpu().numpy()
+            assert np.linalg.norm(Xn - X_o) <= 1e-4 * np.linalg.norm(X_o)
         s.close()
 
 
