@@ -4,9 +4,9 @@
 // same order.
 //
 // A pass over n pairs: rs_hist counts each 2048-pair tile's digits into
-// hist[digit][tile]; rs_scan turns hist into exclusive offsets (digit-major,
-// so that offset(d, tile) = pairs of smaller digits + pairs of digit d in
-// earlier tiles); rs_scatter sorts each tile by the digit in shared memory
+// hist[digit][tile]; three scan launches (sc_*) turn hist into exclusive
+// offsets (digit-major, so that offset(d, tile) = pairs of smaller digits +
+// pairs of digit d in earlier tiles); rs_scatter sorts each tile by the digit in shared memory
 // with eight stable one-bit splits (each a block-wide scan of the threads'
 // zero counts), then writes every pair to offset(d, tile) + its rank among the
 // tile's pairs of digit d.  Positions past n within the last tile hold pads
@@ -69,10 +69,84 @@ __device__ __forceinline__ void rs_scan_body(uint32_t* __restrict__ a, int64_t m
     }
 }
 
-// Exclusive scan in place of the 256 * ntiles words of hist (ntiles from n).
-__global__ void __launch_bounds__(1024) rs_scan(uint32_t* __restrict__ a, int64_t n_host,
-                                                const int64_t* __restrict__ n_dev) {
-    rs_scan_body(a, 256 * ((rs_count(n_host, n_dev) + RS_TILE - 1) / RS_TILE));
+// Exclusive scan in place of the m = 256 * ntiles words of hist (ntiles from
+// n), in three launches over segments of SC_SEG words: the segments' sums,
+// their exclusive scan (one CTA), then each segment's scan plus its offset.
+constexpr int SC_THREADS = 1024;
+constexpr int SC_SEG = SC_THREADS * 8;
+
+__device__ __forceinline__ int64_t rs_words(int64_t n_host, const int64_t* n_dev) {
+    return 256 * ((rs_count(n_host, n_dev) + RS_TILE - 1) / RS_TILE);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) sc_sums(const uint32_t* __restrict__ a, int64_t n_host,
+                                                      const int64_t* __restrict__ n_dev, uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t warp_tot[SC_THREADS / 32];
+    const int64_t m = rs_words(n_host, n_dev);
+    const int64_t base = (int64_t)blockIdx.x * SC_SEG + threadIdx.x * 8;
+    uint32_t v = 0;
+    if (base < m) {   // m is a multiple of 256: a thread's 8 words are all in range or none is
+        const uint4 x = *reinterpret_cast<const uint4*>(a + base);
+        const uint4 y = *reinterpret_cast<const uint4*>(a + base + 4);
+        v = x.x + x.y + x.z + x.w + y.x + y.y + y.z + y.w;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) warp_tot[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t t = 0;
+        for (int w = 0; w < SC_THREADS / 32; ++w) t += warp_tot[w];
+        bsum[blockIdx.x] = t;
+    }
+}
+
+__global__ void __launch_bounds__(1024) sc_bscan(uint32_t* __restrict__ bsum, int64_t n_host,
+                                                 const int64_t* __restrict__ n_dev) {
+    rs_scan_body(bsum, (rs_words(n_host, n_dev) + SC_SEG - 1) / SC_SEG);
+}
+
+__global__ void __launch_bounds__(SC_THREADS) sc_apply(uint32_t* __restrict__ a, int64_t n_host,
+                                                       const int64_t* __restrict__ n_dev,
+                                                       const uint32_t* __restrict__ bsum) {
+    __shared__ uint32_t warp_tot[SC_THREADS / 32];
+    const int64_t m = rs_words(n_host, n_dev);
+    if ((int64_t)blockIdx.x * SC_SEG >= m) return;   // uniform across the CTA
+    const int64_t base = (int64_t)blockIdx.x * SC_SEG + threadIdx.x * 8;
+    uint32_t w[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (base < m) {
+        const uint4 x = *reinterpret_cast<const uint4*>(a + base);
+        const uint4 y = *reinterpret_cast<const uint4*>(a + base + 4);
+        w[0] = x.x; w[1] = x.y; w[2] = x.z; w[3] = x.w; w[4] = y.x; w[5] = y.y; w[6] = y.z; w[7] = y.w;
+    }
+    uint32_t t = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) t += w[i];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t inc = t;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) warp_tot[warp] = inc;
+    __syncthreads();
+    uint32_t before = bsum[blockIdx.x];
+    for (int q = 0; q < warp; ++q) before += warp_tot[q];
+    uint32_t run = before + inc - t;
+    if (base < m) {
+        uint4 x, y;
+        x.x = run; run += w[0];
+        x.y = run; run += w[1];
+        x.z = run; run += w[2];
+        x.w = run; run += w[3];
+        y.x = run; run += w[4];
+        y.y = run; run += w[5];
+        y.z = run; run += w[6];
+        y.w = run;
+        *reinterpret_cast<uint4*>(a + base) = x;
+        *reinterpret_cast<uint4*>(a + base + 4) = y;
+    }
 }
 
 // Block-wide exclusive scan of one value per thread; *total gets the sum.
@@ -207,7 +281,11 @@ cudaError_t exclusive_scan_i64(int64_t* a, const int64_t* n_dev, int64_t* total,
     return cudaGetLastError();
 }
 
-size_t radix_sort_hist_words(int64_t n) { return (size_t)256 * (size_t)((n + RS_TILE - 1) / RS_TILE); }
+// The digit counts (256 per tile) and, after them, the scan's segment sums.
+size_t radix_sort_hist_words(int64_t n) {
+    const size_t m = (size_t)256 * (size_t)((n + RS_TILE - 1) / RS_TILE);
+    return m + (m + SC_SEG - 1) / SC_SEG + 4;
+}
 
 // Stable sort of n pairs by the low `bits` bits of the keys.  (k0, v0) hold the
 // input; (k1, v1) are work arrays of n words; hist has radix_sort_hist_words(n)
@@ -221,11 +299,16 @@ cudaError_t radix_sort_pairs(uint32_t* k0, uint32_t* v0, uint32_t* k1, uint32_t*
     const int64_t ntiles = (n + RS_TILE - 1) / RS_TILE;
     const unsigned g = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ntiles, grid));
     uint32_t *ki = k0, *vi = v0, *ko = k1, *vo = v1;
+    const int64_t m = 256 * ntiles;   // hist words for the bound n
+    const unsigned nseg = (unsigned)((m + SC_SEG - 1) / SC_SEG);
+    uint32_t* bsum = hist + ((m + 3) & ~(int64_t)3);
     for (int shift = 0; shift < bits; shift += 8) {
         rs_hist<<<g, RS_THREADS, 0, st>>>(ki, n, n_dev, shift, hist);
-        rs_scan<<<1, 1024, 0, st>>>(hist, n, n_dev);
+        sc_sums<<<nseg, SC_THREADS, 0, st>>>(hist, n, n_dev, bsum);
+        sc_bscan<<<1, 1024, 0, st>>>(bsum, n, n_dev);
+        sc_apply<<<nseg, SC_THREADS, 0, st>>>(hist, n, n_dev, bsum);
         rs_scatter<<<g, RS_THREADS, 0, st>>>(ki, vi, ko, vo, n, n_dev, shift, hist);
-        for (int q = 0; q < 3; ++q) count_launch();
+        for (int q = 0; q < 5; ++q) count_launch();
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         std::swap(ki, ko);

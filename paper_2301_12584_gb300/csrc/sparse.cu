@@ -16,8 +16,10 @@
 //      samples, in sample order (a warp per fiber);
 //   3. its (fiber, nonzero) pairs are numbered by a scan of the fibers'
 //      lengths and sorted by the nonzero's mode-j row;
-//   4. a warp per row run forms Y[i_j, :] = Σ v acc_u over the run, in order,
-//      and stores it (Y = SBᵀ SA, I_j x R; untouched rows stay zero);
+//   4. the run of pairs of each row i_j forms Y[i_j, :] = Σ v acc_u in an
+//      order fixed by the sorted positions (a warp per run, lanes over the
+//      columns of a short run or over the pairs of a long one) and stores it
+//      (Y = SBᵀ SA, I_j x R; untouched rows stay zero);
 //   5. U_j = Y M⁻¹ with M = SAᵀ SA (FP64 Cholesky inverse, applied in FP32),
 //      the column sums of squares as per-CTA partials summed in CTA order.
 #include "common.cuh"
@@ -158,13 +160,30 @@ __global__ void __launch_bounds__(256) pair_fill(LookupParams P, const int64_t* 
     }
 }
 
-// Step 4: Y[i, :] = Σ v acc_u over the sorted run of row i's pairs, in order.
-// Warps take chunks of 32 sorted positions and own the runs that start there
-// (a run may extend past the chunk); lanes over columns.
+// Step 4a: the sorted pairs' distinct-fiber index and value, in sorted order.
+__global__ void __launch_bounds__(256) pair_gather(LookupParams P, const uint32_t* __restrict__ val,
+                                                   const uint32_t* __restrict__ pu, const uint32_t* __restrict__ pn,
+                                                   const int64_t* __restrict__ cnt, uint32_t* __restrict__ su,
+                                                   float* __restrict__ sv) {
+    const int64_t npairs = cnt[1];
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < npairs; q += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t w = val[q];
+        su[q] = pu[w];
+        sv[q] = __ldg(P.fval + pn[w]);
+    }
+}
+
+// Step 4b: Y[i, :] = Σ v acc_u over row i's run of sorted pairs.  Warps take
+// chunks of 32 sorted positions and own the runs that start there (a run may
+// extend past the chunk).  A run of one pair is written by its own lane; one
+// of up to 32 pairs is summed in order with the lanes over columns; a longer
+// one with pair q on lane (q - start) mod 32, each lane summing its pairs in
+// order for 32 columns at a time, then the lanes' sums combined by a fixed
+// butterfly (lane c ends with column c).
+// Either way the order of every sum depends only on the sorted positions.
 __global__ void __launch_bounds__(256) row_sums(LookupParams P, const uint32_t* __restrict__ key,
-                                                const uint32_t* __restrict__ val, const uint32_t* __restrict__ pu,
-                                                const uint32_t* __restrict__ pn, const int64_t* __restrict__ cnt,
-                                                const float* __restrict__ acc) {
+                                                const uint32_t* __restrict__ su, const float* __restrict__ sv,
+                                                const int64_t* __restrict__ cnt, const float* __restrict__ acc) {
     const int lane = threadIdx.x & 31;
     const int64_t npairs = cnt[1];
     const int64_t nchunk = (npairs + 31) / 32;
@@ -172,24 +191,68 @@ __global__ void __launch_bounds__(256) row_sums(LookupParams P, const uint32_t* 
     for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunk; ch += warps) {
         const int64_t p = ch * 32 + lane;
         const bool head = p < npairs && (p == 0 || key[p] != key[p - 1]);
-        unsigned heads = __ballot_sync(0xffffffffu, head);
+        // runs of one pair (most rows): a lane each
+        if (head && (p + 1 >= npairs || key[p + 1] != key[p])) {
+            const float* au = acc + (int64_t)su[p] * P.R;
+            const float v = sv[p];
+            float* y = P.Y + (int64_t)key[p] * P.RS;
+            for (int c = 0; c < P.R; ++c) y[c] = v * au[c];
+        }
+        unsigned heads = __ballot_sync(0xffffffffu, head && p + 1 < npairs && key[p + 1] == key[p]);
         while (heads) {
             const int h = __ffs(heads) - 1;
             heads &= heads - 1;
             const int64_t p0 = ch * 32 + h;
             const uint32_t row = key[p0];
-            float a[4] = {0.f, 0.f, 0.f, 0.f};
-            for (int64_t q = p0; q < npairs && key[q] == row; ++q) {
-                const uint32_t w = val[q];
-                const int64_t u = pu[w];
-                const float v = __ldg(P.fval + pn[w]);
+            // the run's end, 32 positions at a time
+            int64_t p1 = p0 + 1;
+            for (;;) {
+                const int64_t q = p1 + lane;
+                const unsigned more = __ballot_sync(0xffffffffu, q < npairs && key[q] == row);
+                if (more != 0xffffffffu) {
+                    p1 += __ffs(~more) - 1;
+                    break;
+                }
+                p1 += 32;
+            }
+            float* y = P.Y + (int64_t)row * P.RS;
+            if (p1 - p0 <= 32) {
+                float a[4] = {0.f, 0.f, 0.f, 0.f};
+                for (int64_t q = p0; q < p1; ++q) {
+                    const int64_t u = su[q];
+                    const float v = sv[q];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c)
+                        if (lane + 32 * c < P.R) a[c] = fmaf(v, acc[u * P.R + lane + 32 * c], a[c]);
+                }
 #pragma unroll
                 for (int c = 0; c < 4; ++c)
-                    if (lane + 32 * c < P.R) a[c] = fmaf(v, acc[u * P.R + lane + 32 * c], a[c]);
-            }
+                    if (lane + 32 * c < P.R) y[lane + 32 * c] = a[c];
+            } else {
+                for (int c0 = 0; c0 < P.R; c0 += 32) {
+                    float a[32];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                if (lane + 32 * c < P.R) P.Y[(int64_t)row * P.RS + lane + 32 * c] = a[c];
+                    for (int c = 0; c < 32; ++c) a[c] = 0.f;
+                    for (int64_t q = p0 + lane; q < p1; q += 32) {
+                        const float* au = acc + (int64_t)su[q] * P.R + c0;
+                        const float v = sv[q];
+#pragma unroll
+                        for (int c = 0; c < 32; ++c)
+                            if (c0 + c < P.R) a[c] = fmaf(v, au[c], a[c]);
+                    }
+#pragma unroll
+                    for (int off = 16; off >= 1; off >>= 1) {
+                        const bool upper = (lane & off) != 0;
+#pragma unroll
+                        for (int i = 0; i < off; ++i) {
+                            const float send = upper ? a[i] : a[i + off];
+                            const float keep = upper ? a[i + off] : a[i];
+                            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+                        }
+                    }
+                    if (c0 + lane < P.R) y[c0 + lane] = a[0];
+                }
+            }
         }
     }
 }
@@ -305,6 +368,17 @@ __global__ void sumsq_reduce(const double* __restrict__ part, int nparts, int R,
         sumsq[c] = a;
     }
 }
+
+cudaError_t launch_sumsq_reduce(const double* part, int nparts, int R, double* sumsq, cudaStream_t st) {
+    sumsq_reduce<<<1, 128, 0, st>>>(part, nparts, R, sumsq);
+    count_launch();
+    return cudaGetLastError();
+}
+
+// minv_tc.cu: U = Y M⁻¹ on tensor cores in split TF32 (R <= 104)
+bool minv_tc_supported(int R);
+cudaError_t launch_minv_tc(const float* Y, int RSY, const double* Minv, int64_t I, int R, float* U, double* sumsq,
+                           double* part, int* status, int num_sms, cudaStream_t st);
 
 template <int RP>
 cudaError_t launch_minv_t(const float* Y, int RSY, const double* Minv, int64_t I, int R, float* U, double* sumsq,
@@ -659,8 +733,13 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     e = radix_sort_pairs(t->pk[0], t->pv[0], t->pk[1], t->pv[1], t->hist, pbound, t->cnt + 1, t->kbits[j], grid,
                          &in1, cs);
     if (e != cudaSuccess) return cuda_check(s, e, "pair sort launch");
-    // 4: Y rows
-    row_sums<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->pk[in1 ? 1 : 0], t->pv[in1 ? 1 : 0], t->pu, t->pn,
+    // 4: Y rows (the free pair of sort buffers takes the gathered fiber
+    // indices and values)
+    const int a1 = in1 ? 1 : 0, b1 = in1 ? 0 : 1;
+    pair_gather<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->pv[a1], t->pu, t->pn, t->cnt, t->pk[b1],
+                                                           reinterpret_cast<float*>(t->pv[b1]));
+    count_launch();
+    row_sums<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->pk[a1], t->pk[b1], reinterpret_cast<float*>(t->pv[b1]),
                                                         t->cnt, t->uacc);
     count_launch();
     e = cudaGetLastError();
@@ -668,7 +747,12 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     krp_status st = normal_inverse(s, J, SA, flags);
     if (st != KRP_OK) return st;
     const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
-    e = launch_apply_minv(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->als_part, s->num_sms, s->stream);
+    // split-precision samplers apply M⁻¹ on the tensor cores (TF32x3); FP32
+    // samplers keep the FP32 SIMT product
+    if (s->prec == KRP_PREC_BF16X3 && minv_tc_supported(R))
+        e = launch_minv_tc(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->als_part, s->status, s->num_sms, s->stream);
+    else
+        e = launch_apply_minv(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->als_part, s->num_sms, s->stream);
     if (e != cudaSuccess) return cuda_check(s, e, "apply_minv launch");
     return KRP_OK;
 }
