@@ -179,11 +179,10 @@ __host__ __device__ __forceinline__ float node_alpha(int64_t c, int t, int64_t L
 }
 // Top levels delta-encoded in exact-decision mode (decisions at depth < KRP_EXACT_TOP).
 constexpr int KRP_EXACT_TOP = 10;
-// Near-edge band of the exact-decision mode, relative to the stage total C:
-// a decision whose FP32-path gap |tau - low - m(L(c))| is within this band
-// is re-taken from double-float masses (the FP32 path with a delta-encoded
-// top is off by under 4e-10 C on 2^22-row trees).
-constexpr float KRP_EXACT_BAND = 2e-9f;
+// Margin of the exact-decision mode, relative to the stage total C, added to
+// the FP32 path's modelled error terms: a decision whose gap |tau - low -
+// m(L(c))| is within both is re-taken from double-float masses.
+constexpr float KRP_EXACT_BAND = 5e-10f;
 
 // Butterfly sum of a double-float over the warp; every lane gets the same pair
 // (TwoSum gives the same exact error for either operand order).

@@ -35,14 +35,23 @@
 
 #include <math.h>
 
+// The exact-decision kernels are built in a translation unit of their own
+// (descent_exact.cu sets KRP_DESCENT_EXACT_TU and includes this file), so
+// that their code stays out of the FP32 kernels' unit.
+#ifndef KRP_DESCENT_EXACT_TU
+#define KRP_DESCENT_EXACT_TU 0
+#endif
+
 namespace krp {
 
 
 constexpr int FAST_TRACE_STRIDE = 66;
 
-template <int RMAX>
+// X: exact-decision samplers, whose node slots carry one more float (a bound
+// for the node's masses) after the packed triangle.
+template <int RMAX, bool X = false>
 struct FastCfg {
-    static constexpr int TPMAX = ((RMAX * (RMAX + 1) / 2) + 7) & ~7;
+    static constexpr int TPMAX = ((RMAX * (RMAX + 1) / 2) + (X ? 1 : 0) + 7) & ~7;
     static constexpr int NC4 = TPMAX / 4;           // float4 chunks per node
     static constexpr int NCH = (NC4 + 31) / 32;     // chunks per lane
     static constexpr int WARPS = 8;
@@ -84,6 +93,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, uint32_t parity, int max_
     return false;
 }
 
+#if KRP_DESCENT_EXACT_TU
 // Exact-decision mode: mass h̃ᵀ G h̃ of a node from its double-float slot (ghi,
 // glo: shared or global) with double-float weights of h̃ = (th, thl), ~2^-44
 // relative; every lane of the warp calls it and gets the same value.  It
@@ -139,11 +149,12 @@ __device__ __forceinline__ df exact_low_fn(const float* tr, const float* tl, int
 // Exact-decision mode: a leaf scan re-taken in double-float, every lane
 // calling with its rows t = lane rpt + r of the leaf (rows: nrows rows of R
 // floats, shared or global): q_t = (U[t] · h̃)^2 with h̃ = (th, thl),
-// cumulative right edges from low.  Returns this lane's first row whose edge
-// reaches tau (0x7fffffff if none) and its last row of positive weight (-1).
+// cumulative right edges from low.  Returns this lane's first row of positive
+// weight whose edge reaches tau (0x7fffffff if none) and its last row of
+// positive weight (-1); near_low: some edge lies within mlow of tau.
 template <int RPT>
 __device__ __forceinline__ int2 exact_leaf_scan(const float* rows, int R, int rpt, int nrows, const float* th,
-                                             const float* thl, df tau, df low) {
+                                             const float* thl, df tau, df low, float mlow, bool& near_low) {
     const int lane = threadIdx.x & 31;
     df qd[RPT];
 #pragma unroll 1
@@ -176,23 +187,28 @@ __device__ __forceinline__ int2 exact_leaf_scan(const float* rows, int R, int rp
     if (lane == 0) cd = df{0.f, 0.f};
     cd = df_add(cd, low);
     int first = 0x7fffffff, lastpos = -1;
+    bool nl = false;
 #pragma unroll 1
     for (int r = 0; r < RPT; ++r) {
         const int t = lane * rpt + r;
         if (r < rpt && t < nrows) {
             cd = df_add(cd, qd[r]);
-            if (first == 0x7fffffff && df_le(tau, cd)) first = t;
+            if (first == 0x7fffffff && qd[r].hi > 0.f && df_le(tau, cd)) first = t;
             if (qd[r].hi > 0.f) lastpos = t;
+            if (fabsf(df_add(cd, df_neg(tau)).hi) <= mlow) nl = true;
         }
     }
+    near_low = __any_sync(0xffffffffu, nl);
     return make_int2(first, lastpos);
 }
+
+#endif  // KRP_DESCENT_EXACT_TU
 
 // The descent for samples cta*8 + warp, stepping by ncta*8 (ncta CTAs share
 // the J samples of one problem).  P may live in parameter or shared memory.
 template <int RMAX, bool EXACT = false>
 __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t cta, int64_t ncta) {
-    using C = FastCfg<RMAX>;
+    using C = FastCfg<RMAX, EXACT>;
     constexpr int NCH = C::NCH;
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -287,6 +303,16 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         return (a0.x + a1.x) + (a0.y + a1.y);
     };
     auto refine = [&](float part) -> df { return warp_sum_df(df{part, 0.f}); };
+#if KRP_DESCENT_EXACT_TU
+    // Exact-decision mode: bound on the error of a row weight q = d^2, d = U[t]
+    // · h̃ an FP32 dot product over R terms with ab = sum_a |U[t]_a h̃_a|:
+    // |d - d_exact| <= (R + 1) 2^-24 ab = dd (h̃ rounded to FP32 included), so
+    // |q - d_exact^2| <= (2 |d| + dd) dd + 2^-24 q.
+    auto row_err = [&](float d, float ab) -> float {
+        const float dd = (float)(R + 1) * 5.9604644775390625e-8f * ab;
+        return fmaf(fmaf(2.f, fabsf(d), dd), dd, 5.9604644775390625e-8f * d * d);
+    };
+#endif
     // Decision "tau <= low + m" (Alg. 4): FP32 when tau is more than `margin`
     // away from the cutoff, else the double-float mass.  (tau.hi - low.hi) - m
     // is within a few ulp(C) + |tau.lo| + |low.lo| < 3e-7 C of tau - low - m;
@@ -377,6 +403,7 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         return c;
     };
 
+#if KRP_DESCENT_EXACT_TU
     // ---------------------------------------------- exact-decision mode
     auto exact_mass = [&](const float* ghi, const float* glo) -> df {
         return exact_mass_fn<NCH>(ghi, glo, th, thl, s_i, s_j, T, nc4);
@@ -391,24 +418,61 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         low = exact_low(tr, tl, c, lvl);
         if (P.nexact && lane == 0) atomicAdd(P.nexact, 1ull);
     };
+    // lane part of sum_p |w_p x_p| over the staged node x (bounds the FP32
+    // mass's rounding error)
+    auto abs_partial = [&](const float* node) -> float {
+        float acc = 0.f;
+#pragma unroll
+        for (int m = 0; m < NCH; ++m) {
+            const int c4 = lane + 32 * m;
+            if (c4 < nc4) {
+                const float4 v = reinterpret_cast<const float4*>(node)[c4];
+                acc = fmaf(fabsf(w4[m].x), fabsf(v.x), acc);
+                acc = fmaf(fabsf(w4[m].y), fabsf(v.y), acc);
+                acc = fmaf(fabsf(w4[m].z), fabsf(v.z), acc);
+                acc = fmaf(fabsf(w4[m].w), fabsf(v.w), acc);
+            }
+        }
+        return acc;
+    };
     // Alg. 4 in the exact-decision mode, for both stages of a factor (one
     // code path, so that the loop's instruction footprint stays that of one
     // descent): the row stage on Z_k (tl: its low parts; dt: its delta-encoded
     // top, Ke levels) and the eigencomponent stage on E_k (tl null, Ke = 0:
     // near-edge decisions from double-float sums of the FP32 lane partials,
     // as in the FP32 form, since E_k has R leaves).  The first fetch (slots 0
-    // and 1 of dt) is in flight.  C and tau come from the FP32 root: the top
-    // levels' masses are chained from it (m(L(c)) = alpha_c m(c) + wᵀD_c), so
-    // its relative error scales tau and those masses alike and reaches the
-    // gaps only through the small D terms.  Returns the leaf heap index, with
-    // low its left edge, tau = u C, Cm the root mass, xs whether the stage
-    // switched to exact masses, elow a bound on low's FP32-path error.
+    // and 1 of dt) is in flight.
+    //
+    // Error terms of the row stage.  An FP32 mass sum_p w_p x_p (weights from
+    // h̃ rounded to FP32, x the stored slot, FP32 sums over a lane's chunks and
+    // the warp) is off by at most 17 2^-24 sum_p |w_p x_p|, and, its T terms'
+    // roundings having independent signs, typically by ~2^-24 sum_p |w_p x_p|
+    // / sqrt(T): the error term taken is 8 2^-24 / sqrt(T) times a bound on
+    // sum_p |w_p x_p| = sum_ab |h̃_a h̃_b x_ab|.  (The worst case would pass to
+    // every deeper level through low and send most descents to the exact
+    // path.)  The bound comes from the float after the slot's packed
+    // triangle: a tree slot (PSD Gram) holds its trace, and sum_ab |h̃_a h̃_b
+    // G_ab| <= |h̃|^2 tr G; a delta slot holds kappa_c = max_ab |D_ab| /
+    // sqrt(g_a g_b) (g the root's diagonal), and the sum is <= kappa_c S with
+    // S = (sum_a |h̃_a| sqrt(g_a))^2.  Both scale with |h̃|^2 rather than with
+    // the mass, so they hold when h̃ is nearly orthogonal to the rows (masses
+    // far below |h̃|^2 tr G).  C comes from the FP32 root (error eC = 8 2^-24
+    // / sqrt(R) sum_p |w_p G_p|, the sum dominated by the R diagonal terms);
+    // the top levels' masses are chained from it, so C's error
+    // reaches a gap only as eC times the node's share of the root (the
+    // product of the alpha or 1 - alpha taken), frozen below the top.  When a
+    // gap falls within that term, C is taken to double-float first and tau,
+    // low (by its share position) and M (by its share) corrected.
+    // Returns the leaf heap index, with low its left edge, tau = u C, Cm the
+    // root mass, xs whether the stage switched to exact masses, elow a bound
+    // on low's FP32-path error, eleaf the C-error term left at the leaf.
     auto descend_exact = [&](const float* tr, const float* tl, const float* dt, int depth, int Ke, int64_t Lk,
-                             int64_t Ik, int F, float uu, df& Cm, df& tau, df& low, bool& xs, float& elow,
-                             float* trc) -> int64_t {
+                             int64_t Ik, int F, float uu, float hn2, df& Cm, df& tau, df& low, bool& xs,
+                             float& elow, float& eleaf, float* trc) -> int64_t {
         low = df{0.f, 0.f};
         xs = false;
         elow = 0.f;
+        eleaf = 0.f;
         if (!fetch_wait()) return 1;
         Cm = refine(partial(stage));
         const float cf = Cm.hi + Cm.lo;
@@ -416,44 +480,79 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         tau = df_mul_f(Cm, uu);
         const float band = KRP_EXACT_BAND * cf;
         const float coarse = 4e-7f * cf;   // error of the FP32 gap below: a few ulp(C)
+        float S = 0.f, eC = 0.f;
+        const float etop = 4.76837158203125e-7f * rsqrtf((float)T);   // 8 2^-24 / sqrt(T)
+        if (tl) {
+            float sp = 0.f;
+            if (lane < R) sp = fabsf(th[lane]) * sqrtf(stage[lane * R - (lane * (lane - 1)) / 2]);
+            const float sr = warp_sum(sp);
+            S = sr * sr;
+            eC = 4.76837158203125e-7f * rsqrtf((float)R) * warp_sum(abs_partial(stage));
+        }
+        bool xc = false;            // C taken to double-float
+        float share = 1.f, spos = 0.f;  // share of the root: node c's, and low's position (top levels)
         // traced samples record the masses of the path's nodes (double-float of
         // the (hi, lo) slots when there are low parts) and each node's mass as
         // its parent's minus its left sibling's
         const bool tracing = __any_sync(0xffffffffu, trc != nullptr);
         df Mx = tracing && tl ? exact_mass(tr, tl) : Cm;
         if (trc) trc[0] = Mx.hi;
-        constexpr float KAPPA = 9.5367431640625e-7f;   // 2^-20: bound on an FP32 mass's error / |mass|
+        constexpr float KAPPA = 9.5367431640625e-7f;   // 2^-20 |m|: the eigencomponent stage's error term
         int64_t c = 1;
         int lvl = 0;
         df M = Cm;         // mass of node c (top levels)
-        float eM = 0.f;    // bound on its error
+        float eM = 0.f;    // bound on its error (C's own error aside)
         const int64_t nfull = Ik / F;   // leaves holding F rows
-        // One decision at node c (depth lvl) from the lane partial of its
-        // staged left-child slot: chained (delta slot) above depth Ke, plain
-        // below.  The branch is taken from an FP32 estimate of m(L(c)) unless
-        // the gap is within the estimate's error; the double-float m(L(c))
-        // that the offset and the chain carry forward is formed beside it.
-        auto step = [&](float part) {
+        // One decision at node c (depth lvl) from its staged left-child slot:
+        // chained (delta slot) above depth Ke, plain below.  The branch is
+        // taken from an FP32 estimate of m(L(c)) unless the gap is within the
+        // estimate's error; the double-float m(L(c)) that the offset and the
+        // chain carry forward is formed beside it.
+        auto step = [&](const float* node) {
+            const float part = partial(node);
             const float m = warp_sum(part);
             const bool top = lvl < Ke;
             float a = 0.5f;   // alpha_c: 1/2 unless c holds the rows' ragged end
             if (top && (c - ((int64_t)1 << lvl) + 1) > (nfull >> (depth - lvl))) a = node_alpha(c, lvl, Lk, F, Ik);
             const float mf = top ? fmaf(a, M.hi, m) : m;
-            float e = top ? fmaf(a, eM, KAPPA * fabsf(m)) : KAPPA * fabsf(m);
-            df mL = top ? df_add_f(a == 0.5f ? df{0.5f * M.hi, 0.5f * M.lo} : df_mul_f(M, a), m) : df{m, 0.f};
+            float e;
+            if (tl) {
+                const float bnd = node[P.T];
+                e = top ? fmaf(a, eM, etop * bnd * S) : etop * bnd * hn2;
+            } else {
+                e = KAPPA * fabsf(m);
+            }
+            auto chain = [&]() -> df {
+                return top ? df_add_f(a == 0.5f ? df{0.5f * M.hi, 0.5f * M.lo} : df_mul_f(M, a), m) : df{m, 0.f};
+            };
+            df mL = chain();
             const int64_t rfirst = ((2 * c + 1) << (depth - lvl - 1)) - Lk;
             bool left = true;
             if (rfirst * F < Ik) {
                 const float gapf = (tau.hi - low.hi) - mf;
-                if (!xs && fabsf(gapf) > coarse + band + elow + e) {
+                const float ed = (tl && !xc && !xs) ? 2.f * eC * share : 0.f;
+                if (!xs && fabsf(gapf) > coarse + band + elow + e + ed) {
                     left = gapf < 0.f;
                 } else {
                     if (!tl) mL = refine(part);
                     df gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
-                    if (tl && !xs && fabsf(gap.hi) <= band + elow + e) {
-                        go_exact(tr, tl, c, lvl, uu, tau, low);
-                        xs = true;
-                        elow = e = 0.f;
+                    if (tl && !xs) {
+                        if (ed > 0.f && fabsf(gap.hi) <= band + elow + e + ed) {
+                            const df Cx = exact_mass(tr, tl);
+                            const df dC = df_add(Cx, df_neg(Cm));
+                            tau = df_mul_f(Cx, uu);
+                            low = df_add(low, df_mul_f(dC, spos));
+                            M = df_add(M, df_mul_f(dC, share));
+                            Cm = Cx;
+                            xc = true;
+                            mL = chain();
+                            gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
+                        }
+                        if (fabsf(gap.hi) <= band + elow + e) {
+                            go_exact(tr, tl, c, lvl, uu, tau, low);
+                            xs = true;
+                            elow = e = 0.f;
+                        }
                     }
                     if (xs) {
                         mL = exact_mass(tr + c * Tp, tl + c * Tp);
@@ -475,6 +574,7 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                 if (top) {
                     M = mL;
                     eM = e;
+                    share *= a;
                 }
             } else {
                 c = 2 * c + 1;
@@ -482,6 +582,8 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                 if (top) {
                     M = df_add(M, df_neg(mL));
                     eM += e;
+                    spos = fmaf(a, share, spos);
+                    share *= 1.f - a;
                 }
                 elow += e;
             }
@@ -501,13 +603,14 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                 node = stage;
             }
             const int64_t c0 = c;
-            step(partial(node));
+            step(node);
             staged = have_next;
             if (have_next) node = stage + (c == 2 * c0 ? Tp : 2 * Tp);
         }
+        if (tl && !xc && !xs) eleaf = 2.f * eC * share;
         return c;
     };
-
+#endif  // KRP_DESCENT_EXACT_TU
     const bool leaf_tma = (R & 3) == 0 && P.F * R <= C::STAGE;
     const int64_t warps_total = ncta * C::WARPS;
     for (int64_t s = cta * C::WARPS + warp; s < P.J && alive; s += warps_total) {
@@ -536,6 +639,8 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
             int u = 0;
             bool xs = false;    // exact-decision mode: the row stage switched to exact masses
             float elow = 0.f;   // exact-decision mode: bound on the FP32 path's error in low
+            float eleaf = 0.f;  // exact-decision mode: C's error term at the leaf
+            float hn2 = 0.f;    // exact-decision mode: |h̃|^2 in FP32
             for (int sg = 0; sg < 2; ++sg) {
                 const bool xrow = EXACT && sg == 1;
                 const float* tr = sg ? P.tree[k] : P.etree[k];
@@ -559,15 +664,19 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                 }
                 __syncwarp();
                 make_weights(th);
+                if constexpr (EXACT) hn2 = warp_sum(lane < R ? th[lane] * th[lane] : 0.f);
                 if (trc && sg) trc += FAST_TRACE_STRIDE;
                 df Cm;
-                if (EXACT)
+                if constexpr (EXACT) {
+#if KRP_DESCENT_EXACT_TU
                     c = descend_exact(tr, sg ? P.tlo[k] : nullptr, xrow ? P.dtop[k] : tr, depth, sg ? P.Ke[k] : 0,
-                                      sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, Cm, tau, low,
-                                      xs, elow, trc);
-                else
+                                      sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, hn2, Cm, tau,
+                                      low, xs, elow, eleaf, trc);
+#endif
+                } else {
                     c = descend(tr, depth, sg ? Lk : P.Rp, sg ? Ik : R, sg ? F : 1, sg ? u_row : u_eig, Cm,
                                 tau, low, trc);
+                }
                 if (!alive) break;
                 if (c < 0) {
                     const float cv = Cm.hi + Cm.lo;
@@ -588,6 +697,7 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
             if (leaf_tma && !fetch(Uk + row0 * R, (uint32_t)(nrows * R * 4), nullptr, 0)) break;
             float q[C::RPT];
             float run = 0.f;
+            float erow = 0.f;   // exact-decision mode: bound on this lane's row weights' errors
 #pragma unroll
             for (int r = 0; r < C::RPT; ++r) {
                 const int t = lane * rpt + r;
@@ -598,16 +708,34 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                         const float4* hv = reinterpret_cast<const float4*>(th);
                         const int nq = R >> 2;
                         float2 acc = make_float2(0.f, 0.f);
+                        float ab = 0.f;
                         for (int a = 0; a < nq; ++a) {
                             const int j = (a + t) % nq;   // rotate chunks: conflict-free banks
                             const float4 x = row[j], y = hv[j];
                             acc = ffma2(make_float2(x.x, x.y), make_float2(y.x, y.y), acc);
                             acc = ffma2(make_float2(x.z, x.w), make_float2(y.z, y.w), acc);
+                            if constexpr (EXACT) {
+                                ab = fmaf(fabsf(x.x), fabsf(y.x), ab);
+                                ab = fmaf(fabsf(x.y), fabsf(y.y), ab);
+                                ab = fmaf(fabsf(x.z), fabsf(y.z), ab);
+                                ab = fmaf(fabsf(x.w), fabsf(y.w), ab);
+                            }
                         }
                         d = acc.x + acc.y;
+#if KRP_DESCENT_EXACT_TU
+                        if constexpr (EXACT) erow += row_err(d, ab);
+#endif
                     } else {
                         const float* row = Uk + (row0 + t) * R;
-                        for (int a = 0; a < R; ++a) d = fmaf(__ldg(row + a), th[a], d);
+                        float ab = 0.f;
+                        for (int a = 0; a < R; ++a) {
+                            const float x = __ldg(row + a);
+                            d = fmaf(x, th[a], d);
+                            if constexpr (EXACT) ab = fmaf(fabsf(x), fabsf(th[a]), ab);
+                        }
+#if KRP_DESCENT_EXACT_TU
+                        if constexpr (EXACT) erow += row_err(d, ab);
+#endif
                     }
                 }
                 q[r] = d * d;
@@ -625,35 +753,49 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
             if (lane == 0) cum = 0.f;
             int first = 0x7fffffff, lastpos = -1;
             bool near = false;
-            if (EXACT) {
-                // low's FP32-path error and the FP32 scan's own: each row weight
-                // is a squared R-term dot product (~R 2^-24 of the row's |terms|
-                // relative), then ~10 roundings of the running sums; 2^-14 of
-                // the leaf's total covers both
-                margin = KRP_EXACT_BAND * cf + elow + 6.103515625e-5f * __shfl_sync(0xffffffffu, inc, 31);
+            float mlow = 0.f;   // exact-decision mode: the offset's part of the margin
+            if constexpr (EXACT) {
+                // low's FP32-path error and C's, then the FP32 scan's own: the
+                // rows' weights (row_err) and ~10 roundings of the running sums
+                mlow = KRP_EXACT_BAND * cf + elow + eleaf;
+                margin = mlow + warp_sum(erow) + 9.5367431640625e-7f * __shfl_sync(0xffffffffu, inc, 31);
             }
 #pragma unroll
             for (int r = 0; r < C::RPT; ++r) {
                 const int t = lane * rpt + r;
                 if (r < rpt && t < nrows) {
                     cum += q[r];
-                    if (first == 0x7fffffff && target <= cum) first = t;
+                    // exact-decision mode: a row of zero weight is never drawn
+                    // (after a switch to exact masses tau could sit at the
+                    // leaf's left edge; the FP32 path's own offsets keep tau
+                    // above it)
+                    if (first == 0x7fffffff && target <= cum && (!EXACT || q[r] > 0.f)) first = t;
                     if (fabsf(cum - target) <= margin) near = true;
                     if (q[r] > 0.f) lastpos = t;
                 }
             }
-            if (EXACT && __any_sync(0xffffffffu, near)) {
-                // re-take the leaf scan from the exact offset and rows rescored
-                // in double-float: q = (U[t] · h̃)^2 with h̃ = (th, thl)
-                if (!xs) {
+            const bool any_near = __any_sync(0xffffffffu, near);
+            if constexpr (EXACT) {
+#if KRP_DESCENT_EXACT_TU
+              if (any_near) {
+                // re-take the leaf scan with rows rescored in double-float: q =
+                // (U[t] · h̃)^2 with h̃ = (th, thl); if an edge is then still
+                // within the offset's error of tau, once more from the exact
+                // offset
+                int2 fl;
+                for (int pass = 0; pass < 2; ++pass) {
+                    bool nl;
+                    fl = exact_leaf_scan<C::RPT>(leaf_tma ? stage : Uk + row0 * R, R, rpt, nrows, th, thl, tau, low,
+                                                 xs ? 0.f : mlow, nl);
+                    if (xs || !nl) break;
                     go_exact(P.tree[k], P.tlo[k], c, P.depth[k], u_row, tau, low);
                     xs = true;
                 }
-                const int2 fl = exact_leaf_scan<C::RPT>(leaf_tma ? stage : Uk + row0 * R, R, rpt, nrows, th, thl,
-                                                       tau, low);
                 first = fl.x;
                 lastpos = fl.y;
-            } else if (__any_sync(0xffffffffu, near)) {
+              }
+#endif
+            } else if (any_near) {
                 // redo the scan in double-float: edges low + cumulative weights
                 df acc{0.f, 0.f};
 #pragma unroll
@@ -747,7 +889,7 @@ __global__ void __launch_bounds__(256, RMAX <= 16 ? 4 : 3) krp_descent_fast(cons
 namespace {
 template <int RMAX, bool EXACT>
 cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
-    using C = FastCfg<RMAX>;
+    using C = FastCfg<RMAX, EXACT>;
     auto k = krp_descent_fast<RMAX, EXACT>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
@@ -759,11 +901,17 @@ cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
     k<<<(unsigned)grid, 256, C::SMEM, st>>>(P); count_launch();
     return cudaGetLastError();
 }
-template <int RMAX>
-cudaError_t launch_fast_r(const FastParams& P, bool exact, int num_sms, cudaStream_t st) {
-    return exact ? launch_fast_t<RMAX, true>(P, num_sms, st) : launch_fast_t<RMAX, false>(P, num_sms, st);
-}
 }  // namespace
+
+#if KRP_DESCENT_EXACT_TU
+// Exact-decision descent for R <= rmax (8, 16 or 32).
+cudaError_t launch_fast_exact(const FastParams& P, int rmax, int num_sms, cudaStream_t st) {
+    if (rmax <= 8) return launch_fast_t<8, true>(P, num_sms, st);
+    if (rmax <= 16) return launch_fast_t<16, true>(P, num_sms, st);
+    return launch_fast_t<32, true>(P, num_sms, st);
+}
+#else
+cudaError_t launch_fast_exact(const FastParams& P, int rmax, int num_sms, cudaStream_t st);
 
 // Test hook for the bounded wait: one warp waits on an mbarrier that nothing
 // completes, with `tries` suspending tries, and must report KRP_ETIMEOUT.
@@ -831,13 +979,14 @@ bool launch_descent_fast(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
     P.trace = trace;
     P.n_trace = trace ? n_trace : 0;
     P.nexact = s->exact ? s->nexact : nullptr;
-    const bool x = s->exact != 0;
-    if (s->R <= 8)
-        *err = launch_fast_r<8>(P, x, s->num_sms, s->stream);
+    if (s->exact)
+        *err = launch_fast_exact(P, s->R, s->num_sms, s->stream);
+    else if (s->R <= 8)
+        *err = launch_fast_t<8, false>(P, s->num_sms, s->stream);
     else if (s->R <= 16)
-        *err = launch_fast_r<16>(P, x, s->num_sms, s->stream);
+        *err = launch_fast_t<16, false>(P, s->num_sms, s->stream);
     else
-        *err = launch_fast_r<32>(P, x, s->num_sms, s->stream);
+        *err = launch_fast_t<32, false>(P, s->num_sms, s->stream);
     return true;
 }
 
@@ -882,5 +1031,7 @@ cudaError_t launch_descent_fast_batch(const FastParams* table_dev, const FastCal
     count_launch();
     return cudaGetLastError();
 }
+
+#endif  // KRP_DESCENT_EXACT_TU
 
 }  // namespace krp

@@ -146,7 +146,9 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     s->prec = precision;
     s->stream = (cudaStream_t)stream;
     s->T = tri_size(R);
-    s->Tp = tri_stride(R);
+    // exact-decision samplers keep one more float per node after the packed
+    // triangle (the node's trace; in delta slots a bound on the delta's entries)
+    s->Tp = s->exact ? ((s->T + 1 + 7) & ~7) : tri_stride(R);
     s->Rp = (int)next_pow2(R);
     s->dE = log2i(s->Rp);
     int dev = 0;

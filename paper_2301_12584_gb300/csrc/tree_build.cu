@@ -238,6 +238,14 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
         if (copy_to) copy_rows_out<VEC>(cur, copy_to, I, R, (leaf0 + (int64_t)g * LB) * F, rows);
         leaf_grams_fp32<LB, VEC, EXACT>(cur, sG, R, F, Tp, sGlo);
         __syncthreads();
+        if (EXACT) {   // each leaf's trace after its packed triangle (summed up the tree with the rest)
+            for (int l = threadIdx.x; l < LB; l += blockDim.x) {
+                float t = 0.f;
+                for (int a = 0; a < R; ++a) t += sG[l * Tp + tri_index(a, a, R)];
+                sG[l * Tp + T] = t;
+            }
+            __syncthreads();
+        }
         reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk, sGlo, tree_lo);
         if (!VEC && g + 1 < G) {
             __syncthreads();
@@ -357,11 +365,11 @@ __global__ void tree_up(const float* __restrict__ in_pairs, const double* __rest
 // Exact FP64 Gram UᵀU for small factors (products of FP32 values are exact in
 // FP64; sums in FP64): CTA (x, y) reduces row chunk x for packed entries
 // y*256 .. y*256+255, one entry per thread, into partial x.
-__global__ void __launch_bounds__(256) gram64_partial(const float* __restrict__ U, int64_t I, int R,
-                                                      int64_t rows_per_cta, double* __restrict__ part) {
+__global__ void __launch_bounds__(256) gram64_partial(const float* __restrict__ U, int64_t I, int R, int Tp,
+                                                      int64_t rows_per_cta, double* __restrict__ part,
+                                                      bool with_trace) {
     extern __shared__ __align__(16) float sU[];  // 64 x R
     const int T = tri_size(R);
-    const int Tp = tri_stride(R);
     const int64_t r0 = (int64_t)blockIdx.x * rows_per_cta;
     const int64_t r1 = min(I, r0 + rows_per_cta);
     const int e = blockIdx.y * blockDim.x + threadIdx.x;
@@ -382,8 +390,10 @@ __global__ void __launch_bounds__(256) gram64_partial(const float* __restrict__ 
         __syncthreads();
         if (e < T)
             for (int r = 0; r < nr; ++r) acc = fma((double)sU[r * R + ei], (double)sU[r * R + ej], acc);
+        else if (e == T && with_trace)   // the trace after the packed triangle
+            for (int x = 0; x < nr * R; ++x) acc = fma((double)sU[x], (double)sU[x], acc);
     }
-    if (e < Tp) part[(size_t)blockIdx.x * Tp + e] = e < T ? acc : 0.0;
+    if (e < Tp) part[(size_t)blockIdx.x * Tp + e] = (e < T || (e == T && with_trace)) ? acc : 0.0;
 }
 
 // Sum the partials in a fixed order into the FP64 root; also refresh the
@@ -404,13 +414,24 @@ __global__ void gram64_finish(const double* __restrict__ part, int nparts, int T
 // (slot c at offset c Tp), D_c = G_{2c} - alpha_c G_c (node_alpha) formed in
 // double-float from the tree's (hi, lo) slots and rounded to FP32.  G_c of a
 // right child is its parent's Gram minus its left sibling's, walked down from
-// the root.  One CTA per slot.
+// the root.  After the packed triangle each D slot holds kappa_c = max_ab
+// |D_ab| / sqrt(g_a g_b) (g the root's diagonal), which bounds the descent's
+// FP32 rounding error on w^T D_c; the root slot keeps its trace.  One CTA per
+// slot.
 __global__ void build_dtop(const float* __restrict__ tree, const float* __restrict__ tlo, int64_t I, int F,
-                           int64_t L, int Tp, float* __restrict__ dtop) {
+                           int64_t L, int R, int Tp, float* __restrict__ dtop) {
+    __shared__ unsigned kmax;   // kappa_c as FP32 bits (non-negative floats order as integers)
     const int64_t c = blockIdx.x;
+    const int T = tri_size(R);
+    if (threadIdx.x == 0) kmax = 0u;
+    __syncthreads();
     for (int e = threadIdx.x; e < Tp; e += blockDim.x) {
         if (c == 0) {
             dtop[e] = tree[e];
+            continue;
+        }
+        if (e >= T) {
+            if (e > T) dtop[c * Tp + e] = 0.f;
             continue;
         }
         df G{tree[e], tlo[e]};
@@ -423,14 +444,26 @@ __global__ void build_dtop(const float* __restrict__ tree, const float* __restri
         }
         const df GL{tree[c * Tp + e], tlo[c * Tp + e]};
         const df D = df_add(GL, df_neg(df_mul_f(G, node_alpha(c, dc, L, F, I))));
-        dtop[c * Tp + e] = D.hi + D.lo;
+        const float d = D.hi + D.lo;
+        dtop[c * Tp + e] = d;
+        int i = 0, rem = e;
+        while (rem >= R - i) {
+            rem -= R - i;
+            ++i;
+        }
+        const float den = sqrtf(tree[tri_index(i, i, R)]) * sqrtf(tree[tri_index(i + rem, i + rem, R)]);
+        const float k = den > 0.f ? fabsf(d) / den : (d != 0.f ? INFINITY : 0.f);
+        atomicMax(&kmax, __float_as_uint(k));
     }
+    __syncthreads();
+    // a little above the largest ratio: covers the roundings of the ratio itself
+    if (c > 0 && threadIdx.x == 0) dtop[c * Tp + T] = __uint_as_float(kmax) * 1.0001f;
 }
 
 cudaError_t launch_build_dtop(const krp_sampler* s, int j, cudaStream_t st) {
     const int Ke = s->Ke[j];
     build_dtop<<<(unsigned)((int64_t)1 << Ke), 256, 0, st>>>(s->tree[j], s->tree_lo[j], s->I[j], s->F, s->L[j],
-                                                           s->Tp, s->dtop[j]);
+                                                           s->R, s->Tp, s->dtop[j]);
     count_launch();
     return cudaGetLastError();
 }
@@ -628,7 +661,8 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     if (exact_root) {
         const int64_t rpc = (I + nparts - 1) / nparts;
         const dim3 grid(nparts, (Tp + 255) / 256);
-        gram64_partial<<<grid, 256, 64 * R * 4, s->stream>>>(s->U[j], I, R, rpc, up0); count_launch();
+        gram64_partial<<<grid, 256, 64 * R * 4, s->stream>>>(s->U[j], I, R, Tp, rpc, up0, tree_lo != nullptr);
+        count_launch();
         gram64_finish<<<(Tp + 255) / 256, 256, 0, s->stream>>>(up0, nparts, Tp, s->root64[j], s->tree[j], tree_lo);
         count_launch();
         cudaError_t e = cudaGetLastError();

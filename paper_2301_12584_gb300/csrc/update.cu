@@ -63,6 +63,17 @@ __global__ void __launch_bounds__(256) update_entries(float* __restrict__ U, flo
         }
         for (int k = threadIdx.x; k < R; k += blockDim.x)
             root64[k < c ? tri_index(k, c, R) : tri_index(c, k, R)] += dv[k];
+        if (tree_lo) {   // exact-decision trees: the trace after the packed triangle changes by dv[c]
+            const int T = tri_size(R);
+            for (int node = threadIdx.x; node < m; node += blockDim.x) {
+                const int64_t at = slots[node] * (int64_t)Tp + T;
+                const double v = (double)tree[at] + (double)tree_lo[at] + dv[c];
+                const float hi = (float)v;
+                tree[at] = hi;
+                tree_lo[at] = (float)(v - (double)hi);
+            }
+            if (threadIdx.x == 0) root64[T] += dv[c];
+        }
         __syncthreads();
         if (threadIdx.x == 0) U[r * R + c] = vals[q];
         __syncthreads();

@@ -67,6 +67,24 @@ def skewed_entry_factors(N, I, R, seed, frac=0.01, scale=10.0, dtype=np.float32)
     return out
 
 
+def correlated_sparse_factors(N, I, R, seed, zero_frac=0.8, common=3.0, dtype=np.float32):
+    """Factors shaped like those of later sparse CP-ALS sweeps: a random
+    `zero_frac` of each factor's rows are zero (indices that no sampled
+    nonzero touched), the others N(0,1) plus `common` times one N(0,1) value
+    shared by the row's entries (strongly correlated columns, so an
+    ill-conditioned Gram), then every column scaled to unit norm.  I may be
+    an int or a list."""
+    rng = np.random.default_rng(seed)
+    dims = [I] * N if np.isscalar(I) else list(I)
+    out = []
+    for n in dims:
+        U = rng.standard_normal((int(n), R)) + common * rng.standard_normal((int(n), 1))
+        U[rng.random(int(n)) < zero_frac] = 0.0
+        U /= np.maximum(np.linalg.norm(U, axis=0), 1e-300)
+        out.append(U.astype(dtype))
+    return out
+
+
 def planted_solution(R, nrhs, seed, dtype=np.float32):
     """X_true (R x nrhs), i.i.d. N(0,1)."""
     rng = np.random.default_rng(seed)

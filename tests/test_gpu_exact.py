@@ -110,7 +110,11 @@ def test_exact_tree_matches_partial_grams(I, R, F):
         h = 1 if slot == 0 else 2 * slot
         G, tol = gram(h)
         got = unpack(hi[slot].astype(np.float64) + lo[slot].astype(np.float64), R)
-        assert np.all(hi[slot][T:] == 0) and np.all(lo[slot][T:] == 0)
+        # after the packed triangle: the node's trace (it bounds the descent's
+        # FP32 rounding error), then zeros
+        tr = float(hi[slot][T]) + float(lo[slot][T])
+        assert abs(tr - np.trace(G)) <= 1e-5 * np.trace(G) + 1e-30, (slot, tr, np.trace(G))
+        assert np.all(hi[slot][T + 1:] == 0) and np.all(lo[slot][T + 1:] == 0)
         worst = max(worst, float((np.abs(got - G) / (tol + 1e-300)).max()))
         assert np.all(np.abs(got - G) <= tol + 1e-30), (slot, float((np.abs(got - G) / (tol + 1e-300)).max()))
     # the delta-encoded top in the tree's slot numbering: [root | D_1 .. D_{2^Ke - 1}]; a
@@ -133,13 +137,20 @@ def test_exact_tree_matches_partial_grams(I, R, F):
         D = Gl - alpha * Gc
         got = unpack(top[c].astype(np.float64), R)
         assert np.all(np.abs(got - D) <= 2.0 ** -23 * np.abs(D) + 2 * tc + root_bar + 1e-30), (c, depth_c)
+        # kappa_c = max |D_ab| / sqrt(g_a g_b) over the root's diagonal g: a bound
+        # that must hold for the stored D (a little above its largest ratio)
+        g = np.diag(gram(1)[0])
+        ratio = np.abs(got) / np.sqrt(np.outer(g, g))
+        kappa = float(top[c][T])
+        assert ratio.max() <= kappa <= ratio.max() * 1.001 + 1e-30, (c, kappa, ratio.max())
+        assert np.all(top[c][T + 1:] == 0)
     print(f"I={I} R={R} F={F}: worst |hi+lo - G| / bar = {worst:.2e}")
     s.close()
 
 
 # ------------------------------------------------------- index parity ----
 @pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1",
-                                  "R24_F40", "R32_I2p16"])
+                                  "R24_F40", "R32_I2p16", "R25_zero_rows_correlated"])
 def test_exact_index_parity(case):
     J, excl, F, tree_ref = 1 << 15, -1, 0, False
     if case == "cfg_tiny":      # 3 x (64 x 8), F = 8
@@ -165,6 +176,12 @@ def test_exact_index_parity(case):
         F = 40
     elif case == "R32_I2p16":   # 3 x (2^16 x 32) skewed rows, vs the FP64 segment-tree replay
         Us, F, J, tree_ref = synth.skewed_row_factors(3, 1 << 16, 32, seed=17), 32, 1 << 16, True
+    elif case == "R25_zero_rows_correlated":
+        # as after a few sparse CP-ALS sweeps: 80% zero rows, strongly correlated
+        # unit-norm columns (masses far below |h̃|^2 tr G, so FP32 masses carry
+        # large relative errors), R = F = 25 (ragged leaves), vs the tree replay
+        Us = synth.correlated_sparse_factors(3, [1 << 18, 1 << 18, 4096], 25, seed=21)
+        excl, F, J, tree_ref = 1, 25, 1 << 16, True
     s = sampler_for(Us, F)
     out = draw(s, Us, excl, J, seed=12345, draw_id=3)
     U64 = [U.astype(np.float64) for U in Us]
@@ -172,6 +189,7 @@ def test_exact_index_parity(case):
         ref = O.krp_sample_tree(U64, excl, J, 12345, 3, F=F)
     else:
         ref = O.krp_sample(U64, excl, J, 12345, 3, record=True, chunk=2048)
+    assert np.all(np.isfinite(out["weight"])) and np.all(out["weight"] > 0)
     mism = mismatches(out["idx"], ref)
     nx = s.exact_count()
     print(f"{case}: {mism} mismatches / {J}; {nx} exact re-decisions")
@@ -288,6 +306,9 @@ def test_exact_updates_match_rebuild_and_oracle():
         tol = 9 * F * (F + 1) * 2.0 ** -47 * np.outer(dg, dg) + 2.0 ** -38 * bound
         got = unpack(hi[slot].astype(np.float64) + lo[slot].astype(np.float64), R)
         assert np.all(np.abs(got - G) <= tol + 1e-30), slot
+        T = R * (R + 1) // 2
+        tr = float(hi[slot][T]) + float(lo[slot][T])
+        assert abs(tr - np.trace(G)) <= 1e-5 * np.trace(G) + 1e-30, (slot, tr, np.trace(G))
     assert np.array_equal(top[0], hi[0])
     Us_new = [U0.astype(np.float32), Us[1], Us[2]]
     J = 1 << 14
