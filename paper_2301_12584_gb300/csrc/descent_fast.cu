@@ -131,21 +131,6 @@ __device__ __forceinline__ df exact_mass_fn(const float* ghi, const float* glo, 
     }
     return warp_sum_df(acc);
 }
-// low of node c at depth lvl: the exact masses of the left siblings of the
-// path's right turns (the left sibling of a right child n sits at slot n/2).
-template <int NCH>
-__device__ __forceinline__ df exact_low_fn(const float* tr, const float* tl, int64_t c, int lvl, int Tp,
-                                        const float* th, const float* thl, const uint8_t* s_i, const uint8_t* s_j,
-                                        int T) {
-    df lw{0.f, 0.f};
-    for (int t = 0; t < lvl; ++t) {
-        const int64_t n = c >> (lvl - 1 - t);   // path node at depth t + 1
-        if (n & 1)
-            lw = df_add(lw, exact_mass_fn<NCH>(tr + (n >> 1) * Tp, tl + (n >> 1) * Tp, th, thl, s_i, s_j, T, Tp >> 2));
-    }
-    return lw;
-}
-
 // Exact-decision mode: a leaf scan re-taken in double-float, every lane
 // calling with its rows t = lane rpt + r of the leaf (rows: nrows rows of R
 // floats, shared or global): q_t = (U[t] · h̃)^2 with h̃ = (th, thl),
@@ -206,7 +191,9 @@ __device__ __forceinline__ int2 exact_leaf_scan(const float* rows, int R, int rp
 
 // The descent for samples cta*8 + warp, stepping by ncta*8 (ncta CTAs share
 // the J samples of one problem).  P may live in parameter or shared memory.
-template <int RMAX, bool EXACT = false>
+// TRACE (exact-decision kernels): the instantiation that records traces; the
+// others carry no tracing code.
+template <int RMAX, bool EXACT = false, bool TRACE = false>
 __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t cta, int64_t ncta) {
     using C = FastCfg<RMAX, EXACT>;
     constexpr int NCH = C::NCH;
@@ -405,18 +392,36 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
 
 #if KRP_DESCENT_EXACT_TU
     // ---------------------------------------------- exact-decision mode
-    auto exact_mass = [&](const float* ghi, const float* glo) -> df {
-        return exact_mass_fn<NCH>(ghi, glo, th, thl, s_i, s_j, T, nc4);
-    };
-    auto exact_low = [&](const float* tr, const float* tl, int64_t c, int lvl) -> df {
-        return exact_low_fn<NCH>(tr, tl, c, lvl, Tp, th, thl, s_i, s_j, T);
-    };
-    // Switch a row stage to exact masses at node c (depth lvl): C and tau from
-    // the double-float root, low from the path's right turns.
-    auto go_exact = [&](const float* tr, const float* tl, int64_t c, int lvl, float uu, df& tau, df& low) {
-        tau = df_mul_f(exact_mass(tr, tl), uu);
-        low = exact_low(tr, tl, c, lvl);
-        if (P.nexact && lane == 0) atomicAdd(P.nexact, 1ull);
+    // Double-float masses of a row stage's tree (tr, tl: hi and low parts) for
+    // node c at depth lvl, by one rolled loop with a single inlined mass, so
+    // that the rare exact path adds little to the descent's instruction
+    // footprint.  what: 1 = the root (C), 2 = low (the left siblings of the
+    // path's right turns; the left sibling of a right child n sits at slot
+    // n/2), 4 = m(L(c)) (slot c).
+    auto exact_pass = [&](const float* tr, const float* tl, int64_t c, int lvl, int what, df& Cx, df& lowx,
+                          df& chx) {
+        lowx = df{0.f, 0.f};
+#pragma unroll 1
+        for (int t = -1; t <= lvl; ++t) {
+            int64_t slot = -1;
+            if (t < 0) {
+                if (what & 1) slot = 0;
+            } else if (t < lvl) {
+                const int64_t n = c >> (lvl - 1 - t);   // path node at depth t + 1
+                if ((what & 2) && (n & 1)) slot = n >> 1;
+            } else if (what & 4) {
+                slot = c;
+            }
+            if (slot < 0) continue;   // warp-uniform
+            const df m = exact_mass_fn<NCH>(tr + slot * Tp, tl + slot * Tp, th, thl, s_i, s_j, T, nc4);
+            if (t < 0)
+                Cx = m;
+            else if (t < lvl)
+                lowx = df_add(lowx, m);
+            else
+                chx = m;
+        }
+        if ((what & 2) && P.nexact && lane == 0) atomicAdd(P.nexact, 1ull);
     };
     // lane part of sum_p |w_p x_p| over the staged node x (bounds the FP32
     // mass's rounding error)
@@ -494,9 +499,15 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
         // traced samples record the masses of the path's nodes (double-float of
         // the (hi, lo) slots when there are low parts) and each node's mass as
         // its parent's minus its left sibling's
-        const bool tracing = __any_sync(0xffffffffu, trc != nullptr);
-        df Mx = tracing && tl ? exact_mass(tr, tl) : Cm;
-        if (trc) trc[0] = Mx.hi;
+        const bool tracing = TRACE && __any_sync(0xffffffffu, trc != nullptr);
+        df Mx = Cm;
+        if constexpr (TRACE) {
+            if (tracing && tl) {
+                df l0, c0;
+                exact_pass(tr, tl, 1, 0, 1, Mx, l0, c0);
+            }
+            if (trc) trc[0] = Mx.hi;
+        }
         constexpr float KAPPA = 9.5367431640625e-7f;   // 2^-20 |m|: the eigencomponent stage's error term
         int64_t c = 1;
         int lvl = 0;
@@ -536,38 +547,56 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                 } else {
                     if (!tl) mL = refine(part);
                     df gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
-                    if (tl && !xs) {
-                        if (ed > 0.f && fabsf(gap.hi) <= band + elow + e + ed) {
-                            const df Cx = exact_mass(tr, tl);
+                    // row stage: within C's error term, C to double-float
+                    // (tau, low and M corrected through their shares); within
+                    // the FP32 path's error, the switch to exact masses (C, low
+                    // from the path, m(L(c))); once switched, m(L(c)) exact
+                    float edn = ed;
+#pragma unroll 1
+                    for (int pass = 0; tl && pass < 2; ++pass) {
+                        int what = 0;
+                        if (xs)
+                            what = 4;
+                        else if (edn > 0.f && fabsf(gap.hi) <= band + elow + e + edn)
+                            what = 1;
+                        else if (fabsf(gap.hi) <= band + elow + e)
+                            what = xc ? 6 : 7;
+                        if (!what) break;
+                        df Cx, lx, chx;
+                        exact_pass(tr, tl, c, lvl, what, Cx, lx, chx);
+                        if (what & 1) {
                             const df dC = df_add(Cx, df_neg(Cm));
                             tau = df_mul_f(Cx, uu);
-                            low = df_add(low, df_mul_f(dC, spos));
-                            M = df_add(M, df_mul_f(dC, share));
+                            if (!(what & 2)) {
+                                low = df_add(low, df_mul_f(dC, spos));
+                                M = df_add(M, df_mul_f(dC, share));
+                            }
                             Cm = Cx;
                             xc = true;
-                            mL = chain();
-                            gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
+                            edn = 0.f;
                         }
-                        if (fabsf(gap.hi) <= band + elow + e) {
-                            go_exact(tr, tl, c, lvl, uu, tau, low);
+                        if (what & 2) {
+                            low = lx;
                             xs = true;
                             elow = e = 0.f;
                         }
-                    }
-                    if (xs) {
-                        mL = exact_mass(tr + c * Tp, tl + c * Tp);
+                        mL = (what & 4) ? chx : chain();
                         gap = df_add(df_add(tau, df_neg(low)), df_neg(mL));
+                        if (what & 4) break;
                     }
                     left = gap.hi < 0.f || (gap.hi == 0.f && gap.lo <= 0.f);
                 }
             }
-            if (tracing) {
-                const df mx = tl ? exact_mass(tr + c * Tp, tl + c * Tp) : refine(part);
-                if (trc) {
-                    trc[2 + 2 * lvl] = mx.hi;
-                    trc[3 + 2 * lvl] = Mx.hi;
+            if constexpr (TRACE) {
+                if (tracing) {
+                    df mx = refine(part), c0, l0;
+                    if (tl) exact_pass(tr, tl, c, lvl, 4, c0, l0, mx);
+                    if (trc) {
+                        trc[2 + 2 * lvl] = mx.hi;
+                        trc[3 + 2 * lvl] = Mx.hi;
+                    }
+                    Mx = left ? mx : df_add(Mx, df_neg(mx));
                 }
-                Mx = left ? mx : df_add(Mx, df_neg(mx));
             }
             if (left) {
                 c = 2 * c;
@@ -788,7 +817,9 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
                     fl = exact_leaf_scan<C::RPT>(leaf_tma ? stage : Uk + row0 * R, R, rpt, nrows, th, thl, tau, low,
                                                  xs ? 0.f : mlow, nl);
                     if (xs || !nl) break;
-                    go_exact(P.tree[k], P.tlo[k], c, P.depth[k], u_row, tau, low);
+                    df Cx, chx;
+                    exact_pass(P.tree[k], P.tlo[k], c, P.depth[k], 3, Cx, low, chx);
+                    tau = df_mul_f(Cx, u_row);
                     xs = true;
                 }
                 first = fl.x;
@@ -880,17 +911,20 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
 
 // Four CTAs (32 samples) per SM where the registers allow it without spills
 // (RMAX <= 16: 63 registers); at RMAX = 32 a 64-register cap spills and the
-// draw slows from 1.24 to 1.34 ms, so three.
-template <int RMAX, bool EXACT>
-__global__ void __launch_bounds__(256, RMAX <= 16 ? 4 : 3) krp_descent_fast(const __grid_constant__ FastParams P) {
-    descent_fast_body<RMAX, EXACT>(P, blockIdx.x, gridDim.x);
+// draw slows from 1.24 to 1.34 ms, so three.  The exact-decision kernels keep
+// their double-float state in registers at two CTAs per SM (at three they
+// spill, and run slower).
+template <int RMAX, bool EXACT, bool TRACE = false>
+__global__ void __launch_bounds__(256, EXACT ? 2 : (RMAX <= 16 ? 4 : 3))
+    krp_descent_fast(const __grid_constant__ FastParams P) {
+    descent_fast_body<RMAX, EXACT, TRACE>(P, blockIdx.x, gridDim.x);
 }
 
 namespace {
-template <int RMAX, bool EXACT>
+template <int RMAX, bool EXACT, bool TRACE = false>
 cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
     using C = FastCfg<RMAX, EXACT>;
-    auto k = krp_descent_fast<RMAX, EXACT>;
+    auto k = krp_descent_fast<RMAX, EXACT, TRACE>;
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int per_sm = 0;
@@ -906,6 +940,11 @@ cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
 #if KRP_DESCENT_EXACT_TU
 // Exact-decision descent for R <= rmax (8, 16 or 32).
 cudaError_t launch_fast_exact(const FastParams& P, int rmax, int num_sms, cudaStream_t st) {
+    if (P.trace) {
+        if (rmax <= 8) return launch_fast_t<8, true, true>(P, num_sms, st);
+        if (rmax <= 16) return launch_fast_t<16, true, true>(P, num_sms, st);
+        return launch_fast_t<32, true, true>(P, num_sms, st);
+    }
     if (rmax <= 8) return launch_fast_t<8, true>(P, num_sms, st);
     if (rmax <= 16) return launch_fast_t<16, true>(P, num_sms, st);
     return launch_fast_t<32, true>(P, num_sms, st);
