@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--sts-sweeps", type=int, default=12,
                     help="sampler: STS-CP sweeps per precision at R=25 for the metric's second half (0 skips)")
     ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--sts-seeds", type=int, default=3, help="sampler: STS-CP sampling seeds per precision")
     ap.add_argument("--workload", default="sampler",
                     choices=["sampler", "batch512", "rank_sweep", "sparse_als", "accuracy"],
                     help="sampler: the headline line; batch512: 512 small least-squares problems "
@@ -428,12 +429,15 @@ def sparse_setup(nnz, dev, stream):
     return t, scales, {"generate": t_gen, "index": t_index}
 
 
-def sparse_rank_runs(t, scales, R, S, modes, dev, stream):
+def sparse_rank_runs(t, scales, R, S, modes, dev, stream, seeds=(1,)):
     """S STS-CP sweeps (Alg. 6, J = 2^16 per solve) at rank R from the same
     start for each mode in `modes` (fp32, bf16x3, exact: the sampler's
-    precision; fp32_graph: FP32 with sweeps 2..S replayed from a CUDA graph).
-    Per mode: median sweep time of sweeps 2..S and the fit after each sweep
-    (fit not timed)."""
+    precision; fp32_graph: FP32 with sweeps 2..S replayed from a CUDA graph),
+    once per sampling seed in `seeds`.  Per mode: median sweep time of sweeps
+    2..S (over all seeds) and the fit after each sweep (fit not timed).  Each
+    sweep's fit is that of one random sketch, so precisions are compared by
+    the mean fit of the second half of the sweeps averaged over the seeds,
+    next to FP32's own spread over the seeds."""
     import torch
     from paper_2301_12584_gb300 import krpls, synth
     from paper_2301_12584_gb300.krpls import Sampler
@@ -445,33 +449,42 @@ def sparse_rank_runs(t, scales, R, S, modes, dev, stream):
     precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "exact": krpls.KRP_PREC_EXACT,
              "fp32_graph": krpls.KRP_PREC_FP32}
     for mode in modes:
-        s = Sampler(list(dims), R, 0, precs[mode], stream=stream)
-        for k in range(3):
-            s.set_factor(k, Ud[k])
-        sigma = torch.zeros(R, device=dev)
-        times, fits = [], []
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(stream):
-            for sw in range(S):
-                if mode == "fp32_graph" and sw == 1:
-                    s.capture_begin()
-                    s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
-                    s.capture_end()
-                torch.cuda.synchronize()
-                a.record(stream)
-                if mode == "fp32_graph" and sw >= 1:
-                    s.replay()
-                else:
-                    s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
-                b.record(stream)
-                torch.cuda.synchronize()
-                times.append(a.elapsed_time(b))
-                fits.append(s.cp_fit(t, sigma))
-        status = s.sync_status()
-        row[mode] = {"status": status, "sweep_ms_median_2_to_S": statistics.median(times[1:]),
-                     "first_sweep_ms": times[0], "fit_last": fits[-1],
-                     "fit_mean_second_half": statistics.mean(fits[S // 2:]), "fits": [round(f, 6) for f in fits]}
-        s.close()
+        times, per_seed, fits_first, status = [], [], None, 0
+        for seed in seeds:
+            s = Sampler(list(dims), R, 0, precs[mode], stream=stream)
+            for k in range(3):
+                s.set_factor(k, Ud[k])
+            sigma = torch.zeros(R, device=dev)
+            fits = []
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(stream):
+                for sw in range(S):
+                    if mode == "fp32_graph" and sw == 1:
+                        s.capture_begin()
+                        s.cp_als_sweep(t, J, seed, 3 * sw, sigma)
+                        s.capture_end()
+                    torch.cuda.synchronize()
+                    a.record(stream)
+                    if mode == "fp32_graph" and sw >= 1:
+                        s.replay()
+                    else:
+                        s.cp_als_sweep(t, J, seed, 3 * sw, sigma)
+                    b.record(stream)
+                    torch.cuda.synchronize()
+                    if sw >= 1:
+                        times.append(a.elapsed_time(b))
+                    fits.append(s.cp_fit(t, sigma))
+            status = status or s.sync_status()
+            per_seed.append(statistics.mean(fits[S // 2:]))
+            fits_first = fits_first or fits
+            s.close()
+        mean_fit = statistics.mean(per_seed)
+        row[mode] = {"status": status, "sweep_ms_median_2_to_S": statistics.median(times),
+                     "fit_last": fits_first[-1], "fit_mean_second_half": mean_fit,
+                     "fit_mean_second_half_per_seed": [round(f, 7) for f in per_seed],
+                     "seeds": list(seeds), "fits_first_seed": [round(f, 6) for f in fits_first]}
+        if len(per_seed) > 1:
+            row[mode]["seed_spread_rel"] = (max(per_seed) - min(per_seed)) / abs(mean_fit)
     base = row["fp32"]["fit_mean_second_half"] if "fp32" in row else None
     for mode in modes:
         if mode != "fp32" and base:
@@ -767,12 +780,18 @@ def main():
     sts = None
     if world == 1 and args.sts_sweeps > 0:
         t, scales, setup_s = sparse_setup(args.nnz, dev, stream)
-        row = sparse_rank_runs(t, scales, 25, max(3, args.sts_sweeps), ("fp32", "bf16x3", "exact"), dev, stream)
+        seeds = tuple(range(1, max(1, args.sts_seeds) + 1))
+        row = sparse_rank_runs(t, scales, 25, max(3, args.sts_sweeps), ("fp32", "bf16x3", "exact"), dev, stream,
+                               seeds)
         t.close()
         sts = {"workload": f"sts_cp_2^22x2^22x2^14_nnz{int(args.nnz)}_R25_J2^16", "unit": "ms per sweep",
-               "sweeps": max(3, args.sts_sweeps), "setup_s": setup_s,
+               "sweeps": max(3, args.sts_sweeps), "seeds": list(seeds), "setup_s": setup_s,
+               "fit_note": ("fit_mean_second_half: mean fit of sweeps S/2..S, averaged over the sampling seeds; "
+                            "seed_spread_rel: (max - min) of the per-seed means over their mean"),
                **{m: {"sweep_ms_median_2_to_S": row[m]["sweep_ms_median_2_to_S"],
                       "fit_mean_second_half": row[m]["fit_mean_second_half"], "fit_last": row[m]["fit_last"],
+                      "fit_mean_second_half_per_seed": row[m]["fit_mean_second_half_per_seed"],
+                      "seed_spread_rel": row[m].get("seed_spread_rel"),
                       "mean_fit_rel_diff_vs_fp32": row[m].get("mean_fit_rel_diff_vs_fp32"),
                       "status": row[m]["status"]} for m in ("fp32", "bf16x3", "exact")}}
 

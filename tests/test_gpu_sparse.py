@@ -21,9 +21,9 @@ def _lib():
     krpls.lib()
 
 
-def make(dims, R, coords, vals, Us):
+def make(dims, R, coords, vals, Us, prec=0):
     from paper_2301_12584_gb300.krpls import Sampler, SparseTensor
-    s = Sampler(list(dims), R, 0)
+    s = Sampler(list(dims), R, 0, prec)
     for k, U in enumerate(Us):
         s.set_factor(k, torch.from_numpy(np.ascontiguousarray(U, np.float32)).to(DEV))
     t = SparseTensor(dims, coords, vals)
@@ -31,13 +31,16 @@ def make(dims, R, coords, vals, Us):
 
 
 # I_j spans several row tiles of Y M⁻¹ (64, 128 or 256 rows) with a ragged
-# tail; R covers each padded width (32, 64, 128) and R % 4 != 0
+# tail; R covers each padded width (32, 64, 128) and R % 4 != 0.  prec 1
+# (BF16x3 samplers) takes Y M⁻¹ on the tensor cores as TF32x3 for R <= 104.
+@pytest.mark.parametrize("prec", [0, 1])
 @pytest.mark.parametrize("dims,R,J,nnz", [((60, 50, 20), 6, 3000, 4000), ((700, 40, 30), 40, 3000, 20000),
-                                          ((300, 33, 29), 50, 3000, 15000), ((520, 30, 24), 100, 4000, 20000)])
-def test_sparse_solve_matches_oracle_on_gpu_samples(dims, R, J, nnz):
+                                          ((300, 33, 29), 50, 3000, 15000), ((520, 30, 24), 100, 4000, 20000),
+                                          ((1100, 40, 30), 104, 4000, 30000)])
+def test_sparse_solve_matches_oracle_on_gpu_samples(dims, R, J, nnz, prec):
     coords, vals = synth.sparse_zipf_tensor(dims, nnz, seed=3)
     Us = synth.gaussian_factors(3, list(dims), R, seed=4)
-    s, t = make(dims, R, coords, vals, Us)
+    s, t = make(dims, R, coords, vals, Us, prec)
     U64 = [U.astype(np.float64) for U in Us]
     for j in range(3):
         idx = torch.zeros((3, J), dtype=torch.int32, device=DEV)
