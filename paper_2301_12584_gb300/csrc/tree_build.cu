@@ -246,7 +246,7 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
             }
             __syncthreads();
         }
-        reduce_group<LB>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk, sGlo, tree_lo);
+        reduce_group<LB, true, EXACT>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk, sGlo, tree_lo);
         if (!VEC && g + 1 < G) {
             __syncthreads();
             stage_rows<VEC>(sU0, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);

@@ -35,11 +35,15 @@ __device__ __forceinline__ void df_add(float ah, float al, float bh, float bl, f
 // Pairwise sums of one group's LB leaf Grams (entry e), then the binary-counter
 // merge across the CTA's groups, in double-float (DF) or plain FP32 (for leaf
 // Grams that carry ~1e-5 error of their own, where the sums' 2^-24 per level
-// is immaterial).  Stores the FP32 value of every left child created (and its
-// low part into tree_lo, if given); the subtree root of the G groups (the
-// CTA's, or the block `top_slot` of a persistent CTA) goes to top as (hi, lo).
+// is immaterial).  GDF = false keeps DF for the merge across groups and the
+// levels above but sums inside a group in FP32: the few roundings of each
+// group's sum are independent across the many groups of a tree, so they reach
+// the root as ~2^-24 / sqrt(groups) relative, the size of the leaves' own FP32
+// error there.  Stores the FP32 value of every left child created (and its low
+// part into tree_lo, if given); the subtree root of the G groups (the CTA's,
+// or the block `top_slot` of a persistent CTA) goes to top as (hi, lo).
 // sGlo: the leaf Grams' low parts (exactly accumulated leaves), or nullptr.
-template <int LB, bool DF = true>
+template <int LB, bool DF = true, bool GDF = DF>
 __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float* __restrict__ tree,
                                              float* __restrict__ top, int64_t L, int64_t first_leaf,
                                              int g, int G, int Tp, int64_t top_slot,
@@ -59,7 +63,7 @@ __device__ __forceinline__ void reduce_group(const float* sG, float* stk, float*
             h >>= 1;
 #pragma unroll
             for (int l = 0; l < n / 2; ++l) {
-                if (DF)
+                if (GDF)
                     df_add(vh[2 * l], vl[2 * l], vh[2 * l + 1], vl[2 * l + 1], vh[l], vl[l]);
                 else
                     vh[l] = vh[2 * l] + vh[2 * l + 1];
