@@ -535,33 +535,35 @@ def test_full_size_sampler_sampled_outputs():
 
 def test_full_size_rank_sweep_sampled_outputs():
     """The rank sweep's largest launch (N=4 factors of 2^20 x 128, U(-1,1), F=R,
-    J=2^17: the team descent the benchmark times), checked on sampled outputs
-    the oracle computes one by one, replaying the GPU's eigendecompositions
-    (these spectra cluster tightly: reading C26)."""
-    N, I, R, J = 4, 1 << 20, 128, 1 << 17
+    J=2^17: the team descent the benchmark times).  The first 2048 samples of
+    the launch against the batched FP64 segment-tree replay (Alg. 3/4) with
+    the GPU's eigendecompositions (these spectra cluster tightly: reading
+    C26): every mismatch a near-edge flip (tau within 1e-5 C of the oracle's
+    bin edge), their rate printed, and the weights of matching samples within
+    1e-4.  A mass here sums R^2 = 16384 FP32 terms of both signs over 8192
+    leaves per factor and four factors, so the FP32 form flips ~7% of these
+    samples near an edge (measured 138 of 2048); the bound is 10%."""
+    N, I, R, J, n = 4, 1 << 20, 128, 1 << 17, 2048
     Us = synth.uniform_factors(N, I, R, seed=0)
     s = sampler_for(Us, R)
     out = draw(s, Us, -1, J, seed=1, draw_id=0)
     U64 = [U.astype(np.float64) for U in Us]
     eig = {k: s.get_prep(k)[:2] for k in range(N)}
+    s.close()
     prep = O.SamplerPrep(U64, -1, eig)
     for k in prep.incl:
         lam, V = eig[k]
         rec = (V * np.maximum(lam, 0.0)) @ V.T
         # the eigensolver's own bars are test_prepare_matches_fp64_oracle's
         assert np.abs(rec - prep.Ggt[k]).max() <= 1e-5 * np.abs(prep.Ggt[k]).max()
-    picks = np.random.default_rng(2).choice(J, 12, replace=False)
-    mism = 0
-    for d in picks:
-        ref = O.krp_sample(U64, -1, 1, 1, 0, d0=int(d), record=True, prep=prep)
-        got = out["idx"][:, d:d + 1]
-        if (got != ref["idx"]).any():
-            check_index_parity(got, ref, 1)
-            mism += 1
-            continue
-        assert abs(out["weight"][d] * np.sqrt(J) - ref["weight"][0]) <= 1e-4 * ref["weight"][0]
-    assert mism <= 1
-    s.close()
+    ref = O.krp_sample_tree(U64, -1, n, 1, 0, F=R, prep=prep)
+    got = out["idx"][:, :n]
+    mism = check_index_parity(got, ref, n)
+    assert mism <= 0.10 * n
+    same = ~(got != ref["idx"]).any(axis=0)
+    # the oracle's weights are 1/sqrt(n q); the launch drew J samples
+    np.testing.assert_allclose(out["weight"][:n][same] * np.sqrt(J / n), ref["weight"][same], rtol=1e-4)
+    print(f"rank sweep, full size (R = 128): {mism} near-edge mismatches / {n} ({mism / n:.2e})")
 
 
 def test_full_size_index_parity_fp32_band():
