@@ -100,6 +100,8 @@ struct krp_sptensor {
     uint32_t* pu = nullptr;      // per pair: distinct-fiber index
     uint32_t* pn = nullptr;      // per pair: nonzero (fiber order)
     uint32_t* hist = nullptr;
+    float* seg_part = nullptr;   // per chunk of sorted positions: 2 x R partial sums
+    uint32_t* seg_info = nullptr;   // per chunk: 4 words
     size_t lk_J = 0, lk_pairs = 0, lk_hist = 0, lk_R = 0;
 };
 

@@ -10,7 +10,7 @@
 // B operand, K-major hi and lo copies in shared memory, and walks tiles of
 // 128 rows of Y: its threads split the tile into K-major hi and lo copies
 // (8-row x 16-byte core matrices, no swizzle, as the BF16 leaf kernel lays
-// them out), thread 0 issues KP/8 x 3 MMAs (M = 128, N = NP, K = 8 each) into
+// them out; the rows are read into registers a tile ahead), thread 0 issues KP/8 x 3 MMAs (M = 128, N = NP, K = 8 each) into
 // a 128 x NP FP32 accumulator in tensor memory, commits them to an mbarrier
 // that every thread waits on (bounded), and the warps read the accumulator
 // back (warp w: lanes 32 (w mod 4) .., column half w / 4), store U's rows and,
@@ -96,6 +96,9 @@ __device__ __forceinline__ uint32_t mt_off(int p, int k, int kp) {
            (uint32_t)(k & 3) * 4u;
 }
 
+// MT_LD: float4 loads per thread per tile, 128 rows x KP/4 quads over 256
+// threads (4, 7 or 13 for KP <= 32, 56, 104)
+template <int MT_LD>
 __global__ void __launch_bounds__(MT_THREADS) minv_tc(const float* __restrict__ Y, int RSY,
                                                       const double* __restrict__ Minv, int64_t I, int R, int KP,
                                                       int NP, uint32_t tcols, float* __restrict__ U,
@@ -145,27 +148,46 @@ __global__ void __launch_bounds__(MT_THREADS) minv_tc(const float* __restrict__ 
     df ss[2] = {df{0.f, 0.f}, df{0.f, 0.f}};   // this lane's column (32 per chunk) sums, chunks of its half
     const int nq = KP >> 2;                      // 16-byte quads of K per row
     const int64_t ntiles = (I + 127) / 128;
-    for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+    // A tile's rows are read into registers one tile ahead (all of a thread's
+    // loads issued together), so that they arrive while the previous tile's
+    // products and epilogue run; rows >= I and columns >= R read as zero.
+    float4 cur[MT_LD];
+    auto load_tile = [&](int64_t tile) {
         const int64_t r0 = tile * 128;
-        const int nr = (int)min((int64_t)128, I - r0);
-        // A = the tile's rows (K-major), split; rows >= nr and columns >= R zero
-        for (int e = tid; e < 128 * nq; e += MT_THREADS) {
-            const int p = e / nq, q = e % nq;
+        const int nr = tile < ntiles ? (int)min((int64_t)128, I - r0) : 0;
+#pragma unroll
+        for (int i = 0; i < MT_LD; ++i) {
+            const int e = tid + i * MT_THREADS;
+            const int p = e / nq, q = e - p * nq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (p < nr && 4 * q < R) {
-                v = *reinterpret_cast<const float4*>(Y + (r0 + p) * (int64_t)RSY + 4 * q);
+            if (e < 128 * nq && p < nr && 4 * q < R) {
+                v = __ldg(reinterpret_cast<const float4*>(Y + (r0 + p) * (int64_t)RSY + 4 * q));
                 if (4 * q + 1 >= R) v.y = 0.f;   // columns >= R of Y's row are padding
                 if (4 * q + 2 >= R) v.z = 0.f;
                 if (4 * q + 3 >= R) v.w = 0.f;
             }
-            uint4 h, l;
-            tf32_split(v.x, h.x, l.x);
-            tf32_split(v.y, h.y, l.y);
-            tf32_split(v.z, h.z, l.z);
-            tf32_split(v.w, h.w, l.w);
-            const uint32_t off = mt_off(p, 4 * q, KP);
-            *reinterpret_cast<uint4*>(Ah + off) = h;
-            *reinterpret_cast<uint4*>(Al + off) = l;
+            cur[i] = v;
+        }
+    };
+    load_tile(blockIdx.x);
+    for (int64_t tile = blockIdx.x; tile < ntiles && alive; tile += gridDim.x) {
+        const int64_t r0 = tile * 128;
+        const int nr = (int)min((int64_t)128, I - r0);
+        // A = the tile's rows (K-major), split
+#pragma unroll
+        for (int i = 0; i < MT_LD; ++i) {
+            const int e = tid + i * MT_THREADS;
+            if (e < 128 * nq) {
+                const int p = e / nq, q = e - p * nq;
+                uint4 h, l;
+                tf32_split(cur[i].x, h.x, l.x);
+                tf32_split(cur[i].y, h.y, l.y);
+                tf32_split(cur[i].z, h.z, l.z);
+                tf32_split(cur[i].w, h.w, l.w);
+                const uint32_t off = mt_off(p, 4 * q, KP);
+                *reinterpret_cast<uint4*>(Ah + off) = h;
+                *reinterpret_cast<uint4*>(Al + off) = l;
+            }
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -183,6 +205,7 @@ __global__ void __launch_bounds__(MT_THREADS) minv_tc(const float* __restrict__ 
                              mt_saddr(&bar))
                          : "memory");
         }
+        load_tile(tile + gridDim.x);   // the next tile's rows, while the products run
         const bool ok = mt_wait(&bar, phase);
         alive = __syncthreads_and(ok) != 0;
         if (!alive) break;
@@ -265,16 +288,16 @@ cudaError_t launch_minv_tc(const float* Y, int RSY, const double* Minv, int64_t 
     const int KP = (R + 7) & ~7, NP = (R + 31) & ~31;
     const uint32_t tcols = NP <= 32 ? 32u : NP <= 64 ? 64u : 128u;
     const size_t sm = (size_t)2 * 128 * KP * 4 + (size_t)2 * NP * KP * 4;
-    cudaError_t e = cudaFuncSetAttribute(minv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    auto k = KP <= 32 ? minv_tc<4> : KP <= 56 ? minv_tc<7> : minv_tc<13>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, minv_tc, MT_THREADS, sm);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, MT_THREADS, sm);
     if (e != cudaSuccess) return e;
     per_sm = std::max(1, std::min(per_sm, (int)(512 / tcols)));
     const int64_t ntiles = (I + 127) / 128;
     const int64_t grid = std::min<int64_t>(ntiles, (int64_t)num_sms * std::min(per_sm, 2));
-    minv_tc<<<(unsigned)grid, MT_THREADS, sm, st>>>(Y, RSY, Minv, I, R, KP, NP, tcols, U, sumsq ? part : nullptr,
-                                                    status);
+    k<<<(unsigned)grid, MT_THREADS, sm, st>>>(Y, RSY, Minv, I, R, KP, NP, tcols, U, sumsq ? part : nullptr, status);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess || !sumsq) return e;

@@ -11,15 +11,15 @@
 // scheduling, so a sweep and its CUDA-graph replay are bit-identical):
 //   1. a thread per sampled tuple binary-searches its key among the fiber keys;
 //   2. the samples are sorted by fiber id (stable radix sort, radix_sort.cu):
-//      samples of one fiber differ only in their sketched row, so each
-//      distinct sampled fiber u gets acc_u = Σ_s w_s SA[s, :] over its run of
-//      samples, in sample order (a warp per fiber);
+//      samples of one fiber share its nonzeros, so each distinct sampled
+//      fiber u gets acc_u = Σ_s w_s SA[s, :] over its run of samples (seg_sums:
+//      fixed chunks of sorted positions, runs that cross a chunk summed from
+//      per-chunk partials in chunk order);
 //   3. its (fiber, nonzero) pairs are numbered by a scan of the fibers'
 //      lengths and sorted by the nonzero's mode-j row;
 //   4. the run of pairs of each row i_j forms Y[i_j, :] = Σ v acc_u in an
-//      order fixed by the sorted positions (a warp per run, lanes over the
-//      columns of a short run or over the pairs of a long one) and stores it
-//      (Y = SBᵀ SA, I_j x R; untouched rows stay zero);
+//      order fixed by the sorted positions (the same chunked sums) and stores
+//      it (Y = SBᵀ SA, I_j x R; untouched rows stay zero);
 //   5. U_j = Y M⁻¹ with M = SAᵀ SA (FP64 Cholesky inverse, applied in FP32),
 //      the column sums of squares as per-CTA partials summed in CTA order.
 #include "common.cuh"
@@ -112,29 +112,6 @@ __global__ void __launch_bounds__(256) run_segments(const uint32_t* __restrict__
     }
 }
 
-// Step 2c: acc_u = Σ w_s SA[s, :] over distinct fiber u's samples in order, a
-// warp per fiber (lanes over columns).
-__global__ void __launch_bounds__(256) fiber_acc(LookupParams P, const uint32_t* __restrict__ sval,
-                                                 const int64_t* __restrict__ useg, const int64_t* __restrict__ cnt,
-                                                 float* __restrict__ acc) {
-    const int lane = threadIdx.x & 31;
-    const int64_t U = cnt[0];
-    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t u = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < U; u += warps) {
-        float a[4] = {0.f, 0.f, 0.f, 0.f};
-        for (int64_t p = useg[2 * u]; p < useg[2 * u + 1]; ++p) {
-            const int64_t s = sval[p];
-            const float ws = __ldg(P.weight + s);
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (lane + 32 * q < P.R) a[q] = fmaf(ws, __ldg(P.SA + s * P.R + lane + 32 * q), a[q]);
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q)
-            if (lane + 32 * q < P.R) acc[u * P.R + lane + 32 * q] = a[q];
-    }
-}
-
 // Step 3: pair w (of cnt[1]) belongs to distinct fiber u (poff[u] <= w <
 // poff[u + 1]) and is its nonzero w - poff[u]: key = that nonzero's mode-j
 // row, value = w, and its fiber and nonzero on the side.
@@ -173,87 +150,239 @@ __global__ void __launch_bounds__(256) pair_gather(LookupParams P, const uint32_
     }
 }
 
-// Step 4b: Y[i, :] = Σ v acc_u over row i's run of sorted pairs.  Warps take
-// chunks of 32 sorted positions and own the runs that start there (a run may
-// extend past the chunk).  A run of one pair is written by its own lane; one
-// of up to 32 pairs is summed in order with the lanes over columns; a longer
-// one with pair q on lane (q - start) mod 32, each lane summing its pairs in
-// order for 32 columns at a time, then the lanes' sums combined by a fixed
-// butterfly (lane c ends with column c).
-// Either way the order of every sum depends only on the sorted positions.
-__global__ void __launch_bounds__(256) row_sums(LookupParams P, const uint32_t* __restrict__ key,
-                                                const uint32_t* __restrict__ su, const float* __restrict__ sv,
-                                                const int64_t* __restrict__ cnt, const float* __restrict__ acc) {
+__device__ __forceinline__ void warp_reduce_scatter32(float (&a)[32]) {
     const int lane = threadIdx.x & 31;
-    const int64_t npairs = cnt[1];
-    const int64_t nchunk = (npairs + 31) / 32;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const float send = upper ? a[i] : a[i + off];
+            const float keep = upper ? a[i + off] : a[i];
+            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+}
+
+// Steps 2c and 4b: sums over runs of equal keys in a sorted list, out[o] =
+// Σ_p v_p X[u_p, :] over the run's positions p in order.  Step 2c (FIBER):
+// the samples sorted by fiber, u_p = the sample, v_p = its weight, X = SA,
+// o = the distinct fiber's number (the scanned head flag at the run's head):
+// acc_u = Σ w_s SA[s, :].  Step 4b: the (row, pair) list sorted by mode-j row,
+// u_p = the pair's distinct fiber, v_p = its value, X = acc, o = the row:
+// Y[i, :] = Σ v acc_u.
+//
+// A run can be very long (a fiber that leverage sampling hits thousands of
+// times; a row of a Zipf mode with a large share of the nonzeros), so warps
+// take fixed chunks of sorted positions rather than runs (SEG_CH for the
+// pairs, SEG_CH_S for the J samples, which then still make many chunks): a
+// run inside a chunk is summed there and written out; the piece of a run that continues
+// from the previous chunk (slot 0) and the piece of one that goes on into
+// the next (slot 1) are written to per-chunk partials, which seg_fix then adds
+// in chunk order.  Inside a chunk, runs of one position (four at a time) and
+// of up to 32 are summed in order with the lanes over columns; a longer piece
+// with position q on lane (q - start) mod 32, each lane in order, then a fixed
+// butterfly.  Every sum's order depends only on the sorted positions, so the
+// result does not depend on scheduling.
+constexpr int SEG_CH = 1024;
+constexpr int SEG_CH_S = 64;
+
+struct SegSrc {
+    const uint32_t* key;     // sorted run keys
+    const uint32_t* su;      // 4b: per position, the row of X
+    const float* sv;         // 4b: per position, the scale
+    const uint32_t* sval;    // 2c: per position, the sample (row of X; its weight scales it)
+    const float* weight;     // 2c: the samples' weights
+    const uint32_t* scan;    // 2c: exclusive scan of the run-head flags (the output numbers)
+    const float* X;          // source rows, stride R
+    float* out;              // output rows, stride RO
+    int R, RO;
+};
+
+template <bool FIBER>
+__device__ __forceinline__ void seg_uv(const SegSrc& S, int64_t p, uint32_t& u, float& v) {
+    if (FIBER) {
+        u = S.sval[p];
+        v = __ldg(S.weight + u);
+    } else {
+        u = S.su[p];
+        v = S.sv[p];
+    }
+}
+template <bool FIBER>
+__device__ __forceinline__ int64_t seg_count(const int64_t* cnt, const int64_t* useg) {
+    if (FIBER) return cnt[0] > 0 ? useg[2 * cnt[0] - 1] : 0;   // the found samples (the rest sort last)
+    return cnt[1];
+}
+
+// info[c] = (slot 0 used, the run of slot 0 ends in chunk c, slot 1 used, slot 1's output number)
+template <bool FIBER>
+__global__ void __launch_bounds__(256) seg_sums(SegSrc S, const int64_t* __restrict__ cnt,
+                                                const int64_t* __restrict__ useg, float* __restrict__ part,
+                                                uint4* __restrict__ info) {
+    const int lane = threadIdx.x & 31;
+    constexpr int CH = FIBER ? SEG_CH_S : SEG_CH;
+    const int64_t n = seg_count<FIBER>(cnt, useg);
+    const int64_t nch = (n + CH - 1) / CH;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t ch = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); ch < nchunk; ch += warps) {
-        const int64_t p = ch * 32 + lane;
-        const bool head = p < npairs && (p == 0 || key[p] != key[p - 1]);
-        // runs of one pair (most rows): a lane each
-        if (head && (p + 1 >= npairs || key[p + 1] != key[p])) {
-            const float* au = acc + (int64_t)su[p] * P.R;
-            const float v = sv[p];
-            float* y = P.Y + (int64_t)key[p] * P.RS;
-            for (int c = 0; c < P.R; ++c) y[c] = v * au[c];
-        }
-        unsigned heads = __ballot_sync(0xffffffffu, head && p + 1 < npairs && key[p + 1] == key[p]);
-        while (heads) {
-            const int h = __ffs(heads) - 1;
-            heads &= heads - 1;
-            const int64_t p0 = ch * 32 + h;
-            const uint32_t row = key[p0];
-            // the run's end, 32 positions at a time
-            int64_t p1 = p0 + 1;
-            for (;;) {
-                const int64_t q = p1 + lane;
-                const unsigned more = __ballot_sync(0xffffffffu, q < npairs && key[q] == row);
-                if (more != 0xffffffffu) {
-                    p1 += __ffs(~more) - 1;
-                    break;
+    const int R = S.R;
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += warps) {
+        const int64_t cb = c * CH, ce = min(cb + CH, n);
+        const bool cont_run = cb > 0 && S.key[cb - 1] == S.key[cb];
+        uint32_t has0 = 0, end0 = 0, has1 = 0, out1 = 0;
+        for (int64_t sb = cb; sb < ce; sb += 32) {
+            const int64_t p = sb + lane;
+            const bool valid = p < ce;
+            const uint32_t kr = p < n ? S.key[p] : 0xffffffffu;
+            uint32_t ku = 0;
+            float kv = 0.f;
+            if (valid) seg_uv<FIBER>(S, p, ku, kv);
+            const uint32_t kprev = __shfl_up_sync(0xffffffffu, kr, 1);
+            const uint32_t knext = __shfl_down_sync(0xffffffffu, kr, 1);
+            const uint32_t prev = lane == 0 ? (p > 0 && p - 1 < n ? S.key[p - 1] : 0xffffffffu) : kprev;
+            const uint32_t next = lane == 31 ? (p + 1 < n ? S.key[p + 1] : 0xffffffffu) : knext;
+            const bool start = valid && (p == cb || prev != kr);
+            const bool is_cont = p == cb && cont_run;
+            const bool single = start && !is_cont && next != kr;
+            // runs of one position, four at a time (their loads in flight together)
+            unsigned singles = __ballot_sync(0xffffffffu, single);
+            while (singles) {
+                int hs[4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    hs[t] = singles ? __ffs(singles) - 1 : -1;
+                    singles &= singles ? singles - 1 : 0u;
                 }
-                p1 += 32;
+                uint32_t us[4];
+                int64_t os[4];
+                float vs[4], xs[4][4];
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const int src = hs[t] < 0 ? 0 : hs[t];
+                    us[t] = __shfl_sync(0xffffffffu, ku, src);
+                    vs[t] = __shfl_sync(0xffffffffu, kv, src);
+                    const uint32_t kt = __shfl_sync(0xffffffffu, kr, src);
+                    os[t] = hs[t] < 0 ? 0 : (FIBER ? (int64_t)S.scan[sb + src] : (int64_t)kt);
+                }
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        xs[t][q] = (hs[t] >= 0 && lane + 32 * q < R) ? __ldg(S.X + (int64_t)us[t] * R + lane + 32 * q)
+                                                                      : 0.f;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (hs[t] >= 0 && lane + 32 * q < R) S.out[os[t] * S.RO + lane + 32 * q] = vs[t] * xs[t][q];
             }
-            float* y = P.Y + (int64_t)row * P.RS;
-            if (p1 - p0 <= 32) {
-                float a[4] = {0.f, 0.f, 0.f, 0.f};
-                for (int64_t q = p0; q < p1; ++q) {
-                    const int64_t u = su[q];
-                    const float v = sv[q];
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        if (lane + 32 * c < P.R) a[c] = fmaf(v, acc[u * P.R + lane + 32 * c], a[c]);
-                }
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    if (lane + 32 * c < P.R) y[lane + 32 * c] = a[c];
-            } else {
-                for (int c0 = 0; c0 < P.R; c0 += 32) {
-                    float a[32];
-#pragma unroll
-                    for (int c = 0; c < 32; ++c) a[c] = 0.f;
-                    for (int64_t q = p0 + lane; q < p1; q += 32) {
-                        const float* au = acc + (int64_t)su[q] * P.R + c0;
-                        const float v = sv[q];
-#pragma unroll
-                        for (int c = 0; c < 32; ++c)
-                            if (c0 + c < P.R) a[c] = fmaf(v, au[c], a[c]);
-                    }
-#pragma unroll
-                    for (int off = 16; off >= 1; off >>= 1) {
-                        const bool upper = (lane & off) != 0;
-#pragma unroll
-                        for (int i = 0; i < off; ++i) {
-                            const float send = upper ? a[i] : a[i + off];
-                            const float keep = upper ? a[i + off] : a[i];
-                            a[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+            unsigned heads = __ballot_sync(0xffffffffu, start && !single);
+            while (heads) {
+                const int h = __ffs(heads) - 1;
+                heads &= heads - 1;
+                const int64_t p0 = sb + h;
+                const uint32_t row = __shfl_sync(0xffffffffu, kr, h);
+                // the piece's end within the chunk: from the lanes' keys, then
+                // 32 positions at a time
+                const unsigned same = __ballot_sync(0xffffffffu, valid && kr == row) >> h;
+                const bool to_end = same == (0xffffffffu >> h);
+                int64_t e = to_end ? sb + 32 : p0 + __ffs(~same) - 1;
+                if (to_end)
+                    for (;;) {
+                        const int64_t q = e + lane;
+                        const unsigned more = __ballot_sync(0xffffffffu, q < ce && S.key[q] == row);
+                        if (more != 0xffffffffu) {
+                            e += __ffs(~more) - 1;
+                            break;
                         }
+                        e += 32;
                     }
-                    if (c0 + lane < P.R) y[c0 + lane] = a[0];
+                const bool cont = p0 == cb && cont_run;
+                const bool cross = e == ce && ce < n && S.key[ce] == row;
+                float* dst;
+                if (cont) {
+                    dst = part + (c * 2 + 0) * R;
+                    has0 = 1;
+                    end0 = cross ? 0u : 1u;
+                } else if (cross) {
+                    dst = part + (c * 2 + 1) * R;
+                    has1 = 1;
+                    out1 = FIBER ? S.scan[p0] : row;
+                } else {
+                    dst = S.out + (FIBER ? (int64_t)S.scan[p0] : (int64_t)row) * S.RO;
+                }
+                if (e - p0 <= 32) {
+                    float a[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int64_t q = p0; q < e; ++q) {
+                        const int i = (int)(q - sb);
+                        uint32_t u;
+                        float v;
+                        if (i < 32) {   // warp-uniform
+                            u = __shfl_sync(0xffffffffu, ku, i);
+                            v = __shfl_sync(0xffffffffu, kv, i);
+                        } else {
+                            seg_uv<FIBER>(S, q, u, v);
+                        }
+                        const float* xu = S.X + (int64_t)u * R;
+#pragma unroll
+                        for (int w = 0; w < 4; ++w)
+                            if (lane + 32 * w < R) a[w] = fmaf(v, __ldg(xu + lane + 32 * w), a[w]);
+                    }
+#pragma unroll
+                    for (int w = 0; w < 4; ++w)
+                        if (lane + 32 * w < R) dst[lane + 32 * w] = a[w];
+                } else {
+                    for (int c0 = 0; c0 < R; c0 += 32) {
+                        float a[32];
+#pragma unroll
+                        for (int w = 0; w < 32; ++w) a[w] = 0.f;
+                        for (int64_t q = p0 + lane; q < e; q += 32) {
+                            uint32_t u;
+                            float v;
+                            seg_uv<FIBER>(S, q, u, v);
+                            const float* xu = S.X + (int64_t)u * R + c0;
+#pragma unroll
+                            for (int w = 0; w < 32; ++w)
+                                if (c0 + w < R) a[w] = fmaf(v, __ldg(xu + w), a[w]);
+                        }
+                        warp_reduce_scatter32(a);
+                        if (c0 + lane < R) dst[c0 + lane] = a[0];
+                    }
                 }
             }
         }
+        if (lane == 0) info[c] = make_uint4(has0, end0, has1, out1);
+    }
+}
+
+// The runs that cross chunks: slot 1 of the chunk where the run starts, then
+// slot 0 of each following chunk up to the one where it ends, in that order.
+template <bool FIBER>
+__global__ void __launch_bounds__(256) seg_fix(SegSrc S, const int64_t* __restrict__ cnt,
+                                               const int64_t* __restrict__ useg, const float* __restrict__ part,
+                                               const uint4* __restrict__ info) {
+    const int lane = threadIdx.x & 31;
+    constexpr int CH = FIBER ? SEG_CH_S : SEG_CH;
+    const int64_t n = seg_count<FIBER>(cnt, useg);
+    const int64_t nch = (n + CH - 1) / CH;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int R = S.R;
+    for (int64_t c = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); c < nch; c += warps) {
+        const uint4 in = info[c];
+        if (!in.z) continue;
+        float a[4];
+#pragma unroll
+        for (int w = 0; w < 4; ++w) a[w] = lane + 32 * w < R ? part[(c * 2 + 1) * R + lane + 32 * w] : 0.f;
+        for (int64_t d = c + 1; d < nch; ++d) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w)
+                if (lane + 32 * w < R) a[w] += part[(d * 2 + 0) * R + lane + 32 * w];
+            if (info[d].y) break;
+        }
+        float* dst = S.out + (int64_t)in.w * S.RO;
+#pragma unroll
+        for (int w = 0; w < 4; ++w)
+            if (lane + 32 * w < R) dst[lane + 32 * w] = a[w];
     }
 }
 
@@ -261,7 +390,8 @@ __global__ void __launch_bounds__(256) row_sums(LookupParams P, const uint32_t* 
 // is non-null, the CTA's Σ_i U[i, c]² over its rows into part[cta][c]
 // (double-float partials per thread, summed in thread order; the CTAs'
 // partials are then summed in CTA order by sumsq_reduce).  Persistent CTAs walk tiles of TM rows of
-// Y, staged in shared memory with row stride R | 1 (the rows a warp reads
+// Y (read into registers a tile ahead, coalesced), staged in shared memory
+// with row stride R | 1 (the rows a warp reads
 // fall in distinct banks); thread (ty, tx) accumulates RT rows x 8 columns,
 // {4tx .. 4tx+3} and {RP/2 + 4tx ..}, against float4 rows of M⁻¹ (columns
 // >= R zero).  RP = R padded to 32, 64 or 128.
@@ -294,14 +424,40 @@ __global__ void __launch_bounds__(MINV_THREADS, 2) apply_minv(const float* __res
 #pragma unroll
     for (int q = 0; q < 8; ++q) ss[q] = df{0.f, 0.f};
     const int64_t ntiles = (I + TM - 1) / TM;
+    // A tile of Y is TM contiguous rows of RSY floats (RSY a multiple of 4):
+    // at most 8 float4 per thread, read into registers one tile ahead so that
+    // they arrive during the previous tile's products.
+    constexpr int LDN = 8;
+    static_assert(TM * RP / 4 <= LDN * MINV_THREADS, "tile larger than the prefetch registers");
+    float4 pre[LDN];
+    auto load_tile = [&](int64_t tile) {
+        const int64_t r0 = tile * TM;
+        const int64_t nq = tile < ntiles ? (int64_t)min((int64_t)TM, I - r0) * RSY / 4 : 0;
+        const float4* src = reinterpret_cast<const float4*>(Y + r0 * RSY);
+#pragma unroll
+        for (int i = 0; i < LDN; ++i) {
+            const int e = threadIdx.x + i * MINV_THREADS;
+            pre[i] = e < nq ? __ldg(src + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+    };
+    load_tile(blockIdx.x);
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int64_t r0 = tile * TM;
         const int nr = (int)min((int64_t)TM, I - r0);
         __syncthreads();   // the previous tile's reads of sY (and the writes of sM) are done
-        const float* src = Y + r0 * RSY;
-        for (int r = warp; r < nr; r += MINV_THREADS / 32)
-            for (int k = lane; k < R; k += 32) sY[r * RS + k] = src[(int64_t)r * RSY + k];
+#pragma unroll
+        for (int i = 0; i < LDN; ++i) {
+            const int e = threadIdx.x + i * MINV_THREADS;
+            const int row = (4 * e) / RSY, col = 4 * e - row * RSY;
+            if (row < nr) {
+                const float v[4] = {pre[i].x, pre[i].y, pre[i].z, pre[i].w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (col + j < R) sY[row * RS + col + j] = v[j];
+            }
+        }
         __syncthreads();
+        load_tile(tile + gridDim.x);
         float2 acc[RT][4];
 #pragma unroll
         for (int r = 0; r < RT; ++r)
@@ -513,6 +669,10 @@ void free_lookup_scratch(krp_sptensor* t) {
     cudaFree(t->pu);
     cudaFree(t->pn);
     cudaFree(t->hist);
+    cudaFree(t->seg_part);
+    cudaFree(t->seg_info);
+    t->seg_part = nullptr;
+    t->seg_info = nullptr;
     t->flag = t->pu = t->pn = t->hist = nullptr;
     t->useg = t->ufib = t->poff = t->cnt = nullptr;
     t->uacc = nullptr;
@@ -693,6 +853,8 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
         ok = ok && dmalloc(&t->flag, nJ + 1) && dmalloc(&t->useg, 2 * nJ) && dmalloc(&t->ufib, nJ) &&
              dmalloc(&t->poff, nJ + 1) && dmalloc(&t->cnt, 2) && dmalloc(&t->uacc, nJ * nR) &&
              dmalloc(&t->pu, nP) && dmalloc(&t->pn, nP) && dmalloc(&t->hist, nH);
+        const size_t nC = std::max((nJ + SEG_CH_S - 1) / SEG_CH_S, (nP + SEG_CH - 1) / SEG_CH);   // chunks of the sums
+        ok = ok && dmalloc(&t->seg_part, nC * 2 * nR) && dmalloc(&t->seg_info, nC * 4);
         if (!ok) {
             free_lookup_scratch(t);
             return fail(s, KRP_ENOMEM, "sparse lookup scratch allocation failed");
@@ -722,7 +884,20 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     if (e != cudaSuccess) return cuda_check(s, e, "run scan launch");
     run_segments<<<g0, 256, 0, cs>>>(skey, J, nfib, t->flag, P.fptr, t->useg, t->ufib, t->poff, t->cnt);
     count_launch();
-    fiber_acc<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, sval, t->useg, t->cnt, t->uacc);
+    const unsigned gs = (unsigned)(s->num_sms * 8);
+    uint4* sinfo = reinterpret_cast<uint4*>(t->seg_info);
+    SegSrc S2{};   // 2c: acc_u = Σ w_s SA[s, :]
+    S2.key = skey;
+    S2.sval = sval;
+    S2.weight = weight;
+    S2.scan = t->flag;
+    S2.X = SA;
+    S2.out = t->uacc;
+    S2.R = R;
+    S2.RO = R;
+    seg_sums<true><<<gs, 256, 0, cs>>>(S2, t->cnt, t->useg, t->seg_part, sinfo);
+    count_launch();
+    seg_fix<true><<<gs, 256, 0, cs>>>(S2, t->cnt, t->useg, t->seg_part, sinfo);
     count_launch();
     // 3: the pairs, sorted by mode-j row
     e = exclusive_scan_i64(t->poff, t->cnt, t->cnt + 1, cs);
@@ -739,8 +914,17 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     pair_gather<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->pv[a1], t->pu, t->pn, t->cnt, t->pk[b1],
                                                            reinterpret_cast<float*>(t->pv[b1]));
     count_launch();
-    row_sums<<<(unsigned)(s->num_sms * 8), 256, 0, cs>>>(P, t->pk[a1], t->pk[b1], reinterpret_cast<float*>(t->pv[b1]),
-                                                        t->cnt, t->uacc);
+    SegSrc S4{};   // 4b: Y[i, :] = Σ v acc_u
+    S4.key = t->pk[a1];
+    S4.su = t->pk[b1];
+    S4.sv = reinterpret_cast<const float*>(t->pv[b1]);
+    S4.X = t->uacc;
+    S4.out = t->Y;
+    S4.R = R;
+    S4.RO = RS;
+    seg_sums<false><<<gs, 256, 0, cs>>>(S4, t->cnt, t->useg, t->seg_part, sinfo);
+    count_launch();
+    seg_fix<false><<<gs, 256, 0, cs>>>(S4, t->cnt, t->useg, t->seg_part, sinfo);
     count_launch();
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "fiber lookup launch");

@@ -110,6 +110,51 @@ def minv100():
     assert s.sync_status() == 0, s.last_error()
 
 
+def minv100_tc():
+    """minv100 with a BF16x3 sampler: Y M^-1 on the tensor cores (TF32x3)."""
+    from .krpls import SparseTensor
+    dims, R, J = (1 << 21, 64, 64), 100, 1 << 14
+    coords, vals = synth.sparse_zipf_tensor(dims, 200000, seed=0)
+    Us = synth.gaussian_factors(3, list(dims), R, seed=1)
+    s = Sampler(list(dims), R, R, 1)
+    for k in range(3):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    t = SparseTensor(dims, coords, vals)
+    idx = torch.zeros((3, J), dtype=torch.int32, device="cuda")
+    w = torch.zeros(J, device="cuda")
+    SA = torch.zeros((J, R), device="cuda")
+    Uo = torch.zeros((dims[0], R), device="cuda")
+    for d in range(3):
+        s.sample(0, J, 1, d, idx, w, None, SA)
+        s.solve_sparse(t, 0, J, idx, w, SA, Uo)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def sweep25(precision=0, nnz=20_000_000, sweeps=3):
+    """STS-CP sweeps (Alg. 6) at R = 25, J = 2^16 on the 2^22 x 2^22 x 2^14
+    Zipf tensor with nnz nonzeros (generated on the device), from the
+    benchmark's data-aware start."""
+    import numpy as np
+    from .krpls import SparseTensor
+    dims, R, J = (1 << 22, 1 << 22, 1 << 14), 25, 1 << 16
+    coords, vals = synth.sparse_zipf_tensor(dims, nnz, seed=0, device=torch.device("cuda"))
+    t = SparseTensor(dims, coords, vals)
+    Us = synth.gaussian_factors(3, list(dims), R, seed=0)
+    s = Sampler(list(dims), R, 0, precision)
+    for k in range(3):
+        cnt = np.bincount(coords[k], minlength=dims[k]).astype(np.float64) + 0.01
+        sc = np.sqrt(cnt / cnt.mean()).astype(np.float32)
+        s.set_factor(k, torch.from_numpy(Us[k] * sc[:, None]).cuda())
+    from .krpls import launch_count
+    sigma = torch.zeros(R, device="cuda")
+    n0 = launch_count()
+    for sw in range(sweeps):
+        s.cp_als_sweep(t, J, 1, 3 * sw, sigma)
+        if sw == 0:
+            print("launches per sweep:", launch_count() - n0)
+    assert s.sync_status() == 0, s.last_error()
+
+
 def prep():
     I, R = 1 << 16, 32
     Us = synth.skewed_row_factors(3, I, R, seed=0)
@@ -146,6 +191,7 @@ if __name__ == "__main__":
      "descent64": descent64, "descent100": descent100,
      "descent100_nm": lambda: descent100(2), "build": build, "build_tc": build_tc,
      "build100": lambda: build(0, 1 << 20, 100), "build100_tc": lambda: build(1, 1 << 20, 100),
-     "prep": prep, "prep100": prep100, "minv100": minv100, "peaks": peaks}[sys.argv[1]]()
+     "prep": prep, "prep100": prep100, "minv100": minv100, "minv100_tc": minv100_tc, "sweep25": sweep25,
+     "peaks": peaks}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")
