@@ -7,11 +7,12 @@
 // node L + b.  Only the root (slot 0) and left children (slot h/2) are stored,
 // each as a packed upper triangle with stride Tp floats (see common.cuh).
 //
-// Kernel 1 (tree_leaves_*): each CTA owns G groups of LB consecutive leaves.
-// Rows of the next group stream into shared memory with cp.async while the
-// current group's leaf Grams G^v = U[S(v)]ᵀU[S(v)] are formed (FP32 FMA with
-// 4x4 register tiles on the upper triangle, or tcgen05 BF16x3 in
-// tree_build_tc.cu).  Each thread then owns a fixed set of packed entries and
+// Kernel 1 (tree_leaves_*): each CTA owns G groups of LB consecutive leaves,
+// whose rows stream into shared memory with cp.async (three CTAs per SM
+// overlap one another's staging and sums; the exact-decision leaves, one
+// heavier CTA per SM, stage the next group while the current one is summed),
+// and forms the leaf Grams G^v = U[S(v)]ᵀU[S(v)] (FP32 FMA with 4x4 register
+// tiles on the upper triangle, or tcgen05 BF16x3 in tree_build_tc.cu).  Each thread then owns a fixed set of packed entries and
 // sums them pairwise up the group (parent = left + right, Alg. 3),
 // continuing across groups with a per-entry binary-counter stack, storing
 // every left child it creates.  The CTA's subtree root goes to scratch.
@@ -207,12 +208,16 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
                                                       int G, int Tp, float* __restrict__ tree,
                                                       float* __restrict__ top, float* __restrict__ copy_to,
                                                       int64_t blk, float* __restrict__ tree_lo = nullptr) {
+    // DB: the exact-decision leaves (one CTA of heavier work per SM) stage the
+    // next group while the current one is summed; the FP32 leaves keep one
+    // stage and three CTAs per SM, whose staging overlaps the others' sums.
+    constexpr bool DB = VEC && EXACT;
     extern __shared__ __align__(16) float smem[];
     const int rows = LB * F;
     const int T = tri_size(R);
     float* sU0 = smem;
     float* sU1 = sU0 + (size_t)rows * R;
-    float* sG = (VEC ? sU1 : sU0) + (size_t)rows * R;
+    float* sG = (DB ? sU1 : sU0) + (size_t)rows * R;
     float* sGlo = EXACT ? sG + (size_t)LB * Tp : nullptr;
     float* stk = sG + (size_t)(EXACT ? 2 : 1) * LB * Tp;
     for (int e = threadIdx.x; e < LB * Tp; e += blockDim.x)
@@ -224,8 +229,8 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
     stage_rows<VEC>(sU0, U, I, R, leaf0 * F, rows);
     if (VEC) cp_async_commit();
     for (int g = 0; g < G; ++g) {
-        float* cur = (VEC && (g & 1)) ? sU1 : sU0;
-        if (VEC) {
+        float* cur = (DB && (g & 1)) ? sU1 : sU0;
+        if (DB) {
             if (g + 1 < G) {
                 stage_rows<VEC>((g & 1) ? sU0 : sU1, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);
                 cp_async_commit();
@@ -233,6 +238,8 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
             } else {
                 cp_async_wait<0>();
             }
+        } else if (VEC) {
+            cp_async_wait<0>();
         }
         __syncthreads();
         if (copy_to) copy_rows_out<VEC>(cur, copy_to, I, R, (leaf0 + (int64_t)g * LB) * F, rows);
@@ -247,15 +254,16 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
             __syncthreads();
         }
         reduce_group<LB, true, EXACT>(sG, stk, tree, top, L, leaf0 + (int64_t)g * LB, g, G, Tp, blk, sGlo, tree_lo);
-        if (!VEC && g + 1 < G) {
+        if (!DB && g + 1 < G) {
             __syncthreads();
             stage_rows<VEC>(sU0, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);
+            if (VEC) cp_async_commit();
         }
     }
 }
 
 template <int LB, bool VEC, bool EXACT>
-__global__ void __launch_bounds__(288, 2) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
+__global__ void __launch_bounds__(288, EXACT ? 2 : 3) tree_leaves_fp32(const float* __restrict__ U, int64_t I, int R, int F,
                                                         int64_t L, int G, int Tp, float* __restrict__ tree,
                                                         float* __restrict__ top, float* __restrict__ copy_to,
                                                         float* __restrict__ tree_lo) {
@@ -294,7 +302,7 @@ __device__ __forceinline__ int prefix_find(const int64_t* __restrict__ pre, int 
 // Batched leaf kernel: CTA b builds block b - prefix[t] of tree t (the tree
 // whose block range holds b), with LB leaves per group and the tree's own G.
 template <int LB, bool VEC>
-__global__ void __launch_bounds__(288, 2) tree_leaves_fp32_batch(const TreeDesc* __restrict__ trees,
+__global__ void __launch_bounds__(288, 3) tree_leaves_fp32_batch(const TreeDesc* __restrict__ trees,
                                                               const int64_t* __restrict__ prefix, int ntrees) {
     const int t = prefix_find(prefix, ntrees, blockIdx.x);
     const TreeDesc& d = trees[t];
@@ -522,7 +530,7 @@ void tree_geometry(int R, int F, int64_t L, int Tp, bool vec, int* LB_out, int* 
     auto smem_of = [&](int g) {
         int lv = 0;
         while ((1 << lv) < g) ++lv;
-        return (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)(exact ? 2 : 1) * LB * Tp * 4 +
+        return (size_t)(vec && exact ? 2 : 1) * LB * leaf_bytes + (size_t)(exact ? 2 : 1) * LB * Tp * 4 +
                (size_t)2 * (lv + 1) * Tp * 4;
     };
     const size_t cap = exact ? 110 * 1024 : 160 * 1024;
@@ -539,7 +547,7 @@ cudaError_t launch_leaves_batch(const TreeDesc* trees_dev, const int64_t* block_
     int lv = 0;
     while ((1 << lv) < Gmax) ++lv;
     const size_t leaf_bytes = (size_t)Fmax * Rmax * 4;
-    const size_t smem = (size_t)(vec ? 2 : 1) * LB * leaf_bytes + (size_t)LB * Tpmax * 4 + (size_t)2 * (lv + 1) * Tpmax * 4;
+    const size_t smem = (size_t)LB * leaf_bytes + (size_t)LB * Tpmax * 4 + (size_t)2 * (lv + 1) * Tpmax * 4;
     cudaError_t e = cudaSuccess;
 #define KRP_LB(LBV)                                                                                              \
     {                                                                                                            \
