@@ -130,13 +130,13 @@ def minv100_tc():
     assert s.sync_status() == 0, s.last_error()
 
 
-def sweep25(precision=0, nnz=20_000_000, sweeps=3):
-    """STS-CP sweeps (Alg. 6) at R = 25, J = 2^16 on the 2^22 x 2^22 x 2^14
-    Zipf tensor with nnz nonzeros (generated on the device), from the
-    benchmark's data-aware start."""
+def sweep25(precision=0, nnz=20_000_000, sweeps=3, R=25):
+    """STS-CP sweeps (Alg. 6) at rank R (25 by default), J = 2^16 on the
+    2^22 x 2^22 x 2^14 Zipf tensor with nnz nonzeros (generated on the
+    device), from the benchmark's data-aware start."""
     import numpy as np
     from .krpls import SparseTensor
-    dims, R, J = (1 << 22, 1 << 22, 1 << 14), 25, 1 << 16
+    dims, J = (1 << 22, 1 << 22, 1 << 14), 1 << 16
     coords, vals = synth.sparse_zipf_tensor(dims, nnz, seed=0, device=torch.device("cuda"))
     t = SparseTensor(dims, coords, vals)
     Us = synth.gaussian_factors(3, list(dims), R, seed=0)
@@ -192,6 +192,8 @@ if __name__ == "__main__":
      "descent100_nm": lambda: descent100(2), "build": build, "build_tc": build_tc,
      "build100": lambda: build(0, 1 << 20, 100), "build100_tc": lambda: build(1, 1 << 20, 100),
      "prep": prep, "prep100": prep100, "minv100": minv100, "minv100_tc": minv100_tc, "sweep25": sweep25,
+     "sweep100_bf16x3": lambda: sweep25(precision=1, R=100),
+     "sweep100_bf16x3_2e8": lambda: sweep25(precision=1, nnz=200_000_000, R=100),
      "peaks": peaks}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")
