@@ -123,11 +123,16 @@ __global__ void __launch_bounds__(256) normal_partial(const float* __restrict__ 
 // One CTA.  mode 0: X = M⁻¹ Z (R x nrhs) written as FP32 to X;
 // mode 1: M⁻¹ (R x R) written as FP64 to Xd (sparse path).
 // Work matrices: shared memory when gbuf == nullptr, else gbuf (global).
+// split (mode 1 only): after a successful Cholesky, leave L in gL and a 1 in
+// *gflag for normal_trsm (the R triangular solves for the columns of M⁻¹ then
+// run on R SMs instead of one); otherwise *gflag = 0 and this CTA finishes.
 __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part, int nparts, int R, int nrhs,
                                                   int mode, int flags, float* __restrict__ X,
                                                   double* __restrict__ Xd, int* __restrict__ status,
                                                   double* __restrict__ gbuf, const float* __restrict__ part_exp,
-                                                  const double* __restrict__ sums = nullptr) {
+                                                  const double* __restrict__ sums = nullptr,
+                                                  double* __restrict__ gL = nullptr,
+                                                  double* __restrict__ gflag = nullptr) {
     extern __shared__ __align__(16) double smd[];
     const int RR = R * R;
     const int T = tri_size(R);
@@ -195,6 +200,12 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
         }
         __syncthreads();
     }
+    if (!flag && gL) {
+        if (gL != Lm)
+            for (int e = threadIdx.x; e < RR; e += blockDim.x) gL[e] = Lm[e];
+        if (threadIdx.x == 0) *gflag = 1.0;
+        return;
+    }
     if (!flag) {
         // forward then backward substitution, one thread per right-hand side
         for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
@@ -251,6 +262,7 @@ __device__ __forceinline__ void normal_solve_body(const float* __restrict__ part
         else
             X[e] = (float)Z[e];
     }
+    if (gflag && threadIdx.x == 0) *gflag = 0.0;   // done here: normal_trsm has nothing to do
 }
 
 __global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ part, int nparts, int R, int nrhs,
@@ -275,8 +287,36 @@ __global__ void __launch_bounds__(256) normal_reduce(const float* __restrict__ p
 
 __global__ void __launch_bounds__(256) normal_solve_sums(const double* __restrict__ sums, int R, int nrhs, int mode,
                                                          int flags, float* __restrict__ X, double* __restrict__ Xd,
-                                                         int* __restrict__ status, double* __restrict__ gbuf) {
-    normal_solve_body(nullptr, 0, R, nrhs, mode, flags, X, Xd, status, gbuf, nullptr, sums);
+                                                         int* __restrict__ status, double* __restrict__ gbuf,
+                                                         double* __restrict__ gL, double* __restrict__ gflag) {
+    normal_solve_body(nullptr, 0, R, nrhs, mode, flags, X, Xd, status, gbuf, nullptr, sums, gL, gflag);
+}
+
+// Column c of M⁻¹ = L⁻ᵀ L⁻¹ e_c by forward and backward substitution, one
+// warp per column (CTA c), each inner product summed over the lanes in a
+// fixed order; nothing to do unless normal_solve_sums left *gflag = 1.
+__global__ void __launch_bounds__(32) normal_trsm(const double* __restrict__ L, int R,
+                                                  const double* __restrict__ gflag, double* __restrict__ Xd) {
+    __shared__ double z[128];
+    if (*gflag != 1.0) return;
+    const int col = blockIdx.x, lane = threadIdx.x;
+    for (int i = lane; i < R; i += 32) z[i] = 0.0;
+    __syncwarp();
+    for (int i = col; i < R; ++i) {   // L z = e_col (z_i = 0 for i < col)
+        double a = 0.0;
+        for (int k = col + lane; k < i; k += 32) a += L[(size_t)i * R + k] * z[k];
+        a = warp_sum_d(a);
+        if (lane == 0) z[i] = ((i == col ? 1.0 : 0.0) - a) / L[(size_t)i * R + i];
+        __syncwarp();
+    }
+    for (int i = R - 1; i >= 0; --i) {   // Lᵀ x = z
+        double a = 0.0;
+        for (int k = i + 1 + lane; k < R; k += 32) a += L[(size_t)k * R + i] * z[k];
+        a = warp_sum_d(a);
+        if (lane == 0) z[i] = (z[i] - a) / L[(size_t)i * R + i];
+        __syncwarp();
+    }
+    for (int i = lane; i < R; i += 32) Xd[(size_t)i * R + col] = z[i];
 }
 
 // Batched forms: blockIdx.z (partials) or blockIdx.x (solve) is the problem.
@@ -358,9 +398,17 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
     double* sums = reinterpret_cast<double*>(s->solve_scratch + sums_off);
     normal_reduce<<<(nout + 255) / 256, 256, 0, s->stream>>>(s->solve_scratch, part_exp, nparts, nout, sums);
     count_launch();
-    normal_solve_sums<<<1, 256, smem2, s->stream>>>(sums, R, nrhs, mode, flags, X,
-                                                    s->solve64 + (size_t)(2 * R * R + R * 128), s->status,
-                                                    in_smem ? nullptr : s->solve64); count_launch();
+    // M⁻¹ for the sparse solve at larger R: its R triangular solves over R CTAs
+    const bool split = mode == 1 && R >= 48;
+    double* Xd = s->solve64 + (size_t)(2 * R * R + R * 128);
+    double* gL = split ? s->solve64 + (size_t)R * R : nullptr;
+    double* gflag = split ? s->solve64 + (size_t)2 * R * R : nullptr;
+    normal_solve_sums<<<1, 256, smem2, s->stream>>>(sums, R, nrhs, mode, flags, X, Xd, s->status,
+                                                    in_smem ? nullptr : s->solve64, gL, gflag); count_launch();
+    if (split) {
+        normal_trsm<<<R, 32, 0, s->stream>>>(gL, R, gflag, Xd);
+        count_launch();
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_check(s, e, "normal_solve launch");
     (void)need64;
