@@ -20,7 +20,7 @@ The default workload is the headline line; batch512 (512 small least-squares
 problems: per-problem launches vs one launch per phase vs graph replay) and
 rank_sweep (N=4, 2^20 x R, U(-1,1), J=2^17, dense solve with 8 planted
 right-hand sides) and sparse_als (STS-CP on a 2^22 x 2^22 x 2^14 Zipf tensor:
-FP32, BF16x3 and graph-replayed sweeps) and accuracy (Sec. 4.2: distortion
+FP32, BF16x3, TF32x3 and graph-replayed sweeps) and accuracy (Sec. 4.2: distortion
 and residual ratio for N in {3..9}, R in {16, 32, 64}) print their own lines.
 """
 from __future__ import annotations
@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "exact"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16x3", "tf32x3", "exact"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="sampler: skip the other precision forms")
     ap.add_argument("--sts-sweeps", type=int, default=12,
@@ -446,8 +446,8 @@ def sparse_rank_runs(t, scales, R, S, modes, dev, stream, seeds=(1,)):
     Ud = [torch.from_numpy(U * sc[:, None]).to(dev) for U, sc in zip(Us0, scales)]
     del Us0
     row = {"R": R}
-    precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "exact": krpls.KRP_PREC_EXACT,
-             "fp32_graph": krpls.KRP_PREC_FP32}
+    precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "tf32x3": krpls.KRP_PREC_TF32X3,
+             "exact": krpls.KRP_PREC_EXACT, "fp32_graph": krpls.KRP_PREC_FP32}
     for mode in modes:
         times, per_seed, fits_first, status = [], [], None, 0
         for seed in seeds:
@@ -497,7 +497,7 @@ def sparse_rank_runs(t, scales, R, S, modes, dev, stream, seeds=(1,)):
 def run_sparse_als(args):
     """STS-CP (Alg. 6) on a synthetic sparse 2^22 x 2^22 x 2^14 tensor with Zipf(1.1)
     coordinates and rank-16 U(0,1) values x lognormal(0, 0.5) noise; J = 2^16
-    samples per least-squares solve; per rank: FP32 trees, BF16x3 trees, exact
+    samples per least-squares solve; per rank: FP32 trees, BF16x3 and TF32x3 trees, exact
     decisions (R <= 32), and the FP32 sweep captured as a CUDA graph.  Reports
     the median sweep time of sweeps 2..S and the fit after each sweep (fit not
     timed)."""
@@ -511,7 +511,8 @@ def run_sparse_als(args):
     S = max(int(args.sweeps), 3)
     results = []
     for R in ranks:
-        modes = ("fp32", "bf16x3", "exact", "fp32_graph") if R <= 32 else ("fp32", "bf16x3", "fp32_graph")
+        modes = (("fp32", "bf16x3", "tf32x3", "exact", "fp32_graph") if R <= 32
+                 else ("fp32", "bf16x3", "tf32x3", "fp32_graph"))
         results.append(sparse_rank_runs(t, scales, R, S, modes, dev, stream))
     print(json.dumps({
         "metric": "STS-CP sweep time (median of sweeps 2..S), sparse 3-mode tensor",
@@ -688,7 +689,8 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
     krpls.lib()
-    precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "exact": krpls.KRP_PREC_EXACT}
+    precs = {"fp32": krpls.KRP_PREC_FP32, "bf16x3": krpls.KRP_PREC_BF16X3, "tf32x3": krpls.KRP_PREC_TF32X3,
+             "exact": krpls.KRP_PREC_EXACT}
 
     # ---- inputs (seeded, synthetic): same generator as the tests
     Us = synth.skewed_row_factors(N_FACT, I_ROWS, RANK, seed=0)
@@ -765,7 +767,7 @@ def main():
     forms = {args.precision: {"value": value, "ms_per_step": ms / args.steps, "phases_ms": head["phases_ms"],
                               "exact_redecisions_per_row_stage": head["exact_redecisions_per_row_stage"]}}
     if world == 1 and not args.no_forms:
-        for name in ("fp32", "bf16x3", "exact"):
+        for name in ("fp32", "bf16x3", "tf32x3", "exact"):
             if name == args.precision:
                 continue
             sf, _, _, _, out = sampler_run(precs[name], Ud, Fd, dev, stream, args.warmup, args.steps, draws)
@@ -781,7 +783,8 @@ def main():
     if world == 1 and args.sts_sweeps > 0:
         t, scales, setup_s = sparse_setup(args.nnz, dev, stream)
         seeds = tuple(range(1, max(1, args.sts_seeds) + 1))
-        row = sparse_rank_runs(t, scales, 25, max(3, args.sts_sweeps), ("fp32", "bf16x3", "exact"), dev, stream,
+        row = sparse_rank_runs(t, scales, 25, max(3, args.sts_sweeps), ("fp32", "bf16x3", "tf32x3", "exact"), dev,
+                               stream,
                                seeds)
         t.close()
         sts = {"workload": f"sts_cp_2^22x2^22x2^14_nnz{int(args.nnz)}_R25_J2^16", "unit": "ms per sweep",
@@ -793,7 +796,7 @@ def main():
                       "fit_mean_second_half_per_seed": row[m]["fit_mean_second_half_per_seed"],
                       "seed_spread_rel": row[m].get("seed_spread_rel"),
                       "mean_fit_rel_diff_vs_fp32": row[m].get("mean_fit_rel_diff_vs_fp32"),
-                      "status": row[m]["status"]} for m in ("fp32", "bf16x3", "exact")}}
+                      "status": row[m]["status"]} for m in ("fp32", "bf16x3", "tf32x3", "exact")}}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

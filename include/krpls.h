@@ -54,13 +54,17 @@ typedef enum {
     KRP_PREC_FP32 = 0,    /* segment-tree Grams by FP32 FMA                      */
     KRP_PREC_BF16X3 = 1,  /* Grams on tcgen05 tensor cores, BF16 hi/lo split,    */
                           /* three products, FP32 accumulate                     */
-    KRP_PREC_EXACT = 2    /* exact decisions (sampler-wide, at krp_create, R <= 32): */
+    KRP_PREC_EXACT = 2,   /* exact decisions (sampler-wide, at krp_create, R <= 32): */
                           /* leaf Grams accumulated without rounding error, every */
                           /* tree slot kept as a double-float (hi, lo) pair, the  */
                           /* top tree levels also stored as deviations from their */
-                          /* share of the parent, and every descent decision that */
-                          /* falls within 2e-9 C of a bin edge re-taken from      */
-                          /* double-float masses (Alg. 4 in near-FP64 arithmetic) */
+                          /* share of the parent, and every descent decision whose */
+                          /* FP32 gap lies within its error terms (+5e-10 C) of a */
+                          /* bin edge re-taken from double-float masses (Alg. 4   */
+                          /* in near-FP64 arithmetic)                             */
+    KRP_PREC_TF32X3 = 3   /* Grams on tcgen05 tensor cores, TF32 hi/lo split     */
+                          /* (~22 significant bits), three products, FP32         */
+                          /* accumulate; the sparse solve's Y M^-1 as TF32x3 too  */
 } krp_precision;
 
 #define KRP_PINV_FALLBACK 1  /* krp_solve_*: if Cholesky fails, use the FP64

@@ -134,7 +134,8 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
     for (int k = 0; k < N; ++k)
         if (I_host[k] < 1 || I_host[k] >= ((int64_t)1 << 31))
             return fail(nullptr, KRP_EINVAL, "krp_create: need 1 <= I_k < 2^31");
-    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3 && precision != KRP_PREC_EXACT)
+    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3 && precision != KRP_PREC_EXACT &&
+        precision != KRP_PREC_TF32X3)
         return fail(nullptr, KRP_EINVAL, "krp_create: unknown precision");
     if (precision == KRP_PREC_EXACT && R > 32)
         return fail(nullptr, KRP_EINVAL, "krp_create: the exact-decision mode needs R <= 32");
@@ -206,7 +207,8 @@ krp_status krp_create(krp_sampler** out, int N, const int64_t* I_host, int R, in
 krp_status krp_set_factor_prec(krp_sampler* s, int j, const float* U, int precision) {
     if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");
     if (j < 0 || j >= s->N || !U) return fail(s, KRP_EINVAL, "krp_set_factor: bad factor index or NULL U");
-    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3 && precision != KRP_PREC_EXACT)
+    if (precision != KRP_PREC_FP32 && precision != KRP_PREC_BF16X3 && precision != KRP_PREC_EXACT &&
+        precision != KRP_PREC_TF32X3)
         return fail(s, KRP_EINVAL, "krp_set_factor: unknown precision");
     if (precision == KRP_PREC_EXACT && !s->exact)
         return fail(s, KRP_EINVAL, "krp_set_factor: KRP_PREC_EXACT needs a sampler created with it");

@@ -476,13 +476,14 @@ cudaError_t launch_build_dtop(const krp_sampler* s, int j, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// BF16x3 tensor-core leaf kernel (tree_build_tc.cu).
+// BF16x3 and TF32x3 tensor-core leaf kernels (tree_build_tc.cu).
 bool tree_tc_supported(int R, int F);
 bool tree_tc_pipelined(int R, int F, const float* U);
-void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out);
+void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out,
+                      bool tf32);
 cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
                                   float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
-                                  bool pipelined, int num_sms, cudaStream_t st);
+                                  bool pipelined, int num_sms, cudaStream_t st, bool tf32);
 
 namespace {
 
@@ -590,12 +591,13 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     const bool vec = (R % 4) == 0;
     // exact-decision samplers build every tree with exactly accumulated leaves
     float* tree_lo = s->exact ? s->tree_lo[j] : nullptr;
-    const bool tc = !s->exact && precision == KRP_PREC_BF16X3 && tree_tc_supported(R, F);
-    const bool tc_pipe = tc && tree_tc_pipelined(R, F, src);
+    const bool tf32 = precision == KRP_PREC_TF32X3;
+    const bool tc = !s->exact && (precision == KRP_PREC_BF16X3 || tf32) && tree_tc_supported(R, F);
+    const bool tc_pipe = tc && !tf32 && tree_tc_pipelined(R, F, src);   // the pipelined form is BF16x3 only
     int LB, G, threads = 128;
     size_t smem;
     if (tc)
-        tree_tc_geometry(R, F, L, Tp, tc_pipe, &LB, &G, &smem);
+        tree_tc_geometry(R, F, L, Tp, tc_pipe, &LB, &G, &smem, tf32);
     else
         tree_geometry(R, F, L, Tp, vec, &LB, &G, &threads, &smem, s->exact);
     const int64_t ctas = L / ((int64_t)LB * G);
@@ -620,7 +622,7 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     double* up1 = up0 + (size_t)(ctas / 2 + 2) * Tp;
     if (tc) {
         const cudaError_t e = launch_tree_leaves_tc(src, I, R, F, L, LB, G, Tp, s->tree[j], top, copy_to, s->status,
-                                                    ctas, smem, tc_pipe, s->num_sms, s->stream);
+                                                    ctas, smem, tc_pipe, s->num_sms, s->stream, tf32);
         if (e != cudaSuccess) return cuda_check(s, e, "tensor-core tree leaf kernel launch");
     } else {
         cudaError_t e;

@@ -93,6 +93,25 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, float* v) {
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
+// kind::tf32 instruction descriptor: D FP32, A and B TF32, both K-major, N = 128, M = 128.
+constexpr uint32_t TC_IDESC_TF32 = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void tc_mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(TC_IDESC_TF32), "r"(accumulate)
+        : "memory");
+}
+
+// x = hi + lo with hi = tf32(x) and lo = tf32(x - hi) (round to nearest):
+// about 22 significant bits together.
+__device__ __forceinline__ void split_tf32(float x, uint32_t& hi, uint32_t& lo) {
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hi) : "f"(x));
+    const float r = x - __uint_as_float(hi);
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(lo) : "f"(r));
+}
+
 __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
     const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
     const __nv_bfloat162 l = __floats2bfloat162_rn(a - __low2float(h), b - __high2float(h));
@@ -100,22 +119,26 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t&
     lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
-template <int RP, int LB>
+// TF: TF32x3 operands (hi and lo TF32, 4 elements per 16-byte core-matrix
+// row, K = 8 per MMA, F padded to 8) instead of BF16x3 (8 elements per row,
+// K = 16 per MMA, F padded to 16); everything else is shared.
+template <int RP, int LB, bool TF = false>
 __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ U, int64_t I, int R, int F, int Fp,
                                                       int64_t L, int G, int Tp, float* __restrict__ tree,
                                                       float* __restrict__ top, float* __restrict__ copy_to,
                                                       int* __restrict__ status) {
     constexpr int NL = 128 / RP;              // leaves side by side in one product
     constexpr int NCH = (LB + NL - 1) / NL;   // products per group of LB leaves
+    constexpr int EPC = TF ? 4 : 8;           // K elements per 16-byte core-matrix row
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tmem_base;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int T = tri_size(R);
-    const int nk8 = Fp >> 3;                       // 8-row core-matrix columns along K
+    const int nk8 = Fp / EPC;                       // core-matrix columns along K
     const uint32_t sbo = (uint32_t)nk8 * 128u;      // bytes per 8-row group along M/N
     unsigned char* Xh = smem;
-    unsigned char* Xl = smem + 128u * sbo / 8u;     // 128 rows x Fp bf16
+    unsigned char* Xl = smem + 128u * sbo / 8u;     // 128 rows x Fp operands
     float* sG = reinterpret_cast<float*>(Xl + 128u * sbo / 8u);
     float* stk = sG + (size_t)LB * Tp;
 
@@ -147,21 +170,28 @@ __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ 
                 const int p = task & 127, k8 = task >> 7;
                 const int b = p / RP, c = p % RP;
                 const int ll = ch * NL + b;
-                const int64_t row0 = (gleaf0 + ll) * (int64_t)F + 8 * k8;
+                const int64_t row0 = (gleaf0 + ll) * (int64_t)F + EPC * k8;
                 const bool col_ok = ll < LB && c < R;
-                float v[8];
+                float v[EPC];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) {
+                for (int i = 0; i < EPC; ++i) {
                     const int64_t row = row0 + i;
-                    const bool ok = col_ok && 8 * k8 + i < F && row < I;
+                    const bool ok = col_ok && EPC * k8 + i < F && row < I;
                     v[i] = ok ? __ldg(U + row * R + c) : 0.f;
                     if (ok && copy_to) copy_to[row * R + c] = v[i];
                 }
                 uint4 h, l;
-                split2(v[0], v[1], h.x, l.x);
-                split2(v[2], v[3], h.y, l.y);
-                split2(v[4], v[5], h.z, l.z);
-                split2(v[6], v[7], h.w, l.w);
+                if constexpr (TF) {
+                    split_tf32(v[0], h.x, l.x);
+                    split_tf32(v[1], h.y, l.y);
+                    split_tf32(v[2], h.z, l.z);
+                    split_tf32(v[3], h.w, l.w);
+                } else {
+                    split2(v[0], v[1], h.x, l.x);
+                    split2(v[2], v[3], h.y, l.y);
+                    split2(v[EPC - 4], v[EPC - 3], h.z, l.z);
+                    split2(v[EPC - 2], v[EPC - 1], h.w, l.w);
+                }
                 const uint32_t off = (uint32_t)(p >> 3) * sbo + (uint32_t)k8 * 128u + (uint32_t)(p & 7) * 16u;
                 *reinterpret_cast<uint4*>(Xh + off) = h;
                 *reinterpret_cast<uint4*>(Xl + off) = l;
@@ -172,11 +202,18 @@ __global__ void __launch_bounds__(128) tree_leaves_tc(const float* __restrict__ 
             if (tid == 0) {
                 tc_fence_after();
                 const uint32_t xh = tc_saddr(Xh), xl = tc_saddr(Xl);
-                for (int ks = 0; ks < Fp / 16; ++ks) {
-                    const uint32_t ko = (uint32_t)ks * 256u;  // two 16-byte core-matrix columns per K = 16
-                    tc_mma(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), ks > 0);
-                    tc_mma(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xl + ko, 128u, sbo), 1u);
-                    tc_mma(tmem, tc_desc(xl + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), 1u);
+                // two 16-byte core-matrix columns per MMA (K = 16 BF16 or 8 TF32)
+                for (int ks = 0; ks < Fp / (2 * EPC); ++ks) {
+                    const uint32_t ko = (uint32_t)ks * 256u;
+                    if constexpr (TF) {
+                        tc_mma_tf32(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), ks > 0);
+                        tc_mma_tf32(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xl + ko, 128u, sbo), 1u);
+                        tc_mma_tf32(tmem, tc_desc(xl + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), 1u);
+                    } else {
+                        tc_mma(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), ks > 0);
+                        tc_mma(tmem, tc_desc(xh + ko, 128u, sbo), tc_desc(xl + ko, 128u, sbo), 1u);
+                        tc_mma(tmem, tc_desc(xl + ko, 128u, sbo), tc_desc(xh + ko, 128u, sbo), 1u);
+                    }
                 }
                 tc_commit(&bar);
             }
@@ -518,34 +555,38 @@ __global__ void __launch_bounds__(PIPE_THREADS, PipeCfg<RP>::MINB)
 
 int padded_rank(int R) { return R <= 16 ? 16 : R <= 32 ? 32 : R <= 64 ? 64 : 128; }
 
-size_t tc_smem(int F, int LB, int G, int Tp) {
-    const int Fp = (F + 15) / 16 * 16;
+int tc_fp(int F, bool tf) { return tf ? (F + 7) / 8 * 8 : (F + 15) / 16 * 16; }
+
+size_t tc_smem(int F, int LB, int G, int Tp, bool tf = false) {
+    const int Fp = tc_fp(F, tf);
     int lv = 0;
     while ((1 << lv) < G) ++lv;
-    const size_t need = (size_t)2 * 128 * Fp * 2 + (size_t)LB * Tp * 4 + (size_t)2 * (lv + 1) * Tp * 4;
+    // the cross-group stack only when there are groups to merge
+    const size_t need = (size_t)2 * 128 * Fp * (tf ? 4 : 2) + (size_t)LB * Tp * 4 +
+                        (G > 1 ? (size_t)2 * (lv + 1) * Tp * 4 : 0);
     return std::max<size_t>(need, 48 * 1024);  // at most 4 CTAs (512 TMEM columns) per SM
 }
 
-template <int RP, int LB>
+template <int RP, int LB, bool TF>
 cudaError_t launch_tc(const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree, float* top,
                       float* copy_to, int* status, int64_t ctas, size_t smem, cudaStream_t st) {
-    auto k = tree_leaves_tc<RP, LB>;
+    auto k = tree_leaves_tc<RP, LB, TF>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const int Fp = (F + 15) / 16 * 16;
+    const int Fp = tc_fp(F, TF);
     k<<<(unsigned)ctas, 128, smem, st>>>(U, I, R, F, Fp, L, G, Tp, tree, top, copy_to, status); count_launch();
     return cudaGetLastError();
 }
 
-template <int RP>
+template <int RP, bool TF>
 cudaError_t launch_tc_lb(int LB, const float* U, int64_t I, int R, int F, int64_t L, int G, int Tp, float* tree,
                          float* top, float* copy_to, int* status, int64_t ctas, size_t smem, cudaStream_t st) {
     switch (LB) {
-        case 1: return launch_tc<RP, 1>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        case 2: return launch_tc<RP, 2>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        case 4: return launch_tc<RP, 4>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        case 8: return launch_tc<RP, 8>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        default: return launch_tc<RP, 16>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 1: return launch_tc<RP, 1, TF>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 2: return launch_tc<RP, 2, TF>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 4: return launch_tc<RP, 4, TF>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 8: return launch_tc<RP, 8, TF>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        default: return launch_tc<RP, 16, TF>(U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
     }
 }
 
@@ -610,7 +651,8 @@ bool tree_tc_pipelined(int R, int F, const float* U) {
 // (2 x 256 TMEM columns) share an SM.  Else:
 // LB leaves per group (power of two, <= 16, <= L, one group's leaf Grams
 // <= 64 KB), G groups per CTA (power of two, <= 8, shared memory <= 200 KB).
-void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out) {
+void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_out, int* G_out, size_t* smem_out,
+                      bool tf32) {
     (void)R;
     int LB = 1, G = 1;
     size_t smem;
@@ -631,8 +673,8 @@ void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_o
     } else {
         while (LB < 16 && (int64_t)LB * 2 <= L && (size_t)LB * 2 * Tp * 4 <= 64 * 1024) LB *= 2;
         const int64_t groups = L / LB;
-        while (G < 8 && (int64_t)G * 2 <= groups && tc_smem(F, LB, G * 2, Tp) <= 200 * 1024) G *= 2;
-        smem = tc_smem(F, LB, G, Tp);
+        while (G < 8 && (int64_t)G * 2 <= groups && tc_smem(F, LB, G * 2, Tp, tf32) <= 200 * 1024) G *= 2;
+        smem = tc_smem(F, LB, G, Tp, tf32);
     }
     *LB_out = LB;
     *G_out = G;
@@ -641,7 +683,13 @@ void tree_tc_geometry(int R, int F, int64_t L, int Tp, bool pipelined, int* LB_o
 
 cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64_t L, int LB, int G, int Tp,
                                   float* tree, float* top, float* copy_to, int* status, int64_t ctas, size_t smem,
-                                  bool pipelined, int num_sms, cudaStream_t st) {
+                                  bool pipelined, int num_sms, cudaStream_t st, bool tf32) {
+    if (tf32) switch (padded_rank(R)) {
+            case 16: return launch_tc_lb<16, true>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+            case 32: return launch_tc_lb<32, true>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+            case 64: return launch_tc_lb<64, true>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+            default: return launch_tc_lb<128, true>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        }
     if (pipelined) switch (padded_rank(R)) {
             case 16: return launch_pipe_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
             case 32: return launch_pipe_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
@@ -649,10 +697,10 @@ cudaError_t launch_tree_leaves_tc(const float* U, int64_t I, int R, int F, int64
             default: return launch_pipe_lb<128>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, num_sms, st);
         }
     switch (padded_rank(R)) {
-        case 16: return launch_tc_lb<16>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        case 32: return launch_tc_lb<32>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        case 64: return launch_tc_lb<64>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
-        default: return launch_tc_lb<128>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 16: return launch_tc_lb<16, false>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 32: return launch_tc_lb<32, false>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        case 64: return launch_tc_lb<64, false>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
+        default: return launch_tc_lb<128, false>(LB, U, I, R, F, L, G, Tp, tree, top, copy_to, status, ctas, smem, st);
     }
 }
 

@@ -15,7 +15,7 @@ LIB_PATH = os.path.join(_HERE, "libkrpls.so")
 
 KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EZERO, KRP_ESINGULAR, KRP_ENUMERIC, KRP_ETIMEOUT, KRP_ESTATE = (
     0, -1, -2, -3, -4, -5, -6, -7, -8)
-KRP_PREC_FP32, KRP_PREC_BF16X3, KRP_PREC_EXACT = 0, 1, 2
+KRP_PREC_FP32, KRP_PREC_BF16X3, KRP_PREC_EXACT, KRP_PREC_TF32X3 = 0, 1, 2, 3
 KRP_PINV_FALLBACK = 1
 KRP_DESCENT_AUTO, KRP_DESCENT_TEAM, KRP_DESCENT_NODE_MAJOR = 0, 1, 2
 
