@@ -272,17 +272,27 @@ __global__ void __launch_bounds__(256) normal_solve(const float* __restrict__ pa
     normal_solve_body(part, nparts, R, nrhs, mode, flags, X, Xd, status, gbuf, part_exp);
 }
 
-// The FP64 reduction of normal_solve spread over CTAs (one thread per output
-// entry, partials in the same fixed order): at R = 100 and 304 partials it is
-// 1.5 M FP64 adds, too many for the one SM the solve runs on.
+// The FP64 reduction of normal_solve spread over CTAs: at R = 100 and 304
+// partials it is 1.5 M FP64 adds, too many for the one SM the solve runs on.
+// A CTA takes 32 output entries (one per lane); warp w sums partials w, w + 8,
+// ... in order, then the 8 warps' sums are added in warp order.
 __global__ void __launch_bounds__(256) normal_reduce(const float* __restrict__ part,
                                                      const float* __restrict__ part_exp, int nparts, int nout,
                                                      double* __restrict__ sums) {
-    const int id = blockIdx.x * blockDim.x + threadIdx.x;
-    if (id >= nout) return;
+    __shared__ double ws[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int id = blockIdx.x * 32 + lane;
     double a = 0.0;
-    for (int p = 0; p < nparts; ++p) a += (double)part[(size_t)p * nout + id] * ldexp(1.0, 2 * (int)part_exp[p]);
-    sums[id] = a;
+    if (id < nout)
+        for (int p = warp; p < nparts; p += 8) a += (double)part[(size_t)p * nout + id] * ldexp(1.0, 2 * (int)part_exp[p]);
+    ws[warp][lane] = a;
+    __syncthreads();
+    if (warp == 0 && id < nout) {
+        double t = 0.0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) t += ws[w][lane];
+        sums[id] = t;
+    }
 }
 
 __global__ void __launch_bounds__(256) normal_solve_sums(const double* __restrict__ sums, int R, int nrhs, int mode,
@@ -396,7 +406,7 @@ krp_status normal_common(krp_sampler* s, int64_t J, const float* SA, const float
     if (smem2 > 48 * 1024)
         cudaFuncSetAttribute(normal_solve_sums, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
     double* sums = reinterpret_cast<double*>(s->solve_scratch + sums_off);
-    normal_reduce<<<(nout + 255) / 256, 256, 0, s->stream>>>(s->solve_scratch, part_exp, nparts, nout, sums);
+    normal_reduce<<<(nout + 31) / 32, 256, 0, s->stream>>>(s->solve_scratch, part_exp, nparts, nout, sums);
     count_launch();
     // M⁻¹ for the sparse solve at larger R: its R triangular solves over R CTAs
     const bool split = mode == 1 && R >= 48;

@@ -38,6 +38,11 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, int src
                  "r"(src_bytes)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem, int src_bytes) {
+    const unsigned saddr = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(saddr), "l"(gmem), "r"(src_bytes)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -46,7 +51,7 @@ __device__ __forceinline__ void cp_async_wait() {
 
 // Stage rows [row0, row0 + nrows) of U (zero beyond I) into sU (row stride R).
 // VEC: 16-byte cp.async (needs R % 4 == 0 so every chunk is 16-byte aligned);
-// otherwise plain synchronous loads.
+// otherwise 4-byte cp.async.  The caller commits and waits.
 template <bool VEC>
 __device__ __forceinline__ void stage_rows(float* sU, const float* __restrict__ U, int64_t I, int R,
                                            int64_t row0, int nrows) {
@@ -60,7 +65,8 @@ __device__ __forceinline__ void stage_rows(float* sU, const float* __restrict__ 
             cp_async16(sU + off, bytes > 0 ? (const void*)(src + off) : (const void*)U, bytes);
         }
     } else {
-        for (int64_t e = threadIdx.x; e < nf; e += blockDim.x) sU[e] = e < valid ? src[e] : 0.f;
+        for (int64_t e = threadIdx.x; e < nf; e += blockDim.x)
+            cp_async4(sU + e, e < valid ? (const void*)(src + e) : (const void*)U, e < valid ? 4 : 0);
     }
 }
 
@@ -227,7 +233,7 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
         }
     const int64_t leaf0 = blk * G * LB;
     stage_rows<VEC>(sU0, U, I, R, leaf0 * F, rows);
-    if (VEC) cp_async_commit();
+    cp_async_commit();
     for (int g = 0; g < G; ++g) {
         float* cur = (DB && (g & 1)) ? sU1 : sU0;
         if (DB) {
@@ -238,7 +244,7 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
             } else {
                 cp_async_wait<0>();
             }
-        } else if (VEC) {
+        } else {
             cp_async_wait<0>();
         }
         __syncthreads();
@@ -257,7 +263,7 @@ __device__ __forceinline__ void tree_leaves_fp32_body(const float* __restrict__ 
         if (!DB && g + 1 < G) {
             __syncthreads();
             stage_rows<VEC>(sU0, U, I, R, (leaf0 + (int64_t)(g + 1) * LB) * F, rows);
-            if (VEC) cp_async_commit();
+            cp_async_commit();
         }
     }
 }
