@@ -54,7 +54,7 @@ struct FastCfg {
     static constexpr int TPMAX = ((RMAX * (RMAX + 1) / 2) + (X ? 1 : 0) + 7) & ~7;
     static constexpr int NC4 = TPMAX / 4;           // float4 chunks per node
     static constexpr int NCH = (NC4 + 31) / 32;     // chunks per lane
-    static constexpr int WARPS = 8;
+    static constexpr int WARPS = X ? 4 : 8;   // exact-decision kernels: more, smaller CTAs
     static constexpr int RPT = (4 * RMAX + 31) / 32;  // leaf rows per lane (F <= 4R)
     // per-warp shared memory: 3 staged nodes (slots 0..1 on a stage's first
     // fetch, then slots c, 2c, 2c+1; also the leaf rows), h (hi, lo), h̃ (hi,
@@ -915,7 +915,7 @@ __device__ __forceinline__ void descent_fast_body(const FastParams& P, int64_t c
 // their double-float state in registers at two CTAs per SM (at three they
 // spill, and run slower).
 template <int RMAX, bool EXACT, bool TRACE = false>
-__global__ void __launch_bounds__(256, EXACT ? 2 : (RMAX <= 16 ? 4 : 3))
+__global__ void __launch_bounds__(EXACT ? 128 : 256, EXACT ? 5 : (RMAX <= 16 ? 4 : 3))
     krp_descent_fast(const __grid_constant__ FastParams P) {
     descent_fast_body<RMAX, EXACT, TRACE>(P, blockIdx.x, gridDim.x);
 }
@@ -928,11 +928,11 @@ cudaError_t launch_fast_t(const FastParams& P, int num_sms, cudaStream_t st) {
     cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, C::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, C::WARPS * 32, C::SMEM);
     per_sm = per_sm > 0 ? per_sm : 1;
-    const int64_t need = (P.J + 7) / 8;
+    const int64_t need = (P.J + C::WARPS - 1) / C::WARPS;
     const int64_t grid = need < (int64_t)num_sms * per_sm ? need : (int64_t)num_sms * per_sm;
-    k<<<(unsigned)grid, 256, C::SMEM, st>>>(P); count_launch();
+    k<<<(unsigned)grid, C::WARPS * 32, C::SMEM, st>>>(P); count_launch();
     return cudaGetLastError();
 }
 }  // namespace
