@@ -931,9 +931,10 @@ krp_status solve_sparse_impl(krp_sampler* s, const krp_sptensor* tc, int j, int6
     krp_status st = normal_inverse(s, J, SA, flags);
     if (st != KRP_OK) return st;
     const double* Minv = s->solve64 + (size_t)(2 * R * R + R * 128);
-    // split-precision samplers apply M⁻¹ on the tensor cores (TF32x3); FP32
-    // samplers keep the FP32 SIMT product
-    if ((s->prec == KRP_PREC_BF16X3 || s->prec == KRP_PREC_TF32X3) && minv_tc_supported(R))
+    // split-precision samplers apply M⁻¹ on the tensor cores (TF32x3) from R =
+    // 64 (below, the SIMT product is the faster); FP32 samplers keep the SIMT
+    // product
+    if ((s->prec == KRP_PREC_BF16X3 || s->prec == KRP_PREC_TF32X3) && R >= 64 && minv_tc_supported(R))
         e = launch_minv_tc(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->als_part, s->status, s->num_sms, s->stream);
     else
         e = launch_apply_minv(t->Y, RS, Minv, s->I[j], R, U_out, sumsq, s->als_part, s->num_sms, s->stream);

@@ -597,9 +597,13 @@ krp_status build_tree(krp_sampler* s, int j, int precision, const float* src) {
     const bool vec = (R % 4) == 0;
     // exact-decision samplers build every tree with exactly accumulated leaves
     float* tree_lo = s->exact ? s->tree_lo[j] : nullptr;
+    // BF16x3 takes the tensor cores where the pipelined kernel applies (F R a
+    // multiple of 4, its stages fitting); elsewhere (R = 25, F = R = 128) the
+    // FP32 leaves are faster and more accurate.  TF32x3 always takes the
+    // non-pipelined tensor-core kernel.
     const bool tf32 = precision == KRP_PREC_TF32X3;
-    const bool tc = !s->exact && (precision == KRP_PREC_BF16X3 || tf32) && tree_tc_supported(R, F);
-    const bool tc_pipe = tc && !tf32 && tree_tc_pipelined(R, F, src);   // the pipelined form is BF16x3 only
+    const bool tc_pipe = !s->exact && precision == KRP_PREC_BF16X3 && tree_tc_pipelined(R, F, src);
+    const bool tc = !s->exact && (tc_pipe || (tf32 && tree_tc_supported(R, F)));
     int LB, G, threads = 128;
     size_t smem;
     if (tc)

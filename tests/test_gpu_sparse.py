@@ -31,9 +31,10 @@ def make(dims, R, coords, vals, Us, prec=0):
 
 
 # I_j spans several row tiles of Y M⁻¹ (64, 128 or 256 rows) with a ragged
-# tail; R covers each padded width (32, 64, 128) and R % 4 != 0.  prec 1
-# (BF16x3 samplers) takes Y M⁻¹ on the tensor cores as TF32x3 for R <= 104.
-@pytest.mark.parametrize("prec", [0, 1])
+# tail; R covers each padded width (32, 64, 128) and R % 4 != 0.  prec 1 and
+# 3 (BF16x3, TF32x3 samplers) take Y M⁻¹ on the tensor cores as TF32x3 for
+# 64 <= R <= 104.
+@pytest.mark.parametrize("prec", [0, 1, 3])
 @pytest.mark.parametrize("dims,R,J,nnz", [((60, 50, 20), 6, 3000, 4000), ((700, 40, 30), 40, 3000, 20000),
                                           ((300, 33, 29), 50, 3000, 15000), ((520, 30, 24), 100, 4000, 20000),
                                           ((1100, 40, 30), 104, 4000, 30000)])
