@@ -67,7 +67,7 @@ def parse():
                          "(per-problem launches vs one launch per phase vs graph replay); "
                          "rank_sweep: N=4, I=2^20, U(-1,1), J=2^17 at --rank R")
     ap.add_argument("--rank", type=int, default=32)
-    ap.add_argument("--descent", choices=["auto", "team", "node_major"], default="auto",
+    ap.add_argument("--descent", choices=["auto", "team", "node_major", "node_major_tc"], default="auto",
                     help="rank_sweep: descent form for 32 < R <= 128")
     ap.add_argument("--ranks", default="25,50,100", help="sparse_als: decomposition ranks")
     ap.add_argument("--nnz", type=int, default=200_000_000, help="sparse_als: nonzeros")
@@ -323,7 +323,7 @@ def run_rank_sweep(args):
     stream = torch.cuda.Stream(device=dev)
     Us = synth.uniform_factors(N, I, R, seed=0)
     s = Sampler([I] * N, R, R, stream=stream)
-    s.set_descent_form({"auto": 0, "team": 1, "node_major": 2}[args.descent])
+    s.set_descent_form({"auto": 0, "team": 1, "node_major": 2, "node_major_tc": 3}[args.descent])
     for k in range(N):
         s.set_factor(k, torch.from_numpy(Us[k]).to(dev))
     Xt = synth.planted_solution(R, NRHS, seed=1)
@@ -377,6 +377,7 @@ def run_rank_sweep(args):
     achieved = path_bytes * J / (draw_ms / 1e3) / 1e9
     kernel = "krp_descent_fast" if R <= 32 else (
         ("krp_descent_nm<64>" if R <= 64 else "krp_descent_nm<128>") if args.descent == "node_major" else
+        "nt_level<0..2> + nt_scan + nt_part (tensor-core node-major)" if args.descent == "node_major_tc" else
         ("krp_descent_team<64,2>" if R <= 64 else "krp_descent_team<128,8>"))
     roof = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": path_bytes * J,

@@ -168,10 +168,20 @@ krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t se
  *     every distinct node is fetched once per batch (shared upper levels cost
  *     one fetch per CTA, deeper ones stream through a ring of copies across
  *     the batch); the weights are formed per sample and level.
+ *   KRP_DESCENT_NODE_MAJOR_TC (App. A.10's level-synchronous batches): all J
+ *     samples advance one tree level at a time, grouped by node; for each
+ *     group of up to 128 samples with vectors H (128 x R) the left child's
+ *     masses come from D = H G_v on the tcgen05 tensor cores (split TF32,
+ *     m_s = Σ_j D[s, j] H[s, j]) and the leaf's row weights from
+ *     D = H U_leafᵀ; decisions within 1e-6 C of an edge are re-taken in
+ *     double-float.  Needs F <= 128 and a device workspace of about
+ *     J (3 R + 24) floats; where that does not hold (or no workspace can be
+ *     allocated, e.g. during a graph capture) the team form runs instead.
  * KRP_EINVAL for another value. */
 #define KRP_DESCENT_AUTO 0
 #define KRP_DESCENT_TEAM 1
 #define KRP_DESCENT_NODE_MAJOR 2
+#define KRP_DESCENT_NODE_MAJOR_TC 3
 krp_status krp_set_descent_form(krp_sampler* s, int form);
 
 /* Sampled-row gather: SA[s,:] = weight[s] * ⊛_{k != exclude_j} U_k[idx[k][s], :]

@@ -1,7 +1,8 @@
 // Dispatch of the batched conditional descent (a4 + a5, a6 fused): R <= 32
 // runs descent_fast.cu's warp-per-sample kernel; 32 < R <= 128 descent_team.cu's
 // team-per-sample kernel (the default, faster on GB300) or descent_nm.cu's
-// node-major batches (krp_set_descent_form); all follow the sampling loop of Alg. 2 with the
+// node-major batches or descent_nmtc.cu's level-synchronous node-major form
+// with the masses on the tensor cores (krp_set_descent_form); all follow the sampling loop of Alg. 2 with the
 // loops exchanged as in App. A.6 and Alg. 4 on E_k and Z_k.  Also the
 // sampled-row gather (a6) as a separate kernel.
 #include "common.cuh"
@@ -15,6 +16,9 @@ krp_status launch_descent(krp_sampler* s, int exclude_j, int64_t J, uint64_t see
                           int32_t* idx, float* weight, float* logq, float* SA, float* trace, int64_t n_trace) {
     cudaError_t fe = cudaSuccess;
     if (launch_descent_fast(s, exclude_j, J, seed, draw_id, idx, weight, logq, SA, trace, n_trace, &fe))
+        return fe == cudaSuccess ? KRP_OK : cuda_check(s, fe, "descent launch");
+    if (s->descent_form == KRP_DESCENT_NODE_MAJOR_TC &&
+        launch_descent_nmtc(s, exclude_j, J, seed, draw_id, idx, weight, logq, SA, trace, n_trace, &fe))
         return fe == cudaSuccess ? KRP_OK : cuda_check(s, fe, "descent launch");
     if (s->descent_form == KRP_DESCENT_NODE_MAJOR &&
         launch_descent_nm(s, exclude_j, J, seed, draw_id, idx, weight, logq, SA, trace, n_trace, &fe))

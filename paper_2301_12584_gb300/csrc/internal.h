@@ -55,6 +55,9 @@ struct krp_sampler {
     double* als_sumsq = nullptr;
     double* als_part = nullptr;   // per-CTA partial sums (column norms, fit), summed in a fixed order
     int64_t als_J = 0;
+    // workspace of the tensor-core node-major descent (allocated on first use)
+    char* nm_ws = nullptr;
+    size_t nm_ws_bytes = 0;
     std::string last_error;
     int last_exclude = -2;      // exclude_j of the last prep (for inspection)
     // a captured sequence of this sampler's calls (krp_capture_begin / _end)
@@ -235,6 +238,8 @@ bool launch_descent_team(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed
                          float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
 // 32 < R <= 128 node-major path (descent_nm.cu): CTA batches advanced level by
 // level; false if R is out of range or no batch fits the shared memory.
+bool launch_descent_nmtc(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
+                         float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
 bool launch_descent_nm(krp_sampler* s, int exclude_j, int64_t J, uint64_t seed, uint64_t draw_id, int32_t* idx,
                        float* weight, float* logq, float* SA, float* trace, int64_t n_trace, cudaError_t* err);
 cudaError_t launch_wait_timeout_probe(krp_sampler* s, int tries);

@@ -119,6 +119,7 @@ void krp_destroy(krp_sampler* s) {
     cudaFree(s->als_SA);
     cudaFree(s->als_sumsq);
     cudaFree(s->als_part);
+    cudaFree(s->nm_ws);
     delete s;
 }
 
@@ -240,7 +241,8 @@ krp_status krp_set_factor(krp_sampler* s, int j, const float* U) {
 
 krp_status krp_set_descent_form(krp_sampler* s, int form) {
     if (!s) return fail(nullptr, KRP_EINVAL, "null sampler");
-    if (form != KRP_DESCENT_AUTO && form != KRP_DESCENT_TEAM && form != KRP_DESCENT_NODE_MAJOR)
+    if (form != KRP_DESCENT_AUTO && form != KRP_DESCENT_TEAM && form != KRP_DESCENT_NODE_MAJOR &&
+        form != KRP_DESCENT_NODE_MAJOR_TC)
         return fail(s, KRP_EINVAL, "krp_set_descent_form: unknown form");
     s->descent_form = form;
     return KRP_OK;

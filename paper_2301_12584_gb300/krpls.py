@@ -17,7 +17,7 @@ KRP_OK, KRP_EINVAL, KRP_ENOMEM, KRP_ECUDA, KRP_EZERO, KRP_ESINGULAR, KRP_ENUMERI
     0, -1, -2, -3, -4, -5, -6, -7, -8)
 KRP_PREC_FP32, KRP_PREC_BF16X3, KRP_PREC_EXACT, KRP_PREC_TF32X3 = 0, 1, 2, 3
 KRP_PINV_FALLBACK = 1
-KRP_DESCENT_AUTO, KRP_DESCENT_TEAM, KRP_DESCENT_NODE_MAJOR = 0, 1, 2
+KRP_DESCENT_AUTO, KRP_DESCENT_TEAM, KRP_DESCENT_NODE_MAJOR, KRP_DESCENT_NODE_MAJOR_TC = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "KRP_OK", -1: "KRP_EINVAL", -2: "KRP_ENOMEM", -3: "KRP_ECUDA", -4: "KRP_EZERO",
                 -5: "KRP_ESINGULAR", -6: "KRP_ENUMERIC", -7: "KRP_ETIMEOUT", -8: "KRP_ESTATE"}
@@ -162,7 +162,8 @@ class Sampler:
                                          _P(_ptr(idx)), _P(_ptr(weight)), _P(_ptr(logq)), _P(_ptr(SA))))
 
     def set_descent_form(self, form):
-        """KRP_DESCENT_AUTO / _NODE_MAJOR (batched node-major) or _TEAM (team per sample), 32 < R <= 128."""
+        """KRP_DESCENT_AUTO / _TEAM (team per sample), _NODE_MAJOR (batched node-major) or
+        _NODE_MAJOR_TC (level-synchronous node-major, masses on the tensor cores), 32 < R <= 128."""
         self._check(self._lib.krp_set_descent_form(self.h, int(form)))
 
     def sample_prepare(self, exclude_j):

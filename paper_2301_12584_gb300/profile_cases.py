@@ -13,6 +13,8 @@
   python -m paper_2301_12584_gb300.profile_cases build100_tc # tree_leaves_tc_pipe<128,.> (BF16x3), same factor
   python -m paper_2301_12584_gb300.profile_cases prep100    # prep_pinv / prep_eig / prep_etree, R=100, N=3
   python -m paper_2301_12584_gb300.profile_cases minv100    # apply_minv<128>: U_0 = Y M⁻¹, 2^21 x 100
+  python -m paper_2301_12584_gb300.profile_cases rank_tc64 # tensor-core node-major draw, N=4, I=2^20, R=64, J=2^17
+  python -m paper_2301_12584_gb300.profile_cases rank_tc128 # the same at R=128
   python -m paper_2301_12584_gb300.profile_cases peaks      # FP32 / FP64 FMA and L2 read throughput probes
 
 Each case runs its kernel a few times (the first launches warm up), checks the
@@ -65,6 +67,24 @@ def descent100(form=0):
     SA = torch.zeros((J, R), device="cuda")
     for d in range(3):
         s.sample(0, J, 1, d, idx, w, None, SA)
+    assert s.sync_status() == 0, s.last_error()
+
+
+def rank_tc(R=64, form=3, draws=2):
+    """The rank sweep's draw (N=4, I=2^20, F=R, J=2^17) in the tensor-core
+    node-major form (form 3) or another form."""
+    N, I, J = 4, 1 << 20, 1 << 17
+    Us = synth.uniform_factors(N, I, R, seed=0)
+    s = Sampler([I] * N, R, R)
+    s.set_descent_form(form)
+    for k in range(N):
+        s.set_factor(k, torch.from_numpy(Us[k]).cuda())
+    idx = torch.zeros((N, J), dtype=torch.int32, device="cuda")
+    w = torch.zeros(J, device="cuda")
+    SA = torch.zeros((J, R), device="cuda")
+    s.sample_prepare(-1)
+    for d in range(draws):
+        s.sample_draw(-1, J, 1, d, idx, w, None, SA)
     assert s.sync_status() == 0, s.last_error()
 
 
@@ -194,6 +214,7 @@ if __name__ == "__main__":
      "prep": prep, "prep100": prep100, "minv100": minv100, "minv100_tc": minv100_tc, "sweep25": sweep25,
      "sweep100_bf16x3": lambda: sweep25(precision=1, R=100),
      "sweep100_bf16x3_2e8": lambda: sweep25(precision=1, nnz=200_000_000, R=100),
+     "rank_tc64": lambda: rank_tc(64), "rank_tc128": lambda: rank_tc(128),
      "peaks": peaks}[sys.argv[1]]()
     torch.cuda.synchronize()
     print("ok")

@@ -115,13 +115,18 @@ def test_tree_matches_partial_grams(I, R, F):
 # -------------------------------------------------- sampler index parity ----
 @pytest.mark.parametrize("case", ["cfg_tiny", "ragged", "excl1", "R5_F3", "N4", "R1", "N1", "R32", "F1",
                                   "R64_N4", "R128", "R64_N4_nm", "R128_nm", "R37_excl", "R37_excl_nm",
-                                  "R100_ragged", "R100_ragged_nm", "R48_F20_nm"])
+                                  "R100_ragged", "R100_ragged_nm", "R48_F20_nm", "R64_N4_tc", "R128_tc",
+                                  "R37_excl_tc", "R100_ragged_tc", "R48_F20_tc", "R40_deep_tc"])
 def test_sampler_index_parity(case):
     """For 32 < R <= 128 the default descent is the team-per-sample kernel;
-    "_nm" cases draw with the node-major batched kernel."""
-    from paper_2301_12584_gb300.krpls import KRP_DESCENT_NODE_MAJOR
+    "_nm" cases draw with the node-major batched kernel, "_tc" cases with the
+    level-synchronous node-major form whose masses run on the tensor cores
+    (R40_deep: 256 leaves per factor, ~32 samples per leaf, so the deep levels
+    hold many small groups)."""
+    from paper_2301_12584_gb300.krpls import KRP_DESCENT_NODE_MAJOR, KRP_DESCENT_NODE_MAJOR_TC
     nm = case.endswith("_nm")
-    case = case.replace("_nm", "")
+    tc = case.endswith("_tc")
+    case = case.replace("_nm", "").replace("_tc", "")
     J = 1 << 15
     excl = -1
     F = 0
@@ -153,9 +158,13 @@ def test_sampler_index_parity(case):
         Us, F, J = synth.gaussian_factors(3, [1234, 777, 2001], 100, seed=14), 100, 1 << 12
     elif case == "R48_F20":
         Us, F, J = synth.skewed_row_factors(3, 700, 48, seed=15), 20, 1 << 13
+    elif case == "R40_deep":
+        Us, F, J = synth.uniform_factors(3, 8000, 40, seed=16), 40, 1 << 13
     s = sampler_for(Us, F)
     if nm:
         s.set_descent_form(KRP_DESCENT_NODE_MAJOR)
+    if tc:
+        s.set_descent_form(KRP_DESCENT_NODE_MAJOR_TC)
     out = draw(s, Us, excl, J, seed=12345, draw_id=3, logq=True)
     U64 = [U.astype(np.float64) for U in Us]
     eig = None
@@ -180,7 +189,7 @@ def test_sampler_index_parity(case):
     if case == "R32":
         mism = check_index_parity(out["idx"], ref, J, tol=2e-7)
         assert mism <= 2e-3 * J, f"{mism} mismatches of {J}"
-    elif case in ("R64_N4", "R128", "R37_excl", "R100_ragged", "R48_F20"):
+    elif case in ("R64_N4", "R128", "R37_excl", "R100_ragged", "R48_F20", "R40_deep"):
         # FP32 tree storage: a mass is off by ~6e-8 x (sum of |terms|), and with
         # R^2 terms of both signs that sum exceeds the mass itself; flips stay
         # within 1e-5 C of an edge, at a rate like the R32 case's
@@ -251,10 +260,10 @@ def test_branch_probabilities_match_fp64_tree():
     s.close()
 
 
-@pytest.mark.parametrize("form", [2, 1])
+@pytest.mark.parametrize("form", [2, 1, 3])
 def test_branch_probabilities_r64(form):
-    """Per-level branch probabilities m_L / m_c of the node-major (2) and team
-    (1) descents at R = 64 against the FP64 trees, replaying the GPU's own
+    """Per-level branch probabilities m_L / m_c of the node-major (2), team (1)
+    and tensor-core node-major (3) descents at R = 64 against the FP64 trees, replaying the GPU's own
     eigendecomposition (checked to reconstruct G_{>k}; the basis inside
     clusters of eigenvalues is not pinned)."""
     Us = synth.skewed_entry_factors(3, [300, 260, 170], 64, seed=21)
@@ -304,7 +313,7 @@ def test_branch_probabilities_r64(form):
     s.close()
 
 
-@pytest.mark.parametrize("form", [1, 2])
+@pytest.mark.parametrize("form", [1, 2, 3])
 @pytest.mark.parametrize("dims,R,F,J,excl", [([30], 40, 40, 7, -1),              # one factor, one partial leaf, rank 30
                                              ([20], 24, 24, 9, -1),              # R <= 32 path, rank 20
                                              ([50, 40], 8, 4, 1, 0),              # one included factor, J = 1
@@ -314,7 +323,8 @@ def test_branch_probabilities_r64(form):
                                              ([130, 140, 150], 120, 120, 1, 1)])  # J = 1, an excluded factor
 def test_large_r_edge_cases(form, dims, R, F, J, excl):
     """Degenerate shapes of the R > 32 descents (team: form 1, node-major:
-    form 2) against the oracle, replaying the GPU's eigendecompositions."""
+    form 2, tensor-core node-major: form 3) against the oracle, replaying the
+    GPU's eigendecompositions."""
     Us = synth.gaussian_factors(len(dims), dims, R, seed=sum(dims) + R)
     s = sampler_for(Us, F)
     s.set_descent_form(form)
@@ -350,21 +360,51 @@ def test_pinv_of_a_cluster_of_zero_eigenvalues(I, R):
     s.close()
 
 
-def test_node_major_and_team_draws_agree():
-    """The two descent forms differ only in the rounding of the masses: the
-    same draws but for rare near-edge flips, and the same weights."""
-    from paper_2301_12584_gb300.krpls import KRP_DESCENT_NODE_MAJOR, KRP_DESCENT_TEAM
+@pytest.mark.parametrize("form", [2, 3])
+def test_node_major_and_team_draws_agree(form):
+    """The node-major forms (2: SIMT batches, 3: tensor-core masses) and the
+    team form differ only in the rounding of the masses: the same draws but
+    for rare near-edge flips, and the same weights."""
+    from paper_2301_12584_gb300.krpls import KRP_DESCENT_TEAM
     Us = synth.uniform_factors(4, 3000, 64, seed=31)
     s = sampler_for(Us, 64)
     J = 1 << 15
     outs = []
-    for form in (KRP_DESCENT_NODE_MAJOR, KRP_DESCENT_TEAM):
+    for form in (form, KRP_DESCENT_TEAM):
         s.set_descent_form(form)
         outs.append(draw(s, Us, -1, J, 5, 9, logq=True))
     diff = (outs[0]["idx"] != outs[1]["idx"]).any(axis=0)
     assert diff.mean() <= 2e-3, diff.mean()
     same = ~diff
     np.testing.assert_allclose(outs[0]["weight"][same], outs[1]["weight"][same], rtol=1e-5)
+    s.close()
+
+
+@pytest.mark.parametrize("R,F", [(64, 64), (128, 128), (40, 160)])
+def test_node_major_tc_launches(R, F):
+    """The tensor-core node-major form runs its own level-synchronous launch
+    sequence (init, root, per level mass + scan + partition, leaf, final
+    stage per draw), the team form one launch per draw; with F > 128 the
+    tensor-core form hands the draw to the team form."""
+    from paper_2301_12584_gb300 import krpls
+    Us = synth.uniform_factors(3, 1000, R, seed=R)
+    s = sampler_for(Us, F)
+    J = 1024
+    idx = torch.zeros((3, J), dtype=torch.int32, device=DEV)
+    w = torch.zeros(J, device=DEV)
+    s.sample_prepare(-1)
+    counts = {}
+    for form in (krpls.KRP_DESCENT_TEAM, krpls.KRP_DESCENT_NODE_MAJOR_TC):
+        s.set_descent_form(form)
+        n0 = krpls.launch_count()
+        s.sample_draw(-1, J, 1, 0, idx, w)
+        counts[form] = krpls.launch_count() - n0
+    assert s.sync_status() == 0, s.last_error()
+    assert counts[krpls.KRP_DESCENT_TEAM] == 1
+    L = 1 << (-(-1000 // F) - 1).bit_length()
+    d, dE = L.bit_length() - 1, (R - 1).bit_length()
+    want = 3 * (2 + 2 + 3 * (d + dE) + 1) + 2 if F <= 128 else 1
+    assert counts[krpls.KRP_DESCENT_NODE_MAJOR_TC] == want, counts
     s.close()
 
 
