@@ -377,7 +377,7 @@ def run_rank_sweep(args):
     achieved = path_bytes * J / (draw_ms / 1e3) / 1e9
     kernel = "krp_descent_fast" if R <= 32 else (
         ("krp_descent_nm<64>" if R <= 64 else "krp_descent_nm<128>") if args.descent == "node_major" else
-        "nt_level<0..2> + nt_scan + nt_part (tensor-core node-major)" if args.descent == "node_major_tc" else
+        "nt_level<0..3> + nt_scan + nt_part (tensor-core node-major)" if args.descent == "node_major_tc" else
         ("krp_descent_team<64,2>" if R <= 64 else "krp_descent_team<128,8>"))
     roof = {"kernel": kernel, "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
             "frac": achieved / hbm, "traffic": None, "algorithmic_bytes_per_launch": path_bytes * J,

@@ -174,7 +174,9 @@ krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t se
  *     masses come from D = H G_v on the tcgen05 tensor cores (split TF32,
  *     m_s = Σ_j D[s, j] H[s, j]) and the leaf's row weights from
  *     D = H U_leafᵀ; decisions within 1e-6 C of an edge are re-taken in
- *     double-float.  Needs F <= 128 and a device workspace of about
+ *     double-float.  Faster than TEAM from R ~ 96 up, but its split-TF32
+ *     masses are less exact: at R = 128 it flips about twice as many draws
+ *     within 1e-5 C of a bin edge.  Needs F <= 128 and a device workspace of about
  *     J (3 R + 24) floats; where that does not hold (or no workspace can be
  *     allocated, e.g. during a graph capture) the team form runs instead.
  * KRP_EINVAL for another value. */

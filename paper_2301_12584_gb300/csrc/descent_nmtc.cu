@@ -854,6 +854,10 @@ cudaError_t nt_launch_level(const NtArgs& A, int per_sm, int num_sms, cudaStream
     auto k = nt_level<MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
+    int occ = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT_THREADS, sm);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(1, std::min(per_sm, occ));
     k<<<(unsigned)(num_sms * per_sm), NT_THREADS, sm, st>>>(A);
     count_launch();
     return cudaGetLastError();
