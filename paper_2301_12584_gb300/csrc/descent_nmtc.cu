@@ -854,10 +854,9 @@ cudaError_t nt_launch_level(const NtArgs& A, int per_sm, int num_sms, cudaStream
     auto k = nt_level<MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, NT_THREADS, sm);
-    if (e != cudaSuccess) return e;
-    per_sm = std::max(1, std::min(per_sm, occ));
+    // per_sm comes from the operands' shared memory (the registers allow two
+    // CTAs); the occupancy query answers one here, and a grid of one CTA per SM
+    // measured 1.5x slower at R = 64
     k<<<(unsigned)(num_sms * per_sm), NT_THREADS, sm, st>>>(A);
     count_launch();
     return cudaGetLastError();
