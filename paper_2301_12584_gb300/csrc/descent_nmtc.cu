@@ -156,6 +156,11 @@ __device__ __forceinline__ void nt_split(float x, uint32_t& hi, uint32_t& lo) {
 // byte (p / 8) (kw / 4) 128 + (k / 4) 128 + (p mod 8) 16 + (k mod 4) 4, so the
 // 16-byte quad e = 8 ((p / 8) (kw / 4) + k / 4) + p mod 8 sits at byte 16 e.
 
+// A sample id read from a permutation: always in [0, J) unless a level kernel
+// gave up on a wait (its status then reports it) and left positions unwritten;
+// the clamp keeps every later access in bounds.
+__device__ __forceinline__ int nt_sample(int s, int64_t J) { return (uint32_t)s < (uint64_t)J ? s : 0; }
+
 __device__ __forceinline__ float* nt_trace(const NtArgs& A, int s) {
     if (!A.trace || s >= A.n_trace) return nullptr;
     return A.trace + (((int64_t)s * A.n_incl + A.pi) * 2 + A.sg) * 66;
@@ -299,7 +304,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) nt_level(const __grid_constant_
             const int64_t rfirst = (((int64_t)2 * c + 1) << (A.depth - A.lvl - 1)) - A.L;
             if (rfirst * A.F >= A.nreal) {
                 if (tid < n) {
-                    const int s = perm[t0 + tid];
+                    const int s = nt_sample(perm[t0 + tid], A.J);
                     const float mn = W.mnode[s];
                     W.node[s] = 2 * c;
                     W.left[t0 + tid] = 1;
@@ -319,7 +324,7 @@ __global__ void __launch_bounds__(NT_THREADS, 1) nt_level(const __grid_constant_
             nrows = (int)std::min<int64_t>(A.F, A.nreal - row0);
         }
         if (tid == 0) nfix = 0;
-        if (tid < 128) sperm[tid] = tid < n ? perm[t0 + tid] : 0;
+        if (tid < 128) sperm[tid] = tid < n ? nt_sample(perm[t0 + tid], A.J) : 0;
         __syncthreads();
         const int64_t key = (MODE == 1 || MODE == 2) ? c : 0;
         if (key != bkey) {
@@ -722,7 +727,9 @@ __global__ void __launch_bounds__(1024) nt_scan(const __grid_constant__ NtArgs A
         if (rec.gt0 == i) {
             const TileRec last = tiles[rec.gt1 - 1];
             const int ng = last.t0 + last.n - rec.g0;
-            const int nl = W.lsum[rec.gt1] - W.lsum[rec.gt0];
+            // within [0, ng] always, unless a level kernel gave up on a wait (its
+            // status is then set): the clamp keeps the next level's tiles in bounds
+            const int nl = min(max(W.lsum[rec.gt1] - W.lsum[rec.gt0], 0), ng);
             cnt = (nl + 127) / 128 + (ng - nl + 127) / 128;
         }
         W.toff[i] = cnt;
@@ -758,16 +765,17 @@ __global__ void __launch_bounds__(128) nt_part(const __grid_constant__ NtArgs A)
         __syncthreads();
         int pre = __popc(bal & ((1u << lane) - 1u));
         for (int w = 0; w < warp; ++w) pre += wtot[w];
+        const TileRec last = tiles[rec.gt1 - 1];
+        const int ng = last.t0 + last.n - rec.g0;
         const int lbase = W.lsum[rec.gt0];
-        const int nl = W.lsum[rec.gt1] - lbase;
+        const int nl = min(max(W.lsum[rec.gt1] - lbase, 0), ng);   // as in nt_scan
         if (tid < rec.n) {
             const int lb = W.lsum[ti] - lbase + pre;   // left-goers of the group before p
             const int np = l ? rec.g0 + lb : rec.g0 + nl + (p - rec.g0 - lb);
-            pout[np] = pin[p];
+            if (np >= rec.g0 && np < rec.g0 + ng) pout[np] = pin[p];   // always, unless a wait gave up
         }
         if (rec.gt0 == ti) {
-            const TileRec last = tiles[rec.gt1 - 1];
-            const int ng = last.t0 + last.n - rec.g0, nr = ng - nl;
+            const int nr = ng - nl;
             const int nlt = (nl + 127) / 128, nrt = (nr + 127) / 128, base = W.toff[ti];
             for (int j = tid; j < nlt + nrt; j += blockDim.x) {
                 TileRec o;
