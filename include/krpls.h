@@ -159,7 +159,7 @@ krp_status krp_sample_draw(krp_sampler* s, int exclude_j, int64_t J, uint64_t se
 
 /* Form of the descent for 32 < R <= 128 (no effect at R <= 32): the same
  * draws up to the rounding of the masses (flips only where a uniform lies
- * within ~1e-6 of a bin edge).
+ * within ~1e-6 of a bin edge; ~1e-5 for the tensor-core form at R = 128).
  *   KRP_DESCENT_AUTO (default) and KRP_DESCENT_TEAM: one team of warps per
  *     sample, two tree levels per fetch, the sample's quadratic-form weights
  *     kept in registers for a whole tree;

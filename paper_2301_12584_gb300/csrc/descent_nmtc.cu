@@ -13,7 +13,8 @@
 // the tensor cores into tensor memory and m_s = Σ_j D[s, j] x_s[j] is read
 // back.  At a leaf the same product with the leaf's rows, D = H U_leafᵀ, gives
 // the rank-1 row weights (U[t] · x_s)² of Eq. second_conditional_dist, and each
-// sample scans its row of D.
+// sample scans its row of D; after the last factor the leverage hᵀG⁺h of every
+// sample (Sec. 2.1's q_s) is the same contraction with G⁺.
 //
 // Precision: split TF32 (TF32x3).  Every operand x = hi + lo (hi = tf32(x),
 // lo = tf32(x - hi)); a product is hi hi' + hi lo' + lo hi', accumulated in
